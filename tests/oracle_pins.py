@@ -1,0 +1,319 @@
+"""Pins for the CPU oracle: checks against what the paper and mathematics fix,
+independent of the oracle's own code.
+
+Each ``check_*`` takes an ``oracle.Oracle`` and raises AssertionError on a
+mismatch. ``test_oracle_pins.py`` runs them on the real oracle;
+``test_oracle_mutations.py`` runs them on copies of the oracle with planted
+mistakes and requires every mistake to be caught.
+
+Independent references used here:
+  * Floyd-Warshall on a dense matrix (distances), a different algorithm from BFS;
+  * closed-form hop distances on grids, paths, cycles, stars, complete graphs;
+  * hand-derived kNN lists (tests/golden/closed_forms.json);
+  * the calibration equation sum_j exp(-(d_j - rho)/sigma) = log2 k written as
+    a polynomial in x = exp(-1/sigma) and solved by numpy.roots (companion
+    matrix eigenvalues), not by bisection;
+  * closed-form fuzzy-union weights on a star.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+
+import numpy as np
+
+from paper_2509_19703_gb300 import graphgen as gg
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "closed_forms.json")
+INF16 = 0xFFFF
+
+
+# --------------------------------------------------------------------------
+# small graph zoo
+# --------------------------------------------------------------------------
+
+def tiny_graphs():
+    """Seeded tiny graphs (n <= 64), connected and disconnected."""
+    out = []
+    for n, p, seed in [(1, 0.5, 1), (2, 1.0, 2), (5, 0.4, 3), (17, 0.15, 4), (40, 0.06, 5),
+                       (64, 0.05, 6), (64, 0.2, 7), (33, 0.0, 8)]:
+        out.append(gg.gnp(n, p, seed))
+    out.append(gg.random_tree(50, 9))
+    out.append(gg.barabasi_albert(60, 2, 10))
+    out.append(gg.disjoint_union([gg.path(3), gg.cycle(7), gg.star(9), gg.grid(4, 5)], "mix"))
+    out.append(gg.disjoint_union([gg.gnp(20, 0.2, 11), gg.complete(6), gg.path(1)], "mix2"))
+    return out
+
+
+def floyd_warshall(g) -> np.ndarray:
+    n = g.n
+    D = np.full((n, n), np.inf)
+    if n:
+        np.fill_diagonal(D, 0.0)
+    for u in range(n):
+        for e in range(g.row_ptr[u], g.row_ptr[u + 1]):
+            D[u, g.col[e]] = 1.0
+    for m in range(n):
+        D = np.minimum(D, D[:, m:m + 1] + D[m:m + 1, :])
+    return D
+
+
+def brute_knn(D: np.ndarray, k: int):
+    n = D.shape[0]
+    idx = np.full((n, k), -1, dtype=np.int64)
+    dist = np.full((n, k), INF16, dtype=np.int64)
+    for s in range(n):
+        cand = sorted((D[s, v], v) for v in range(n) if v != s and np.isfinite(D[s, v]))[:k]
+        for t, (d, v) in enumerate(cand):
+            idx[s, t] = v
+            dist[s, t] = int(d)
+    return idx, dist
+
+
+# --------------------------------------------------------------------------
+# distances and lists
+# --------------------------------------------------------------------------
+
+def check_apsp_floyd_warshall(orc):
+    for g in tiny_graphs():
+        D = floyd_warshall(g)
+        A = orc.apsp(g).astype(np.float64)
+        A[A == INF16] = np.inf
+        assert np.array_equal(A, D), g.name
+
+
+def check_knn_brute_force(orc):
+    for g in tiny_graphs():
+        if g.n < 2:
+            continue
+        D = floyd_warshall(g)
+        for k in sorted({1, 3, 15, g.n - 1}):
+            bi, bd = brute_knn(D, k)
+            for fn in (orc.knn_full, orc.knn_partial):
+                idx, dist = fn(g, k)
+                assert np.array_equal(idx, bi), (g.name, k, fn.__name__)
+                assert np.array_equal(dist.astype(np.int64), bd), (g.name, k, fn.__name__)
+
+
+def check_closed_form_distances(orc):
+    W, H = 6, 9
+    D = orc.apsp(gg.grid(W, H)).astype(np.int64)
+    r, c = np.divmod(np.arange(W * H), W)
+    assert np.array_equal(D, np.abs(r[:, None] - r[None, :]) + np.abs(c[:, None] - c[None, :]))
+    i = np.arange(13)
+    assert np.array_equal(orc.apsp(gg.path(13)).astype(np.int64), np.abs(i[:, None] - i[None, :]))
+    for n in (11, 12):
+        i = np.arange(n)
+        a = np.abs(i[:, None] - i[None, :])
+        assert np.array_equal(orc.apsp(gg.cycle(n)).astype(np.int64), np.minimum(a, n - a))
+    K = orc.apsp(gg.complete(9)).astype(np.int64)
+    assert np.array_equal(K, 1 - np.eye(9, dtype=np.int64))
+    S = orc.apsp(gg.star(10)).astype(np.int64)
+    exp = np.full((10, 10), 2)
+    exp[0, :] = 1
+    exp[:, 0] = 1
+    np.fill_diagonal(exp, 0)
+    assert np.array_equal(S, exp)
+
+
+def _golden_graph(case):
+    kind = case["graph"]
+    if kind == "grid":
+        return gg.grid(case["W"], case["H"])
+    return {"path": gg.path, "cycle": gg.cycle, "star": gg.star, "complete": gg.complete}[kind](case["n"])
+
+
+def check_golden_lists(orc):
+    with open(GOLDEN) as f:
+        cases = json.load(f)["cases"]
+    for case in cases:
+        g = _golden_graph(case)
+        v, k = case["vertex"], case["k"]
+        for fn in (orc.knn_full, orc.knn_partial):
+            idx, dist = fn(g, k, sources=np.array([v]))
+            assert idx[0].tolist() == case["idx"], (case["why"], fn.__name__, idx[0].tolist())
+            assert dist[0].astype(int).tolist() == case["dist"], (case["why"], fn.__name__)
+
+
+def check_full_equals_partial(orc):
+    graphs = [gg.barabasi_albert(400, 3, 21), gg.gnp(300, 0.02, 22), gg.random_tree(300, 23),
+              gg.grid(17, 23), gg.disjoint_union([gg.gnp(100, 0.01, 24), gg.path(5)], "dis")]
+    for g in graphs:
+        for k in (1, 7, 15, 50):
+            a = orc.knn_full(g, k)
+            b = orc.knn_partial(g, k)
+            assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]), (g.name, k)
+
+
+def check_partial_work(orc):
+    """Edges scanned before the stopping level on a grid interior vertex:
+    k=15 stops at D=3 after expanding 1+4+8 vertices of degree 4 (52);
+    k=50 stops at D=5 after 1+4+8+12+16 vertices (164)."""
+    W = 30
+    g = gg.grid(W, W)
+    v = 15 * W + 15
+    for k, want in ((15, 52), (50, 164)):
+        _, _, work = orc.knn_partial(g, k, sources=np.array([v]), return_work=True)
+        assert int(work[0]) == want, (k, int(work[0]))
+
+
+# --------------------------------------------------------------------------
+# rho, sigma, weights
+# --------------------------------------------------------------------------
+
+def _root_in_unit(coeffs_high_to_low):
+    r = np.roots(coeffs_high_to_low)
+    real = [z.real for z in r if abs(z.imag) < 1e-12 and 0.0 < z.real < 1.0]
+    assert len(real) == 1, r
+    return real[0]
+
+
+def _sigma_of_x(x):
+    return -1.0 / math.log(x)
+
+
+def _row(orc, g, v, k):
+    idx, dist = orc.knn_full(g, k, sources=np.array([v]))
+    rho, sigma, a = orc.smooth_knn(dist)
+    return idx[0], dist[0].astype(int), float(rho[0]), float(sigma[0]), a[0]
+
+
+def check_sigma_closed_forms(orc):
+    T15 = math.log2(15)
+    # star leaf: 1 + 14 x = log2 15
+    idx, d, rho, sigma, a = _row(orc, gg.star(40), 5, 15)
+    x = (T15 - 1.0) / 14.0
+    assert rho == 1.0
+    assert abs(sigma - _sigma_of_x(x)) <= 1e-12 * _sigma_of_x(x), (sigma, _sigma_of_x(x))
+    assert abs(a[0] - 1.0) == 0.0 and np.allclose(a[1:], x, rtol=1e-12, atol=0)
+    # star centre: all 15 at d = rho, no root -> sigma floor 1e-3 * mean(d) = 1e-3, weights 1
+    idx, d, rho, sigma, a = _row(orc, gg.star(40), 0, 15)
+    assert abs(sigma - 1e-3) <= 1e-15 and np.all(a == 1.0)
+    # grid top-edge vertex: 3 + 5x + 7x^2 = log2 15
+    idx, d, rho, sigma, a = _row(orc, gg.grid(9, 9), 4, 15)
+    x = (-5.0 + math.sqrt(25.0 + 28.0 * (T15 - 3.0))) / 14.0
+    assert abs(sigma - _sigma_of_x(x)) <= 1e-12 * _sigma_of_x(x)
+    want = np.array([x ** (dd - 1) for dd in d])
+    assert np.allclose(a, want, rtol=1e-11, atol=0)
+    # grid interior, k = 50: 4 + 8x + 12x^2 + 16x^3 + 10x^4 = log2 50
+    idx, d, rho, sigma, a = _row(orc, gg.grid(21, 21), 10 * 21 + 10, 50)
+    x = _root_in_unit([10.0, 16.0, 12.0, 8.0, 4.0 - math.log2(50)])
+    assert abs(sigma - _sigma_of_x(x)) <= 1e-10 * _sigma_of_x(x)
+    assert np.allclose(a, [x ** (dd - 1) for dd in d], rtol=1e-9, atol=0)
+    # path interior, k = 15: 2 + 2x + ... + 2x^6 + x^7 = log2 15
+    idx, d, rho, sigma, a = _row(orc, gg.path(40), 20, 15)
+    x = _root_in_unit([1.0, 2, 2, 2, 2, 2, 2, 2.0 - T15])
+    assert abs(sigma - _sigma_of_x(x)) <= 1e-10 * _sigma_of_x(x)
+    # grid interior, k = 15: 4 at d = rho > log2 15: no root, sigma = 1e-3 * mean d
+    idx, d, rho, sigma, a = _row(orc, gg.grid(9, 9), 40, 15)
+    mean = (4 * 1 + 8 * 2 + 3 * 3) / 15.0
+    assert abs(sigma - 1e-3 * mean) <= 1e-15
+    assert np.all(a[:4] == 1.0) and np.all(a[4:] < 1e-200)
+    # complete graph: every weight 1
+    idx, d, rho, sigma, a = _row(orc, gg.complete(20), 3, 15)
+    assert np.all(a == 1.0)
+    # component of 3 vertices with k = 15: 2 valid entries <= log2 15, sigma = inf, weights 1
+    idx, d, rho, sigma, a = _row(orc, gg.path(3), 0, 15)
+    assert math.isinf(sigma) and a[0] == 1.0 and a[1] == 1.0 and np.all(a[2:] == 0.0)
+    # isolated vertex: nothing valid
+    idx, d, rho, sigma, a = _row(orc, gg.disjoint_union([gg.path(1), gg.path(4)]), 0, 5)
+    assert rho == 0.0 and sigma == 0.0 and np.all(a == 0.0)
+
+
+def check_sigma_residual(orc):
+    """Wherever a root exists, f(sigma) hits log2 k to 1e-12 relative."""
+    for g, k in ((gg.barabasi_albert(500, 3, 31), 15), (gg.random_tree(400, 32), 15),
+                 (gg.gnp(300, 0.03, 33), 30)):
+        idx, dist = orc.knn_full(g, k)
+        rho, sigma, a = orc.smooth_knn(dist)
+        T = math.log2(k)
+        checked = 0
+        for i in range(g.n):
+            d = dist[i][dist[i] != INF16].astype(np.float64)
+            if d.size == 0:
+                continue
+            c_eq = int(np.sum(d == rho[i]))
+            if not (c_eq < T < d.size):
+                continue
+            f = float(np.sum(np.exp(-np.maximum(0.0, d - rho[i]) / sigma[i])))
+            assert abs(f - T) <= 1e-12 * T, (g.name, i, f, T)
+            checked += 1
+        assert checked > 0
+
+
+# --------------------------------------------------------------------------
+# fuzzy union
+# --------------------------------------------------------------------------
+
+def check_union_star(orc):
+    """Star with centre 0 and leaves 1..39, k = 15. A leaf j lists the centre
+    (a = 1) and the 14 smallest other leaves (a = x, x = (log2 15 - 1)/14);
+    the centre lists leaves 1..15 (a = 1). So w(i, j) = 1 when either end is
+    the centre, 2x - x^2 between two leaves that list each other and x when
+    only one does."""
+    n, k = 40, 15
+    g = gg.star(n)
+    r = orc.knn_pipeline(g, k)
+    x = (math.log2(15) - 1.0) / 14.0
+
+    def listed(i, j):  # does i list j?
+        if i == 0:
+            return 1 <= j <= 15
+        if j == 0:
+            return True
+        others = [v for v in range(1, n) if v != i][:14]
+        return j in others
+
+    for i in range(n):
+        for t in range(k):
+            j = int(r["idx"][i, t])
+            if i == 0 or j == 0:
+                want = 1.0
+            else:
+                want = 2 * x - x * x if listed(j, i) else x
+            assert abs(r["w"][i, t] - want) <= 1e-13, (i, j, r["w"][i, t], want)
+    row, col, w = r["coo"]
+    pairs = {(int(a), int(b)): float(c) for a, b, c in zip(row, col, w)}
+    expected = set()
+    for i in range(n):
+        for j in range(n):
+            if i != j and (listed(i, j) or listed(j, i)):
+                expected.add((i, j))
+    assert set(pairs) == expected
+    for (i, j), v in pairs.items():
+        if i == 0 or j == 0:
+            want = 1.0
+        else:
+            want = 2 * x - x * x if (listed(i, j) and listed(j, i)) else x
+        assert abs(v - want) <= 1e-13, (i, j, v, want)
+
+
+def check_union_properties(orc):
+    for g, k in ((gg.barabasi_albert(300, 3, 41), 15), (gg.grid(12, 9), 15),
+                 (gg.disjoint_union([gg.random_tree(80, 42), gg.path(2)]), 10)):
+        r = orc.knn_pipeline(g, k)
+        row, col, w = r["coo"]
+        key = row.astype(np.int64) * g.n + col
+        assert np.all(np.diff(key) > 0), "COO not strictly sorted"
+        assert np.all((w >= 0) & (w <= 1))
+        pairs = {(int(a), int(b)): float(c) for a, b, c in zip(row, col, w)}
+        for (i, j), v in pairs.items():
+            assert pairs.get((j, i)) == v, "COO not symmetric"
+        valid = int(np.sum(r["idx"] >= 0))
+        assert valid <= row.shape[0] <= 2 * valid
+        for i in range(g.n):
+            for t in range(k):
+                j = int(r["idx"][i, t])
+                if j < 0:
+                    assert r["w"][i, t] == 0.0
+                    continue
+                assert abs(pairs[(i, j)] - r["w"][i, t]) <= 1e-15
+                if r["dist"][i, t] == r["rho"][i]:
+                    assert r["w"][i, t] == 1.0
+
+
+ALL_CHECKS = [check_apsp_floyd_warshall, check_knn_brute_force, check_closed_form_distances,
+              check_golden_lists, check_full_equals_partial, check_partial_work,
+              check_sigma_closed_forms, check_sigma_residual, check_union_star,
+              check_union_properties]
