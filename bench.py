@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark of the graph-kNN path: BFS-kNN GTEPS and fraction of HBM peak.
+
+Workload (one step): the full all-pairs form (GUMAP, Algorithm 1: BFS from
+every vertex, kNN in (distance, id) order, UMAP weights, fuzzy union, sorted
+COO) with k = 15 on two seeded synthetic graphs shaped like the paper's
+scale-free and dense inputs: Barabasi-Albert n = 20,000 with 5 edges per new
+vertex (seed 1) and G(n = 5,000, p = 0.1) (seed 2). All sources, so both
+graphs' complete outputs are produced every step.
+
+Work unit (Graph500 convention, as for the paper's O(nm) analysis of the
+all-pairs form): per source, the undirected edges of its connected
+component. GTEPS = work / device time.
+
+value: device time (CUDA events on the launching stream) with the graphs
+  resident in HBM; L2 is flushed (512 MB write) before every timed step and
+  each step is timed on its own.
+e2e: the same metric through the public API from pinned host buffers:
+  gumap_knn_create (H2D copy + validation), gumap_knn_run, D2H copy of
+  idx/dist/w, gumap_knn_destroy, wall-clock per step.
+--impl reference: the CPU oracle (test infrastructure) on a bounded sample
+  of the same sources, same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+K_NEIGHBOURS = 15
+METRIC = "BFS-kNN GTEPS (full all-pairs form, k=15) and % of HBM peak"
+WORKLOAD = ("full-APSP GUMAP kNN + UMAP weights + fuzzy union + sorted COO, k=15, all sources, on "
+            "BA n=20000 m0=5 seed 1 and G(n=5000, p=0.1) seed 2")
+FLUSH_BYTES = 512 << 20
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "msbfs_kernel_traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_2509_19703_gb300", "csrc", "msbfs.cu")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample budget")
+    return p.parse_args()
+
+
+def dist_info():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def build_graphs():
+    from paper_2509_19703_gb300 import graphgen as gg
+    return [gg.config_ba20k(), gg.config_er5k()]
+
+
+def component_work(g):
+    """Per-source work of the full form: undirected edges of the source's component."""
+    import numpy as np
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    A = sp.csr_matrix((np.ones(g.nnz, dtype=np.int8), g.col, g.row_ptr), shape=(g.n, g.n))
+    ncomp, lab = connected_components(A, directed=False)
+    edges = np.bincount(np.repeat(lab, np.diff(g.row_ptr)), minlength=ncomp) // 2
+    return edges[lab].astype(np.int64)  # per source
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        self.tmp = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                          "-lms", "50", "-i", str(self.dev)], stdout=self.tmp,
+                                         stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.1)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        self.tmp.seek(0)
+        rows = [r.strip() for r in self.tmp.read().splitlines() if r.strip()]
+        os.unlink(self.tmp.name)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            f = [x.strip() for x in r.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                smax = max(smax, float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+
+def measured_peak_gbs():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_sha():
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def recorded_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; otherwise None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sha256") != kernel_sha():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def msbfs_alg_bytes(g, block_bits, level_sum, launches):
+    """Algorithmic bytes of the MS-BFS launches: per level the four bitset
+    streams (read F and V, write V and N: 16 n W bytes, W = bits / 32) plus
+    the CSR once; per launch the clearing of V and N (8 n W bytes)."""
+    W = block_bits // 32
+    per_level = 16 * g.n * W + 4 * (g.n + 1) + 4 * g.nnz
+    return level_sum * per_level + launches * 8 * g.n * W
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(graphs, works, budget_s):
+    """Time the CPU oracle (full BFS per source, (dist, id) sort, FP64
+    weights) on seeded source samples, scaled to the GPU's per-graph time
+    share; returns (GTEPS, description)."""
+    import numpy as np
+    import oracle
+    total_work, total_t, parts = 0, 0.0, []
+    per_graph = budget_s / len(graphs)
+    for g, w in zip(graphs, works):
+        rng = np.random.default_rng(1234)
+        order = rng.permutation(g.n).astype(np.int32)
+        t0 = time.perf_counter()
+        done = 0
+        chunk = 16
+        while done < g.n and time.perf_counter() - t0 < per_graph:
+            src = order[done:done + chunk]
+            _, dist = oracle.knn_full(g, K_NEIGHBOURS, sources=src)
+            oracle.smooth_knn(dist)
+            done += len(src)
+        dt = time.perf_counter() - t0
+        total_work += int(w[order[:done]].sum())
+        total_t += dt
+        parts.append(f"{done} of {g.n} sources of {g.name}")
+    return total_work / total_t / 1e9, "; ".join(parts) + " (seeded random order, 1 thread)"
+
+
+# ---------------------------------------------------------------- arms
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    graphs = build_graphs()
+    works = [component_work(g) for g in graphs]
+    budget = max(0.2, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    desc = ""
+    for i in range(args.warmup + args.steps):
+        v, desc = oracle_sample(graphs, works, budget)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": budget * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "k": K_NEIGHBOURS},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {desc}, about {budget:.0f} s"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2509_19703_gb300 import gumap
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    graphs = build_graphs()
+    works = [component_work(g) for g in graphs]
+    work_per_step = int(sum(int(w.sum()) for w in works))
+    kgs = [gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=gumap.FULL) for g in graphs]
+    for kg in kgs:
+        kg.set_option(gumap.OPT_PROFILE, 1)
+    outs = [kg.alloc_outputs(g.n) for kg, g in zip(kgs, graphs)]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        for kg, o in zip(kgs, outs):
+            kg.run(out=o)
+    for kg in kgs:
+        kg.check()
+        kg.reset_stats()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        ev[s][0].record(stream)
+        for kg, o in zip(kgs, outs):
+            kg.run(out=o)
+        ev[s][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    for kg in kgs:
+        kg.check()
+    stats = [kg.stats() for kg in kgs]
+    value = world * work_per_step / (ms * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (the MS-BFS launches)
+    alg = sum(msbfs_alg_bytes(g, st["block_bits"], st["bfs_level_sum"], st["bfs_launches"])
+              for g, st in zip(graphs, stats))
+    bfs_ms = sum(st["bfs_ms"] for st in stats)
+    launches = sum(st["bfs_launches"] for st in stats)
+    peak, peak_kind = measured_peak_gbs()
+    achieved = alg / (bfs_ms * 1e-3) / 1e9 if bfs_ms > 0 else 0.0
+    traffic = recorded_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if peak else None,
+                "traffic": traffic, "peak_source": peak_kind,
+                "kernel": "msbfs_kernel", "launches": launches,
+                "avg_launch_ms": bfs_ms / launches if launches else None,
+                "alg_bytes_per_launch": alg / launches if launches else None,
+                "kernel_share_of_step": (bfs_ms / args.steps) / ms if ms else None}
+    gpu_launches = sum(st["kernel_launches"] for st in stats)
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = []
+        h2d = d2h = 0
+        for g in graphs:
+            rp = torch.from_numpy(g.row_ptr).pin_memory()
+            col = torch.from_numpy(g.col).pin_memory()
+            pinned.append((rp, col))
+            h2d += rp.numel() * 4 + col.numel() * 4
+        host_out = [dict(idx=torch.empty((g.n, K_NEIGHBOURS), dtype=torch.int32).pin_memory(),
+                         dist=torch.empty((g.n, K_NEIGHBOURS), dtype=torch.int16).pin_memory(),
+                         w=torch.empty((g.n, K_NEIGHBOURS), dtype=torch.float32).pin_memory()) for g in graphs]
+        d2h = sum(o[key].numel() * o[key].element_size() for o in host_out for key in o)
+        times = []
+        for s in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for g, (rp, col), ho, o in zip(graphs, pinned, host_out, outs):
+                drp = rp.to("cuda", non_blocking=True)
+                dcol = col.to("cuda", non_blocking=True)
+                h = gumap.gumap_knn_create(drp, dcol, g.n, g.nnz, K_NEIGHBOURS, gumap.FULL, gumap.CSR_ON_DEVICE)
+                gumap.gumap_knn_run(h, None, g.n, o["idx"], o["dist"], o["w"])
+                for key in ("idx", "dist", "w"):
+                    ho[key].copy_(o[key], non_blocking=True)
+                torch.cuda.synchronize()
+                gumap.gumap_knn_destroy(h)
+            dt = time.perf_counter() - t0
+            if s > 0:
+                times.append(dt)
+        e2e_t = statistics.median(times)
+        e2e = {"value": world * work_per_step / e2e_t / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t * 1e3, "timing": "wall clock, median"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc = oracle_sample(graphs, works, args.cpu_seconds)
+        cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "u32 bitsets / f32 weights", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "k": K_NEIGHBOURS,
+                           "graphs": [{"name": g.name, "n": g.n, "m": g.m} for g in graphs],
+                           "work_edges_per_step": work_per_step, "parallelism": f"replicas x{world}",
+                           "l2": "flushed (512 MB write) before each timed step",
+                           "block_bits": [st["block_bits"] for st in stats],
+                           "levels_max": [st["levels_max"] for st in stats]},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    for kg in kgs:
+        kg.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,203 @@
+/*
+ * gumap.h - C ABI of the GB300 graph-kNN library.
+ *
+ * The library computes, for an undirected unweighted graph G = (V, E) and a
+ * neighbourhood size k, the graph-theoretic kNN graph used by UMAP-based
+ * graph drawing, and the UMAP fuzzy weights of its edges:
+ *
+ *   C0  hop distances by breadth-first search from each source vertex,
+ *       either to completion (the all-pairs form of GUMAP, Algorithm 1,
+ *       "S = AllPairsShortestPath(G)") or stopped once k other vertices are
+ *       reached (PartialBFS of SL-GUMAP, Algorithm 4, Section 3.3.1);
+ *   C1  the k nearest other vertices of each source in (distance, vertex id)
+ *       order (Algorithm 1 "kNN(S)"; the paper breaks ties at random, this
+ *       library fixes the tie rule to ascending vertex id so the result is
+ *       unique and identical between the two forms);
+ *   W   rho_i = distance to the nearest neighbour, sigma_i solving
+ *       sum_j exp(-max(0, d_ij - rho_i) / sigma_i) = log2 k, and the directed
+ *       similarity a_ij = exp(-max(0, d_ij - rho_i) / sigma_i) (Section 2.1,
+ *       h_ij), then the fuzzy union w_ij = a_ij + a_ji - a_ij a_ji of the
+ *       UMAP implementation the paper builds on (Section 5.1.1).
+ *
+ * Conventions shared by every call:
+ *   - Vertex ids are int32 in [0, n). Distances are hop counts stored as
+ *     uint16; GUMAP_DIST_INF (0xFFFF) marks a padded slot.
+ *   - A source with fewer than k reachable other vertices gets its reachable
+ *     ones followed by padding: id -1, distance 0xFFFF, weight 0 (Section 3.2:
+ *     pairs with no connecting path carry an "infinite" value).
+ *   - Every call returns an int status (GUMAP_OK = 0). Nothing throws or
+ *     aborts across the ABI. gumap_status_string() names a status;
+ *     gumap_last_error() returns a message for the calling thread's last
+ *     failure.
+ *   - "device" pointers are CUDA device (or managed) memory of the handle's
+ *     device; "host" pointers are ordinary CPU memory.
+ *   - A gumap_knn handle is not thread-safe: one thread (or external locking)
+ *     per handle. Different handles may be used concurrently.
+ *   - Work is enqueued on the caller's cudaStream_t passed as `void* stream`
+ *     (NULL = the legacy default stream). Calls marked "asynchronous" return
+ *     before the device work finishes; their outputs are valid once the
+ *     stream reaches that point.
+ */
+#ifndef GUMAP_H
+#define GUMAP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define GUMAP_OK                  0
+#define GUMAP_ERR_INVALID_ARG     1  /* a pointer, size, k, mode or flag is invalid */
+#define GUMAP_ERR_INVALID_GRAPH   2  /* CSR not symmetric / unsorted / self loop / duplicate / id out of range */
+#define GUMAP_ERR_OOM             3  /* device or host allocation failed */
+#define GUMAP_ERR_CUDA            4  /* a CUDA runtime call failed (see gumap_last_error) */
+#define GUMAP_ERR_AGAIN           5  /* server queue full: retry later */
+#define GUMAP_PENDING             6  /* server request not finished yet */
+#define GUMAP_ERR_TIMEOUT         7  /* a bounded device-side wait gave up (no hang, no trap) */
+#define GUMAP_ERR_TOO_LARGE       8  /* request can never fit the server's device-memory budget */
+#define GUMAP_ERR_UNKNOWN_REQUEST 9  /* server request id unknown or already released */
+
+/* ------------------------------------------------------------------ modes */
+#define GUMAP_FULL    0  /* BFS to completion from each source (GUMAP, Algorithm 1) */
+#define GUMAP_PARTIAL 1  /* BFS stopped at the level that reaches k (SL-GUMAP, Algorithm 4) */
+
+/* ------------------------------------------------------------------ flags */
+#define GUMAP_WEIGHTS_UNION    0x0u /* out_w = fuzzy-union weight w_ij (default; sources must be NULL) */
+#define GUMAP_WEIGHTS_DIRECTED 0x1u /* out_w = directed similarity a_ij of the source's own list */
+#define GUMAP_CSR_ON_DEVICE    0x2u /* row_ptr / col_idx passed to gumap_knn_create are device pointers */
+
+#define GUMAP_MAX_K    256
+#define GUMAP_DIST_INF 0xFFFFu
+
+/* ---------------------------------------------------------------- engines */
+#define GUMAP_ENGINE_AUTO     0 /* pick by graph size, mode and the tuned table */
+#define GUMAP_ENGINE_MSBFS    1 /* bit-parallel multi-source BFS, bitsets in global memory (L2) */
+#define GUMAP_ENGINE_MSBFS_SM 2 /* bit-parallel multi-source BFS, bitsets in one CTA's shared memory */
+#define GUMAP_ENGINE_FRONTIER 3 /* partial form only: warp per source, bounded merge of sorted rows */
+
+/* --------------------------------------------------------------- options */
+#define GUMAP_OPT_ENGINE      1 /* value: GUMAP_ENGINE_*                                 */
+#define GUMAP_OPT_BLOCK_BITS  2 /* value: sources per MS-BFS block (multiple of 128), 0 = auto */
+#define GUMAP_OPT_PROFILE     3 /* value: 1 = time each BFS launch with CUDA events       */
+#define GUMAP_OPT_STATE_BYTES 4 /* value: device bytes allowed for MS-BFS bitsets, 0 = auto */
+
+typedef struct gumap_knn gumap_knn;
+
+/*
+ * gumap_knn_create - validate and take a copy of a graph (step "input G",
+ * Algorithm 1 / Algorithm 4 line 1).
+ *
+ *   h        out: new handle (NULL on failure).
+ *   row_ptr  CSR row offsets, int32[n + 1], row_ptr[0] = 0, row_ptr[n] = nnz.
+ *   col_idx  CSR column ids, int32[nnz]. The graph must be undirected and
+ *            simple: every row sorted strictly ascending (no duplicates), no
+ *            self loop, ids in [0, n), and (u, v) present iff (v, u) present.
+ *   n        number of vertices, 1 <= n < 2^31.
+ *   nnz      number of directed entries (2 |E|), 0 <= nnz < 2^31.
+ *   k        neighbourhood size, 1 <= k <= min(n - 1, GUMAP_MAX_K) (k = 1 if n = 1 is rejected).
+ *   mode     GUMAP_FULL or GUMAP_PARTIAL.
+ *   flags    GUMAP_WEIGHTS_* | GUMAP_CSR_ON_DEVICE.
+ *   device   CUDA device ordinal; it becomes current on the calling thread.
+ *
+ * Host CSR (default) is validated on the host; device CSR is validated by a
+ * device kernel before being copied (the call synchronises once). The
+ * library copies the CSR into memory it owns; the caller's arrays may be
+ * freed on return. Errors: INVALID_ARG, INVALID_GRAPH, OOM, CUDA.
+ */
+int gumap_knn_create(gumap_knn **h, const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
+                     int64_t nnz, int32_t k, int mode, uint32_t flags, int device);
+
+/*
+ * gumap_knn_run - compute the kNN lists and weights of a set of sources
+ * (C0 + C1 + weights; Algorithm 1 lines "S = AllPairsShortestPath(G)",
+ * "G_k = kNN(S)"; Algorithm 4; Section 2.1). Asynchronous on `stream`.
+ *
+ *   sources  device int32[n_src] of source vertex ids, or NULL for all
+ *            vertices 0..n-1 in order (then n_src must equal n).
+ *   n_src    number of sources, 0 <= n_src <= 2^31 - 1.
+ *   out_idx  device int32[n_src][k], row-major: row i lists the neighbours of
+ *            sources[i] in (distance, id) order, padded with -1.
+ *   out_dist device uint16[n_src][k]: hop distance of each slot, 0xFFFF pad.
+ *   out_w    device float[n_src][k]: the union weight w_ij (GUMAP_WEIGHTS_UNION,
+ *            requires sources == NULL) or the directed a_ij
+ *            (GUMAP_WEIGHTS_DIRECTED); 0 for padded slots.
+ *
+ * All three outputs are owned by the caller and must not overlap. The call
+ * may grow library-owned scratch (which may synchronise the device) when
+ * n_src exceeds every earlier call. With union weights the symmetric COO is
+ * also built and kept in the handle for gumap_knn_coo(). Errors:
+ * INVALID_ARG (bad pointer/size, union with explicit sources), OOM, CUDA.
+ * Device-side failures (a bounded wait that timed out) are reported by
+ * gumap_knn_check().
+ */
+int gumap_knn_run(gumap_knn *h, const int32_t *sources, int32_t n_src, int32_t *out_idx,
+                  uint16_t *out_dist, float *out_w, void *stream);
+
+/*
+ * gumap_knn_rho_sigma - copy rho_i and sigma_i of the last run (Section 2.1)
+ * into device float[n_src] buffers. Asynchronous on `stream` (use the run's
+ * stream or order it after). sigma is +inf for a row whose valid entries
+ * number at most log2 k (every weight 1) and 0 for a row with no valid entry.
+ * Errors: INVALID_ARG (no run yet, NULL pointer).
+ */
+int gumap_knn_rho_sigma(gumap_knn *h, float *rho, float *sigma, void *stream);
+
+/*
+ * gumap_knn_coo - copy the symmetric fuzzy-union graph of the last run as a
+ * COO sorted by (row, col) (the union of Section 5.1.1's UMAP
+ * implementation; every pair appears once, w_ij = w_ji).
+ *
+ *   row, col  device int32[2 * n * k] (capacity bound; may be NULL to skip)
+ *   w         device float[2 * n * k] (may be NULL to skip)
+ *   nnz       device int64[1]: receives the entry count, nk_valid <= nnz <= 2 nk_valid.
+ *
+ * Asynchronous on `stream`. Errors: INVALID_ARG (last run had no union).
+ */
+int gumap_knn_coo(gumap_knn *h, int32_t *row, int32_t *col, float *w, int64_t *nnz, void *stream);
+
+/*
+ * gumap_knn_check - wait for `stream` and report the device status word of
+ * the handle's kernels: GUMAP_OK or GUMAP_ERR_TIMEOUT (a bounded device
+ * barrier gave up; the outputs of that run are undefined, the context
+ * stays usable). Clears the word.
+ */
+int gumap_knn_check(gumap_knn *h, void *stream);
+
+/* gumap_knn_set_option - set a GUMAP_OPT_* value (takes effect on the next run). */
+int gumap_knn_set_option(gumap_knn *h, int option, int64_t value);
+
+typedef struct {
+    int32_t engine;          /* GUMAP_ENGINE_* used by the last run */
+    int32_t block_bits;      /* sources per MS-BFS block in the last run (0 if none) */
+    int32_t n_blocks;        /* MS-BFS launches (source blocks) in the last run */
+    int32_t levels_max;      /* deepest BFS level over the blocks of the last run */
+    int64_t bfs_launches;    /* BFS kernel launches since the last reset */
+    double  bfs_ms;          /* summed device time of those launches (GUMAP_OPT_PROFILE on), ms */
+    int64_t bfs_level_sum;   /* sum over launches of the BFS levels each ran */
+    int64_t kernel_launches; /* all library kernel launches since the last reset */
+    int64_t device_bytes;    /* device memory held by the handle */
+} gumap_knn_stats;
+
+/*
+ * gumap_knn_get_stats - counters since the last reset. Synchronises the
+ * device (it reads device-side level counters and CUDA events).
+ */
+int gumap_knn_get_stats(gumap_knn *h, gumap_knn_stats *out);
+int gumap_knn_reset_stats(gumap_knn *h);
+
+/* gumap_knn_destroy - free everything the handle owns (synchronises the device). NULL is allowed. */
+int gumap_knn_destroy(gumap_knn *h);
+
+/* Static string for a status code (never NULL). */
+const char *gumap_status_string(int status);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char *gumap_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GUMAP_H */

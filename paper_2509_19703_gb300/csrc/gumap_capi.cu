@@ -1,0 +1,549 @@
+// Host runtime of libgumap: the C ABI of include/gumap.h.
+//
+// A handle owns a device copy of the CSR graph and the scratch of the
+// engines. gumap_knn_run enqueues, on the caller's stream and without any
+// host synchronisation:
+//   C0+C1  the BFS engine over blocks of sources (msbfs.cu, frontier.cu),
+//          writing the (distance, id)-ordered kNN rows into the caller's
+//          out_idx/out_dist;
+//   W      rho/sigma/a_ij (weights.cu) and, for union weights, the fuzzy
+//          union and the symmetric COO sorted by an LSD radix sort (sort.cu).
+#include "gumap.h"
+#include "gumap_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace gumap;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(GUMAP_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(GUMAP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);  \
+    } while (0)
+
+int key_bits_for(int32_t n) {
+    unsigned x = n > 1 ? (unsigned)(n - 1) : 1u;
+    int b = 0;
+    while (x) {
+        ++b;
+        x >>= 1;
+    }
+    return b;
+}
+
+// Host-side CSR validation (same rules as the device validator).
+bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, std::string& why) {
+    if (rp[0] != 0) { why = "row_ptr[0] != 0"; return false; }
+    if ((int64_t)rp[n] != nnz) { why = "row_ptr[n] != nnz"; return false; }
+    for (int32_t u = 0; u < n; ++u)
+        if (rp[u + 1] < rp[u]) { why = "row_ptr not monotone"; return false; }
+    for (int32_t u = 0; u < n; ++u) {
+        int32_t prev = -1;
+        for (int32_t p = rp[u]; p < rp[u + 1]; ++p) {
+            const int32_t v = col[p];
+            if (v < 0 || v >= n) { why = "column id out of range"; return false; }
+            if (v == u) { why = "self loop"; return false; }
+            if (v <= prev) { why = "row not strictly ascending (unsorted or duplicate)"; return false; }
+            prev = v;
+            const int32_t* b = col + rp[v];
+            const int32_t* e = col + rp[v + 1];
+            const int32_t* f = std::lower_bound(b, e, u);
+            if (f == e || *f != u) { why = "graph not symmetric"; return false; }
+        }
+    }
+    return true;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct gumap_knn {
+    int device = 0;
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t k = 1;
+    int mode = GUMAP_FULL;
+    uint32_t flags = 0;
+    int num_sms = 0;
+    int coop_grid = 0;
+
+    int32_t* d_rp = nullptr;
+    int32_t* d_col = nullptr;
+    int32_t* d_identity = nullptr;
+    DeviceCounters* d_ctr = nullptr;
+
+    // options
+    int opt_engine = GUMAP_ENGINE_AUTO;
+    int64_t opt_block_bits = 0;
+    int opt_profile = 0;
+    int64_t opt_state_bytes = 0;
+
+    // MS-BFS scratch
+    DevBuf bits;        // F, N, V
+    DevBuf act, need, cnt;
+
+    // per-run scratch
+    DevBuf rho, sigma, a;
+    DevBuf keys, vals, keys_tmp, vals_tmp, sort_temp;
+
+    // last run
+    int32_t last_n_src = -1;
+    bool last_union = false;
+    unsigned long long* coo_keys = nullptr;
+    float* coo_vals = nullptr;
+    int coo_key_bits = 0;
+    int last_engine = 0;
+    int last_block_bits = 0;
+    int last_blocks = 0;
+
+    // stats
+    int64_t bfs_launches = 0;
+    int64_t kernel_launches = 0;
+    std::vector<cudaEvent_t> ev_pool;  // pairs
+    size_t ev_used = 0;
+    double bfs_ms_done = 0.0;
+};
+
+namespace {
+
+int ensure(DevBuf& b, size_t bytes, const char* what) {
+    if (b.bytes >= bytes && b.p) return GUMAP_OK;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (bytes == 0) bytes = 16;
+    CK(cudaMalloc(&b.p, bytes), what);
+    b.bytes = bytes;
+    return GUMAP_OK;
+}
+
+void release(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+size_t held_bytes(const gumap_knn* h) {
+    size_t t = (size_t)(h->n + 1) * 4 + (size_t)h->nnz * 4 + (size_t)h->n * 4 + sizeof(DeviceCounters);
+    const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
+                          &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
+    for (const DevBuf* b : bs) t += b->bytes;
+    return t;
+}
+
+// Sources per MS-BFS block: the largest multiple of 128 whose three bitsets
+// fit the state budget (default 96 MB, so a block's state stays resident in
+// the 126 MB L2), balanced over the blocks the sources need.
+int choose_block_bits(const gumap_knn* h, int32_t n_src) {
+    if (h->opt_block_bits > 0) return (int)h->opt_block_bits;
+    const double budget = h->opt_state_bytes > 0 ? (double)h->opt_state_bytes : 96.0 * 1024 * 1024;
+    long long smax = (long long)(budget * 8.0 / (3.0 * (double)std::max<int32_t>(h->n, 1)));
+    smax = (smax / 128) * 128;
+    if (smax < 128) smax = 128;
+    if (smax > 32768) smax = 32768;
+    const long long want = std::max<long long>(n_src, 1);
+    const long long nblocks = (want + smax - 1) / smax;
+    long long s = (want + nblocks - 1) / nblocks;
+    s = ((s + 127) / 128) * 128;
+    return (int)s;
+}
+
+int pick_engine(const gumap_knn* h) {
+    if (h->opt_engine != GUMAP_ENGINE_AUTO) return h->opt_engine;
+    return h->mode == GUMAP_PARTIAL ? GUMAP_ENGINE_FRONTIER : GUMAP_ENGINE_MSBFS;
+}
+
+int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b) {
+    if (h->ev_used + 2 > h->ev_pool.size()) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e), "cudaEventCreate");
+            h->ev_pool.push_back(e);
+        }
+    }
+    *a = h->ev_pool[h->ev_used];
+    *b = h->ev_pool[h->ev_used + 1];
+    h->ev_used += 2;
+    return GUMAP_OK;
+}
+
+int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
+              cudaStream_t st) {
+    const int S = choose_block_bits(h, n_src);
+    if (S % 128 != 0 || S <= 0) return fail(GUMAP_ERR_INVALID_ARG, "block bits must be a positive multiple of 128");
+    const int W = S / 32;
+    const size_t words = (size_t)h->n * W;
+    int rc;
+    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t), "bitsets"))) return rc;
+    if ((rc = ensure(h->act, (size_t)W * 4, "act"))) return rc;
+    if ((rc = ensure(h->need, (size_t)W * 4, "need"))) return rc;
+    if ((rc = ensure(h->cnt, (size_t)S * 4, "cnt"))) return rc;
+    uint32_t* base = static_cast<uint32_t*>(h->bits.p);
+    const int nblocks = (int)(((long long)n_src + S - 1) / S);
+    for (int b = 0; b < nblocks; ++b) {
+        MsbfsArgs a{};
+        a.row_ptr = h->d_rp;
+        a.col = h->d_col;
+        a.n = h->n;
+        a.src = src + (size_t)b * S;
+        a.nb = std::min<int32_t>(S, n_src - b * S);
+        a.W = W;
+        a.F = base;
+        a.N = base + words;
+        a.V = base + 2 * words;
+        a.act = static_cast<uint32_t*>(h->act.p);
+        a.need = static_cast<uint32_t*>(h->need.p);
+        a.cnt = static_cast<int32_t*>(h->cnt.p);
+        a.out_idx = out_idx + (size_t)b * S * h->k;
+        a.out_dist = out_dist + (size_t)b * S * h->k;
+        a.k = h->k;
+        a.partial = h->mode == GUMAP_PARTIAL ? 1 : 0;
+        a.ctr = h->d_ctr;
+        CK(cudaMemsetAsync(&h->d_ctr->bar, 0, sizeof(GridBarrier), st), "reset barrier");
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (h->opt_profile) {
+            if ((rc = next_event_pair(h, &e0, &e1))) return rc;
+            CK(cudaEventRecord(e0, st), "cudaEventRecord");
+        }
+        CK(launch_msbfs(a, h->coop_grid, 256, st), "msbfs launch");
+        if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
+        h->bfs_launches++;
+        h->kernel_launches++;
+    }
+    h->last_block_bits = S;
+    h->last_blocks = nblocks;
+    return GUMAP_OK;
+}
+
+int run_frontier(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
+                 cudaStream_t st) {
+    FrontierArgs a{};
+    a.row_ptr = h->d_rp;
+    a.col = h->d_col;
+    a.n = h->n;
+    a.src = src;
+    a.n_src = n_src;
+    a.k = h->k;
+    a.out_idx = out_idx;
+    a.out_dist = out_dist;
+    a.status = &h->d_ctr->status;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc;
+    if (h->opt_profile) {
+        if ((rc = next_event_pair(h, &e0, &e1))) return rc;
+        CK(cudaEventRecord(e0, st), "cudaEventRecord");
+    }
+    CK(launch_frontier(a, st), "frontier launch");
+    if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
+    h->bfs_launches++;
+    h->kernel_launches++;
+    h->last_block_bits = 0;
+    h->last_blocks = 1;
+    return GUMAP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gumap_status_string(int s) {
+    switch (s) {
+        case GUMAP_OK: return "GUMAP_OK";
+        case GUMAP_ERR_INVALID_ARG: return "GUMAP_ERR_INVALID_ARG";
+        case GUMAP_ERR_INVALID_GRAPH: return "GUMAP_ERR_INVALID_GRAPH";
+        case GUMAP_ERR_OOM: return "GUMAP_ERR_OOM";
+        case GUMAP_ERR_CUDA: return "GUMAP_ERR_CUDA";
+        case GUMAP_ERR_AGAIN: return "GUMAP_ERR_AGAIN";
+        case GUMAP_PENDING: return "GUMAP_PENDING";
+        case GUMAP_ERR_TIMEOUT: return "GUMAP_ERR_TIMEOUT";
+        case GUMAP_ERR_TOO_LARGE: return "GUMAP_ERR_TOO_LARGE";
+        case GUMAP_ERR_UNKNOWN_REQUEST: return "GUMAP_ERR_UNKNOWN_REQUEST";
+        default: return "GUMAP_ERR_UNKNOWN_STATUS";
+    }
+}
+
+const char* gumap_last_error(void) { return g_last_error.c_str(); }
+
+int gumap_knn_destroy(gumap_knn* h) {
+    if (!h) return GUMAP_OK;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    cudaFree(h->d_rp);
+    cudaFree(h->d_col);
+    cudaFree(h->d_identity);
+    cudaFree(h->d_ctr);
+    DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
+                    &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
+    for (DevBuf* b : bs) release(*b);
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    delete h;
+    return GUMAP_OK;
+}
+
+int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
+                     int32_t k, int mode, uint32_t flags, int device) {
+    if (!out) return fail(GUMAP_ERR_INVALID_ARG, "h is NULL");
+    *out = nullptr;
+    if (!row_ptr || (!col_idx && nnz > 0)) return fail(GUMAP_ERR_INVALID_ARG, "NULL CSR pointer");
+    if (n < 2) return fail(GUMAP_ERR_INVALID_ARG, "n must be >= 2 (got %d)", n);
+    if (nnz < 0 || nnz > 0x7FFFFFFFll) return fail(GUMAP_ERR_INVALID_ARG, "nnz out of range");
+    if (k < 1 || k > GUMAP_MAX_K || k > n - 1) return fail(GUMAP_ERR_INVALID_ARG, "k must be in [1, min(n-1, %d)]", GUMAP_MAX_K);
+    if (mode != GUMAP_FULL && mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "bad mode");
+    if (flags & ~(GUMAP_WEIGHTS_DIRECTED | GUMAP_CSR_ON_DEVICE)) return fail(GUMAP_ERR_INVALID_ARG, "unknown flag");
+    if (2ll * n * k > 0x7FFFFFFFll * 2) return fail(GUMAP_ERR_INVALID_ARG, "n * k too large");
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
+    if (device < 0 || device >= ndev) return fail(GUMAP_ERR_INVALID_ARG, "bad device %d", device);
+    CK(cudaSetDevice(device), "cudaSetDevice");
+
+    if (!(flags & GUMAP_CSR_ON_DEVICE)) {
+        std::string why;
+        if (!host_csr_ok(row_ptr, col_idx, n, nnz, why)) return fail(GUMAP_ERR_INVALID_GRAPH, "invalid CSR: %s", why.c_str());
+    }
+    gumap_knn* h = new (std::nothrow) gumap_knn();
+    if (!h) return fail(GUMAP_ERR_OOM, "host allocation");
+    h->device = device;
+    h->n = n;
+    h->nnz = nnz;
+    h->k = k;
+    h->mode = mode;
+    h->flags = flags;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) { gumap_knn_destroy(h); return cuda_fail(e, "cudaGetDeviceProperties"); }
+    h->num_sms = prop.multiProcessorCount;
+    const int per_sm = msbfs_max_blocks_per_sm(256);
+    if (per_sm <= 0) { gumap_knn_destroy(h); return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident"); }
+    h->coop_grid = h->num_sms * per_sm;
+
+    const cudaMemcpyKind kind = (flags & GUMAP_CSR_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if ((e = cudaMalloc(&h->d_rp, sizeof(int32_t) * (n + 1))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_col, sizeof(int32_t) * std::max<int64_t>(nnz, 1))) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_identity, sizeof(int32_t) * n)) != cudaSuccess ||
+        (e = cudaMalloc(&h->d_ctr, sizeof(DeviceCounters))) != cudaSuccess) {
+        gumap_knn_destroy(h);
+        return cuda_fail(e, "cudaMalloc");
+    }
+    if ((e = cudaMemcpy(h->d_rp, row_ptr, sizeof(int32_t) * (n + 1), kind)) != cudaSuccess ||
+        (nnz > 0 && (e = cudaMemcpy(h->d_col, col_idx, sizeof(int32_t) * nnz, kind)) != cudaSuccess) ||
+        (e = cudaMemset(h->d_ctr, 0, sizeof(DeviceCounters))) != cudaSuccess ||
+        (e = launch_identity(h->d_identity, n, 0)) != cudaSuccess) {
+        gumap_knn_destroy(h);
+        return cuda_fail(e, "upload");
+    }
+    if (flags & GUMAP_CSR_ON_DEVICE) {
+        int32_t bad = 0;
+        if ((e = launch_validate_csr(h->d_rp, h->d_col, n, nnz, &h->d_ctr->status, 0)) != cudaSuccess ||
+            (e = cudaMemcpy(&bad, &h->d_ctr->status, sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            gumap_knn_destroy(h);
+            return cuda_fail(e, "device CSR validation");
+        }
+        cudaMemset(&h->d_ctr->status, 0, sizeof(int32_t));
+        if (bad) {
+            gumap_knn_destroy(h);
+            return fail(GUMAP_ERR_INVALID_GRAPH, "invalid CSR (device validation)");
+        }
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+        gumap_knn_destroy(h);
+        return cuda_fail(e, "create");
+    }
+    *out = h;
+    return GUMAP_OK;
+}
+
+int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
+                  float* out_w, void* stream) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    if (n_src < 0) return fail(GUMAP_ERR_INVALID_ARG, "n_src < 0");
+    if (!sources && n_src != h->n) return fail(GUMAP_ERR_INVALID_ARG, "sources == NULL requires n_src == n");
+    const bool want_union = !(h->flags & GUMAP_WEIGHTS_DIRECTED);
+    if (want_union && sources) return fail(GUMAP_ERR_INVALID_ARG, "union weights need sources == NULL (all vertices)");
+    if (n_src > 0 && (!out_idx || !out_dist || !out_w)) return fail(GUMAP_ERR_INVALID_ARG, "NULL output");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    h->last_n_src = n_src;
+    h->last_union = false;
+    if (n_src == 0) return GUMAP_OK;
+    const int32_t* src = sources ? sources : h->d_identity;
+    const int32_t k = h->k;
+    int rc;
+    const size_t slots = (size_t)n_src * k;
+    if ((rc = ensure(h->rho, (size_t)n_src * 4, "rho")) || (rc = ensure(h->sigma, (size_t)n_src * 4, "sigma")))
+        return rc;
+    if (want_union && (rc = ensure(h->a, slots * 4, "a"))) return rc;
+
+    const int engine = pick_engine(h);
+    h->last_engine = engine;
+    if (engine == GUMAP_ENGINE_MSBFS) {
+        rc = run_msbfs(h, src, n_src, out_idx, out_dist, st);
+    } else if (engine == GUMAP_ENGINE_FRONTIER) {
+        if (h->mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
+        rc = run_frontier(h, src, n_src, out_idx, out_dist, st);
+    } else {
+        return fail(GUMAP_ERR_INVALID_ARG, "engine %d not available", engine);
+    }
+    if (rc) return rc;
+
+    const float T = (float)std::log2((double)k);
+    float* a_dst = want_union ? static_cast<float*>(h->a.p) : out_w;
+    CK(launch_smooth_knn(out_dist, n_src, k, T, static_cast<float*>(h->rho.p), static_cast<float*>(h->sigma.p), a_dst, st),
+       "smooth_knn");
+    h->kernel_launches++;
+    if (want_union) {
+        const long long cnt = 2ll * n_src * k;
+        if ((rc = ensure(h->keys, cnt * 8, "coo keys")) || (rc = ensure(h->vals, cnt * 4, "coo vals")) ||
+            (rc = ensure(h->keys_tmp, cnt * 8, "coo keys tmp")) || (rc = ensure(h->vals_tmp, cnt * 4, "coo vals tmp")) ||
+            (rc = ensure(h->sort_temp, radix_sort_temp_bytes(cnt), "sort temp")))
+            return rc;
+        const int B = key_bits_for(h->n);
+        CK(cudaMemsetAsync(&h->d_ctr->coo_nnz, 0, sizeof(unsigned long long), st), "memset nnz");
+        CK(launch_union(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, B,
+                        static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), h->d_ctr, st),
+           "union");
+        h->kernel_launches++;
+        int launches = 0;
+        CK(radix_sort_pairs(static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
+                            static_cast<unsigned long long*>(h->keys_tmp.p), static_cast<float*>(h->vals_tmp.p), cnt,
+                            2 * B, h->sort_temp.p, h->sort_temp.bytes, st, &h->coo_keys, &h->coo_vals, &launches),
+           "radix sort");
+        h->kernel_launches += launches;
+        h->coo_key_bits = B;
+        h->last_union = true;
+    }
+    return GUMAP_OK;
+}
+
+int gumap_knn_rho_sigma(gumap_knn* h, float* rho, float* sigma, void* stream) {
+    if (!h || h->last_n_src < 0) return fail(GUMAP_ERR_INVALID_ARG, "no run yet");
+    if (h->last_n_src == 0) return GUMAP_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    if (rho) CK(cudaMemcpyAsync(rho, h->rho.p, (size_t)h->last_n_src * 4, cudaMemcpyDeviceToDevice, st), "copy rho");
+    if (sigma) CK(cudaMemcpyAsync(sigma, h->sigma.p, (size_t)h->last_n_src * 4, cudaMemcpyDeviceToDevice, st), "copy sigma");
+    return GUMAP_OK;
+}
+
+int gumap_knn_coo(gumap_knn* h, int32_t* row, int32_t* col, float* w, int64_t* nnz, void* stream) {
+    if (!h || !h->last_union) return fail(GUMAP_ERR_INVALID_ARG, "last run built no union COO");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    const long long cap = 2ll * h->last_n_src * h->k;
+    CK(launch_coo_unpack(h->coo_keys, h->coo_vals, h->coo_key_bits, h->d_ctr, cap, row, col, w, nnz,
+                         static_cast<cudaStream_t>(stream)),
+       "coo unpack");
+    h->kernel_launches++;
+    return GUMAP_OK;
+}
+
+int gumap_knn_check(gumap_knn* h, void* stream) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)), "stream sync");
+    int32_t st = 0;
+    CK(cudaMemcpy(&st, &h->d_ctr->status, sizeof(int32_t), cudaMemcpyDeviceToHost), "read status");
+    if (st != 0) {
+        CK(cudaMemset(&h->d_ctr->status, 0, sizeof(int32_t)), "clear status");
+        return fail(st, "device reported %s", gumap_status_string(st));
+    }
+    return GUMAP_OK;
+}
+
+int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    switch (option) {
+        case GUMAP_OPT_ENGINE:
+            if (value < GUMAP_ENGINE_AUTO || value > GUMAP_ENGINE_FRONTIER) return fail(GUMAP_ERR_INVALID_ARG, "bad engine");
+            if (value == GUMAP_ENGINE_FRONTIER && h->mode != GUMAP_PARTIAL)
+                return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
+            h->opt_engine = (int)value;
+            return GUMAP_OK;
+        case GUMAP_OPT_BLOCK_BITS:
+            if (value < 0 || value % 128 != 0 || value > (1 << 20)) return fail(GUMAP_ERR_INVALID_ARG, "block bits must be a multiple of 128");
+            h->opt_block_bits = value;
+            return GUMAP_OK;
+        case GUMAP_OPT_PROFILE:
+            h->opt_profile = value ? 1 : 0;
+            return GUMAP_OK;
+        case GUMAP_OPT_STATE_BYTES:
+            if (value < 0) return fail(GUMAP_ERR_INVALID_ARG, "negative budget");
+            h->opt_state_bytes = value;
+            return GUMAP_OK;
+        default:
+            return fail(GUMAP_ERR_INVALID_ARG, "unknown option %d", option);
+    }
+}
+
+int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
+    if (!h || !out) return fail(GUMAP_ERR_INVALID_ARG, "NULL argument");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaDeviceSynchronize(), "sync");
+    DeviceCounters c;
+    CK(cudaMemcpy(&c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) == cudaSuccess) h->bfs_ms_done += ms;
+    }
+    h->ev_used = 0;
+    memset(out, 0, sizeof(*out));
+    out->engine = h->last_engine;
+    out->block_bits = h->last_block_bits;
+    out->n_blocks = h->last_blocks;
+    out->levels_max = c.levels_max;
+    out->bfs_launches = h->bfs_launches;
+    out->bfs_ms = h->bfs_ms_done;
+    out->bfs_level_sum = c.level_sum;
+    out->kernel_launches = h->kernel_launches;
+    out->device_bytes = (int64_t)held_bytes(h);
+    return GUMAP_OK;
+}
+
+int gumap_knn_reset_stats(gumap_knn* h) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    CK(cudaDeviceSynchronize(), "sync");
+    h->bfs_launches = 0;
+    h->kernel_launches = 0;
+    h->bfs_ms_done = 0.0;
+    h->ev_used = 0;
+    DeviceCounters c;
+    CK(cudaMemcpy(&c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    c.levels_max = 0;
+    c.level_sum = 0;
+    CK(cudaMemcpy(h->d_ctr, &c, sizeof(c), cudaMemcpyHostToDevice), "write counters");
+    return GUMAP_OK;
+}
+
+}  // extern "C"

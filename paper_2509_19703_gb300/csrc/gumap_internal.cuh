@@ -1,0 +1,102 @@
+// Internal declarations shared by the CUDA translation units of libgumap.
+// Nothing here is part of the public ABI (include/gumap.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gumap {
+
+constexpr uint16_t kDistInf = 0xFFFFu;
+constexpr int kMaxK = 256;
+// A device-side wait that has not finished after this long gives up and
+// reports GUMAP_ERR_TIMEOUT instead of hanging the GPU.
+constexpr unsigned long long kWaitLimitNs = 10ull * 1000ull * 1000ull * 1000ull;
+
+// Status values written by kernels into DeviceCounters::status.
+constexpr int kStatusTimeout = 7;     // == GUMAP_ERR_TIMEOUT
+constexpr int kStatusBadSource = 1;   // == GUMAP_ERR_INVALID_ARG (a source id outside [0, n))
+
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+// Small per-handle block of device counters; zeroed at handle creation.
+struct DeviceCounters {
+    GridBarrier bar;
+    int32_t status;
+    int32_t n_need;            // sources of the running block whose list is incomplete
+    uint32_t lvl_any[3];       // "some vertex was reached at level d" in slot d % 3
+    int32_t levels;            // deepest level reached by the last MS-BFS launch
+    int32_t levels_max;        // max over launches since the last host reset
+    int32_t pad0;
+    long long level_sum;       // sum of levels over launches since the last host reset
+    unsigned long long coo_nnz;
+};
+
+// Arguments of one multi-source BFS launch over a block of sources.
+struct MsbfsArgs {
+    const int32_t* row_ptr;  // CSR (device, read-only during the launch)
+    const int32_t* col;
+    int32_t n;
+    const int32_t* src;      // block's sources: vertex of bit j is src[j]
+    int32_t nb;              // sources in the block (<= 32 * W)
+    int32_t W;               // 32-bit words per vertex row, multiple of 4
+    uint32_t* F;             // frontier  [n][W]
+    uint32_t* N;             // next      [n][W]
+    uint32_t* V;             // visited   [n][W]
+    uint32_t* act;           // [W] bit j: source j still propagates
+    uint32_t* need;          // [W] bit j: list of source j still incomplete
+    int32_t* cnt;            // [nb] entries found so far
+    int32_t* out_idx;        // [nb][k] rows of this block
+    uint16_t* out_dist;      // [nb][k]
+    int32_t k;
+    int32_t partial;         // 1: stop each source once its list is complete
+    DeviceCounters* ctr;
+};
+
+// Arguments of one partial-BFS launch with one warp per source.
+struct FrontierArgs {
+    const int32_t* row_ptr;
+    const int32_t* col;
+    int32_t n;
+    const int32_t* src;      // NULL = identity
+    int32_t n_src;
+    int32_t k;
+    int32_t* out_idx;
+    uint16_t* out_dist;
+    int32_t* status;         // set to kStatusBadSource for a source outside [0, n)
+};
+
+// ---- msbfs.cu
+int msbfs_max_blocks_per_sm(int block_threads);
+cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);
+cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s);
+
+// ---- frontier.cu
+cudaError_t launch_frontier(const FrontierArgs& a, cudaStream_t s);
+
+// ---- weights.cu
+cudaError_t launch_smooth_knn(const uint16_t* dist, int32_t n_rows, int32_t k, float T, float* rho,
+                              float* sigma, float* a, cudaStream_t s);
+// Union weights into w; when keys != NULL also the 2 * n * k COO (key, value)
+// pairs, counting the valid keys into ctr->coo_nnz.
+cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k, float* w,
+                         int key_bits, unsigned long long* keys, float* vals, DeviceCounters* ctr, cudaStream_t s);
+cudaError_t launch_coo_unpack(const unsigned long long* keys, const float* vals, int key_bits,
+                              const DeviceCounters* ctr, long long cap, int32_t* row, int32_t* col, float* w,
+                              int64_t* nnz_out, cudaStream_t s);
+
+// ---- sort.cu: LSD radix sort of (u64 key, float value) on the low `bits` key bits.
+size_t radix_sort_temp_bytes(long long count);
+cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned long long* keys_tmp,
+                             float* vals_tmp, long long count, int bits, void* temp, size_t temp_bytes,
+                             cudaStream_t s, unsigned long long** keys_out, float** vals_out, int* launches);
+
+// ---- validate.cu
+// Device-side CSR validation; writes 0 to *bad if the graph is valid.
+cudaError_t launch_validate_csr(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz,
+                                int32_t* bad, cudaStream_t s);
+
+}  // namespace gumap

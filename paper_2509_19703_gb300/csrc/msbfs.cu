@@ -1,0 +1,348 @@
+// Bit-parallel multi-source BFS (MS-BFS) with kNN extraction.
+//
+// One launch processes one block of up to 32*W sources. Each vertex row of
+// the three bitsets holds one bit per source (vertex-major, W 32-bit words,
+// W a multiple of 4 so a thread moves 128 bits with one uint4 access):
+//   F[v]  frontier: sources that reached v at the previous level
+//   N[v]  next:     sources that reach v at the current level
+//   V[v]  visited:  sources that reached v before the previous level
+// A level is the pull step  N[v] = (OR_{u in adj(v)} F[u]) & act & ~(V[v] | F[v]),
+// which is the frontier expansion of Algorithm 4 (tovisit -> newvisit) and of
+// the BFS inside AllPairsShortestPath (Algorithm 1) run for 32*W sources at
+// once. The OR over neighbours stops as soon as every still-missing source
+// bit is covered (the bottom-up early exit), and a vertex already reached by
+// every active source costs no neighbour loads at all.
+//
+// Level 1 is a push from the sources (their adjacency rows), and its kNN
+// entries are the first k entries of each source's sorted CSR row.
+// For later levels the extraction phase scans each word column of N in
+// vertex order, transposes 32x32 bit tiles with warp ballots, and appends
+// to every incomplete source the vertices it reached at this level in
+// ascending id until its list holds k entries: this is exactly the
+// (distance, id) order, because levels are visited in increasing distance
+// and vertices in increasing id. In the partial form (Algorithm 4,
+// "break if visited.size > k") a source whose list is complete stops
+// propagating: its bit leaves `act`. The full form keeps every source
+// propagating until no source reaches a new vertex.
+//
+// All levels run inside one cooperative launch; phases are separated by a
+// grid barrier whose waits are bounded in time (kWaitLimitNs).
+#include "gumap_internal.cuh"
+
+namespace gumap {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int32_t* p) {
+    return *reinterpret_cast<const volatile int32_t*>(p);
+}
+
+__device__ __forceinline__ unsigned ld_volatile_u32(const uint32_t* p) {
+    return *reinterpret_cast<const volatile uint32_t*>(p);
+}
+
+// Grid-wide barrier for a cooperative launch. Thread 0 of each CTA arrives
+// on a counter; the last arrival bumps the generation. Waiters poll the
+// generation for at most kWaitLimitNs, then record a timeout and return
+// false (every later barrier of that CTA is skipped by the caller).
+__device__ bool grid_barrier(GridBarrier* bar, int32_t* status) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned nblocks = gridDim.x;
+        unsigned gen0 = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        unsigned prev = atomicAdd(&bar->count, 1u);
+        if (prev == nblocks - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire_u32(&bar->gen) == gen0) {
+                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                    atomicExch(status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ uint4 or4(uint4 a, uint4 b) {
+    return make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w);
+}
+__device__ __forceinline__ uint4 and4(uint4 a, uint4 b) {
+    return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
+__device__ __forceinline__ uint4 andnot4(uint4 a, uint4 b) {  // a & ~b
+    return make_uint4(a.x & ~b.x, a.y & ~b.y, a.z & ~b.z, a.w & ~b.w);
+}
+__device__ __forceinline__ bool nz4(uint4 a) { return (a.x | a.y | a.z | a.w) != 0u; }
+// true when every bit of `todo` is present in `acc`
+__device__ __forceinline__ bool covers4(uint4 acc, uint4 todo) { return !nz4(andnot4(todo, acc)); }
+
+__device__ __forceinline__ uint4 ldcg4(const uint4* p) { return __ldcg(p); }
+
+// ---------------------------------------------------------------- phases
+
+// Phase 0: clear V and N, prefill the block's output rows with padding,
+// mark valid source bits in act/need.
+__device__ void phase_init(const MsbfsArgs& a) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const long long words4 = (long long)a.n * (a.W >> 2);
+    uint4* V4 = reinterpret_cast<uint4*>(a.V);
+    uint4* N4 = reinterpret_cast<uint4*>(a.N);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    for (long long i = tid; i < words4; i += nthr) {
+        V4[i] = z;
+        N4[i] = z;
+    }
+    for (long long i = tid; i < a.W; i += nthr) {
+        long long lo = i * 32;
+        uint32_t m;
+        if (lo + 32 <= a.nb) m = kFull;
+        else if (lo >= a.nb) m = 0u;
+        else m = (1u << (a.nb - lo)) - 1u;
+        a.act[i] = m;
+        a.need[i] = m;
+    }
+    const long long slots = (long long)a.nb * a.k;
+    for (long long i = tid; i < slots; i += nthr) {
+        a.out_idx[i] = -1;
+        a.out_dist[i] = kDistInf;
+    }
+    for (long long i = tid; i < a.nb; i += nthr) a.cnt[i] = 0;
+    if (tid == 0) {
+        a.ctr->n_need = a.nb;
+        a.ctr->lvl_any[0] = 0u;
+        a.ctr->lvl_any[1] = 0u;
+        a.ctr->lvl_any[2] = 0u;
+    }
+}
+
+// Phase 1: seed V with the sources (level 0), push level 1 into N, and take
+// the level-1 kNN entries straight from each source's sorted CSR row.
+__device__ void phase_seed(const MsbfsArgs& a) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    for (long long j = tid; j < a.nb; j += nthr) {
+        const int s = a.src[j];
+        if (s >= 0 && s < a.n) atomicOr(&a.V[(size_t)s * a.W + (j >> 5)], 1u << (j & 31));
+    }
+    const int lane = threadIdx.x & 31;
+    const long long warp = tid >> 5;
+    const long long nwarps = nthr >> 5;
+    int any = 0;
+    for (long long j = warp; j < a.nb; j += nwarps) {
+        const int s = a.src[j];
+        const bool ok = s >= 0 && s < a.n;  // an invalid source is an empty row
+        if (!ok && lane == 0) atomicExch(&a.ctr->status, kStatusBadSource);
+        const int e0 = ok ? __ldg(a.row_ptr + s) : 0, e1 = ok ? __ldg(a.row_ptr + s + 1) : 0;
+        const int deg = e1 - e0;
+        const uint32_t bit = 1u << (j & 31);
+        uint32_t* Ncol = a.N + (j >> 5);
+        for (int e = e0 + lane; e < e1; e += 32) {
+            int u = __ldg(a.col + e);
+            atomicOr(Ncol + (size_t)u * a.W, bit);
+        }
+        const int take = deg < a.k ? deg : a.k;
+        int32_t* oi = a.out_idx + (size_t)j * a.k;
+        uint16_t* od = a.out_dist + (size_t)j * a.k;
+        for (int t = lane; t < take; t += 32) {
+            oi[t] = __ldg(a.col + e0 + t);
+            od[t] = 1;
+        }
+        if (lane == 0) {
+            a.cnt[j] = take;
+            if (deg > 0) any = 1;
+            if (take >= a.k || deg == 0) {
+                atomicAnd(&a.need[j >> 5], ~bit);
+                if (a.partial || deg == 0) atomicAnd(&a.act[j >> 5], ~bit);
+                atomicSub(&a.ctr->n_need, 1);
+            }
+        }
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[1], 1u);
+}
+
+// Pull step of level d (see file comment). Returns nothing; sets lvl_any.
+__device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
+                           int slot) {
+    const int G = a.W >> 2;
+    const long long total = (long long)a.n * G;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
+    uint4* N4 = reinterpret_cast<uint4*>(Nc);
+    uint4* V4 = reinterpret_cast<uint4*>(a.V);
+    const uint4* act4 = reinterpret_cast<const uint4*>(a.act);
+    int any = 0;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += nthr) {
+        const int v = (int)(t / G);
+        const int g = (int)(t - (long long)v * G);
+        const size_t off = (size_t)v * G + g;
+        const uint4 vis = or4(ldcg4(V4 + off), ldcg4(F4 + off));
+        const uint4 todo = andnot4(ldcg4(act4 + g), vis);
+        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+        if (nz4(todo)) {
+            const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+            int e = e0;
+            // two neighbours per iteration: both loads in flight before the test
+            for (; e + 1 < e1; e += 2) {
+                const int u0 = __ldg(a.col + e), u1 = __ldg(a.col + e + 1);
+                const uint4 f0 = ldcg4(F4 + (size_t)u0 * G + g);
+                const uint4 f1 = ldcg4(F4 + (size_t)u1 * G + g);
+                acc = or4(acc, or4(f0, f1));
+                if (covers4(acc, todo)) break;
+            }
+            if (e + 1 == e1) {
+                const int u0 = __ldg(a.col + e);
+                acc = or4(acc, ldcg4(F4 + (size_t)u0 * G + g));
+            }
+            acc = and4(acc, todo);
+        }
+        N4[off] = acc;
+        V4[off] = vis;
+        any |= nz4(acc) ? 1 : 0;
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
+}
+
+// Extraction of level d: one warp per 32-source word column with incomplete
+// sources. Lane b owns source 32*w + b.
+__device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
+    const int lane = threadIdx.x & 31;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int Wv = (a.nb + 31) >> 5;
+    for (long long w = warp; w < Wv; w += nwarps) {
+        const uint32_t need0 = ld_volatile_u32(a.need + w);
+        if (need0 == 0u) continue;
+        const long long j = w * 32 + lane;
+        const bool mine_need = (need0 >> lane) & 1u;
+        int c = mine_need ? __ldcg(a.cnt + j) : a.k;
+        bool found = false;
+        uint32_t needw = need0;
+        int32_t* oi = a.out_idx + (size_t)j * a.k;
+        uint16_t* od = a.out_dist + (size_t)j * a.k;
+        for (int v0 = 0; v0 < a.n; v0 += 32) {
+            const int v = v0 + lane;
+            uint32_t x = (v < a.n) ? __ldcg(Nc + (size_t)v * a.W + w) : 0u;
+            x &= needw;
+            if (__ballot_sync(kFull, x != 0u) == 0u) continue;
+            uint32_t mine = 0u;
+#pragma unroll
+            for (int b = 0; b < 32; ++b) {
+                const uint32_t t = __ballot_sync(kFull, (x >> b) & 1u);
+                if (lane == b) mine = t;
+            }
+            if (mine) found = true;
+            while (mine && c < a.k) {
+                const int i = __ffs(mine) - 1;
+                mine &= mine - 1u;
+                oi[c] = v0 + i;
+                od[c] = (uint16_t)d;
+                ++c;
+            }
+            needw = __ballot_sync(kFull, mine_need && c < a.k);
+            if (needw == 0u) break;
+        }
+        // a source is finished when its list is full or its BFS ran dry
+        const bool done = mine_need && (c >= a.k || !found);
+        const uint32_t done_mask = __ballot_sync(kFull, done);
+        if (mine_need) a.cnt[j] = c;
+        if (lane == 0 && done_mask) {
+            a.need[w] = need0 & ~done_mask;
+            // partial form: a finished source stops propagating
+            if (a.partial) a.act[w] = __ldcg(a.act + w) & ~done_mask;
+            atomicSub(&a.ctr->n_need, __popc(done_mask));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
+    phase_init(a);
+    if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+    phase_seed(a);
+    if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+
+    uint32_t* Fc = a.N;  // level-1 frontier was pushed into N
+    uint32_t* Nc = a.F;
+    int last = 1;
+    bool go = ld_volatile_u32(&a.ctr->lvl_any[1]) != 0u;
+    if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) go = false;
+    for (int d = 2; go && d <= a.n; ++d) {
+        const int need_now = ld_volatile_i32(&a.ctr->n_need);
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr->lvl_any[(d + 1) % 3] = 0u;
+        phase_pull(a, Fc, Nc, d % 3);
+        if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+        if (ld_volatile_u32(&a.ctr->lvl_any[d % 3]) == 0u) break;
+        last = d;
+        if (need_now > 0) {
+            phase_extract(a, Nc, d);
+            if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+            if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) break;
+        }
+        uint32_t* t = Fc;
+        Fc = Nc;
+        Nc = t;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctr->levels = last;
+        a.ctr->level_sum += last;
+        if (last > a.ctr->levels_max) a.ctr->levels_max = last;
+    }
+}
+
+__global__ void identity_kernel(int32_t* dst, int32_t n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (int32_t)i;
+}
+
+}  // namespace
+
+int msbfs_max_blocks_per_sm(int block_threads) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, msbfs_kernel, block_threads, 0) != cudaSuccess)
+        return 0;
+    return nb;
+}
+
+cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s) {
+    MsbfsArgs copy = a;
+    void* params[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void*)msbfs_kernel, dim3(grid), dim3(block), params, 0, s);
+}
+
+cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    identity_kernel<<<grid, 256, 0, s>>>(dst, n);
+    return cudaGetLastError();
+}
+
+}  // namespace gumap

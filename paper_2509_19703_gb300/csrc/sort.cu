@@ -1,0 +1,153 @@
+// LSD radix sort of (uint64 key, float value) pairs on the low `bits` key
+// bits, 8 bits per pass. Used to order the fuzzy-union COO by (row, col):
+// the key of entry (i, j) is (i << B) | j with B = ceil(log2 n).
+//
+// Each pass: (1) a tile histogram of the digit (256 bins per 4096-key tile,
+// stored digit-major), (2) one exclusive scan over that table, giving every
+// (digit, tile) its output start, (3) a stable scatter: inside a tile the
+// keys are ranked in input order with warp match/ballot ranks plus per-warp
+// digit counts in shared memory.
+#include "gumap_internal.cuh"
+
+namespace gumap {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+__global__ void __launch_bounds__(kThreads) hist_kernel(const unsigned long long* __restrict__ keys,
+                                                        long long count, int shift, int num_tiles,
+                                                        unsigned int* __restrict__ hist) {
+    __shared__ unsigned int h[256];
+    const int tid = threadIdx.x;
+    h[tid] = 0u;
+    __syncthreads();
+    const long long base = (long long)blockIdx.x * kTile;
+#pragma unroll 4
+    for (int c = 0; c < kItems; ++c) {
+        const long long i = base + c * kThreads + tid;
+        if (i < count) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 0xFFu], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)tid * num_tiles + blockIdx.x] = h[tid];
+}
+
+// Exclusive scan of `len` counts in place with one CTA of 1024 threads:
+// each thread sums a contiguous chunk, the CTA scans the chunk sums, then
+// each thread rewrites its chunk.
+__global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ data, long long len) {
+    __shared__ unsigned int part[1024];
+    const int tid = threadIdx.x;
+    const long long chunk = (len + 1023) / 1024;
+    const long long b = tid * chunk;
+    const long long e = (b + chunk < len) ? b + chunk : len;
+    unsigned int s = 0u;
+    for (long long i = b; i < e; ++i) s += data[i];
+    part[tid] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned int v = tid >= o ? part[tid - o] : 0u;
+        __syncthreads();
+        part[tid] += v;
+        __syncthreads();
+    }
+    unsigned int run = part[tid] - s;  // exclusive prefix of this chunk
+    for (long long i = b; i < e; ++i) {
+        const unsigned int x = data[i];
+        data[i] = run;
+        run += x;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) scatter_kernel(const unsigned long long* __restrict__ kin,
+                                                           const float* __restrict__ vin,
+                                                           unsigned long long* __restrict__ kout,
+                                                           float* __restrict__ vout, long long count, int shift,
+                                                           int num_tiles, const unsigned int* __restrict__ offs) {
+    __shared__ unsigned int run[256];
+    __shared__ unsigned int wcnt[kWarps][256];
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    run[tid] = offs[(size_t)tid * num_tiles + blockIdx.x];
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0u;
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    const long long base = (long long)blockIdx.x * kTile;
+    for (int c = 0; c < kItems; ++c) {
+        const long long i = base + c * kThreads + tid;
+        const bool valid = i < count;
+        unsigned long long key = 0ull;
+        float val = 0.0f;
+        int d = 256;  // invalid lanes form their own group
+        if (valid) {
+            key = kin[i];
+            val = vin[i];
+            d = (int)((key >> shift) & 0xFFull);
+        }
+        const unsigned peers = __match_any_sync(kFull, d);
+        const unsigned rank = __popc(peers & lt);
+        if (valid && rank == 0u) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            unsigned int pos = run[d] + rank;
+            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        unsigned int tot = 0u;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            tot += wcnt[w][tid];
+            wcnt[w][tid] = 0u;
+        }
+        run[tid] += tot;
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t radix_sort_temp_bytes(long long count) {
+    const long long tiles = (count + kTile - 1) / kTile;
+    return (size_t)(256 * (tiles > 0 ? tiles : 1)) * sizeof(unsigned int);
+}
+
+cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned long long* keys_tmp, float* vals_tmp,
+                             long long count, int bits, void* temp, size_t temp_bytes, cudaStream_t s,
+                             unsigned long long** keys_out, float** vals_out, int* launches) {
+    *keys_out = keys;
+    *vals_out = vals;
+    if (count <= 1 || bits <= 0) return cudaSuccess;
+    if (count > 0xFFFFFFFFll) return cudaErrorInvalidValue;  // 32-bit output offsets
+    const long long tiles = (count + kTile - 1) / kTile;
+    if (temp_bytes < radix_sort_temp_bytes(count)) return cudaErrorInvalidValue;
+    unsigned int* hist = static_cast<unsigned int*>(temp);
+    unsigned long long *ka = keys, *kb = keys_tmp;
+    float *va = vals, *vb = vals_tmp;
+    for (int shift = 0; shift < bits; shift += 8) {
+        hist_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, count, shift, (int)tiles, hist);
+        scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * tiles);
+        scatter_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, va, kb, vb, count, shift, (int)tiles, hist);
+        if (launches) *launches += 3;
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        unsigned long long* tk = ka;
+        ka = kb;
+        kb = tk;
+        float* tv = va;
+        va = vb;
+        vb = tv;
+    }
+    *keys_out = ka;
+    *vals_out = va;
+    return cudaSuccess;
+}
+
+}  // namespace gumap

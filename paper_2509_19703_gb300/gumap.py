@@ -1,0 +1,269 @@
+"""Thin ctypes binding of libgumap (include/gumap.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. PyTorch supplies device memory (tensors) and streams. There is no
+CPU fallback: if ``libgumap.so`` is missing, loading fails with an error.
+
+The functions keep the C names (gumap_knn_create, gumap_knn_run, ...);
+``KnnGraph`` is a small convenience wrapper that allocates output tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+from . import _build
+
+# modes, flags, engines, options (mirror include/gumap.h)
+FULL, PARTIAL = 0, 1
+WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE = 0x0, 0x1, 0x2
+ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER = 0, 1, 2, 3
+OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES = 1, 2, 3, 4
+MAX_K = 256
+DIST_INF = 0xFFFF
+
+OK = 0
+ERR_INVALID_ARG, ERR_INVALID_GRAPH, ERR_OOM, ERR_CUDA = 1, 2, 3, 4
+ERR_AGAIN, PENDING, ERR_TIMEOUT, ERR_TOO_LARGE, ERR_UNKNOWN_REQUEST = 5, 6, 7, 8, 9
+
+_lock = threading.Lock()
+_lib = None
+
+
+class GumapError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(msg)
+        self.status = status
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("engine", ctypes.c_int32), ("block_bits", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
+                ("levels_max", ctypes.c_int32), ("bfs_launches", ctypes.c_int64), ("bfs_ms", ctypes.c_double),
+                ("bfs_level_sum", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libgumap.so (built by ``__graft_entry__.build()``); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libgumap.so not built at {path}: run __graft_entry__.build() "
+                                   "(there is no CPU fallback)")
+            lib = ctypes.CDLL(path)
+            vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+            sig = {
+                "gumap_knn_create": [ctypes.POINTER(vp), vp, vp, i32, i64, i32, ctypes.c_int, u32, ctypes.c_int],
+                "gumap_knn_run": [vp, vp, i32, vp, vp, vp, vp],
+                "gumap_knn_rho_sigma": [vp, vp, vp, vp],
+                "gumap_knn_coo": [vp, vp, vp, vp, vp, vp],
+                "gumap_knn_check": [vp, vp],
+                "gumap_knn_set_option": [vp, ctypes.c_int, i64],
+                "gumap_knn_get_stats": [vp, ctypes.POINTER(_Stats)],
+                "gumap_knn_reset_stats": [vp],
+                "gumap_knn_destroy": [vp],
+            }
+            for name, args in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = ctypes.c_int
+            lib.gumap_status_string.argtypes = [ctypes.c_int]
+            lib.gumap_status_string.restype = ctypes.c_char_p
+            lib.gumap_last_error.argtypes = []
+            lib.gumap_last_error.restype = ctypes.c_char_p
+            _lib = lib
+    return _lib
+
+
+def gumap_status_string(status: int) -> str:
+    return load().gumap_status_string(status).decode()
+
+
+def gumap_last_error() -> str:
+    return load().gumap_last_error().decode()
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise GumapError(rc, f"{what}: {gumap_status_string(rc)}: {gumap_last_error()}")
+
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---------------------------------------------------------------- C names
+
+def gumap_knn_create(row_ptr, col_idx, n: int, nnz: int, k: int, mode: int = FULL, flags: int = 0,
+                     device: int = 0):
+    """Returns an opaque handle. row_ptr/col_idx: host numpy int32 arrays, or
+    CUDA int32 tensors together with CSR_ON_DEVICE in flags."""
+    lib = load()
+    keep = []
+    if flags & CSR_ON_DEVICE:
+        rp, col = _dptr(row_ptr, torch.int32, "row_ptr"), _dptr(col_idx, torch.int32, "col_idx")
+    else:
+        rp_a = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col_a = np.ascontiguousarray(col_idx, dtype=np.int32)
+        keep += [rp_a, col_a]
+        rp, col = rp_a.ctypes.data, (col_a.ctypes.data if col_a.size else None)
+    h = ctypes.c_void_p()
+    _check(lib.gumap_knn_create(ctypes.byref(h), rp, col, int(n), int(nnz), int(k), int(mode), int(flags),
+                                int(device)), "gumap_knn_create")
+    return h
+
+
+def gumap_knn_run(h, sources, n_src: int, out_idx, out_dist, out_w, stream=None):
+    """sources: CUDA int32 tensor or None (all vertices); outputs: CUDA tensors
+    int32 / int16 (uint16 bit pattern) / float32 of shape [n_src, k]."""
+    _check(load().gumap_knn_run(h, _dptr(sources, torch.int32, "sources"), int(n_src),
+                                _dptr(out_idx, torch.int32, "out_idx"), _dptr(out_dist, torch.int16, "out_dist"),
+                                _dptr(out_w, torch.float32, "out_w"), _stream(stream)), "gumap_knn_run")
+
+
+def gumap_knn_rho_sigma(h, rho, sigma, stream=None):
+    _check(load().gumap_knn_rho_sigma(h, _dptr(rho, torch.float32, "rho"), _dptr(sigma, torch.float32, "sigma"),
+                                      _stream(stream)), "gumap_knn_rho_sigma")
+
+
+def gumap_knn_coo(h, row, col, w, nnz, stream=None):
+    _check(load().gumap_knn_coo(h, _dptr(row, torch.int32, "row"), _dptr(col, torch.int32, "col"),
+                                _dptr(w, torch.float32, "w"), _dptr(nnz, torch.int64, "nnz"), _stream(stream)),
+           "gumap_knn_coo")
+
+
+def gumap_knn_check(h, stream=None):
+    _check(load().gumap_knn_check(h, _stream(stream)), "gumap_knn_check")
+
+
+def gumap_knn_set_option(h, option: int, value: int):
+    _check(load().gumap_knn_set_option(h, int(option), int(value)), "gumap_knn_set_option")
+
+
+def gumap_knn_get_stats(h) -> dict:
+    s = _Stats()
+    _check(load().gumap_knn_get_stats(h, ctypes.byref(s)), "gumap_knn_get_stats")
+    return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def gumap_knn_reset_stats(h):
+    _check(load().gumap_knn_reset_stats(h), "gumap_knn_reset_stats")
+
+
+def gumap_knn_destroy(h):
+    _check(load().gumap_knn_destroy(h), "gumap_knn_destroy")
+
+
+# ---------------------------------------------------------------- wrapper
+
+class KnnGraph:
+    """A graph resident on the GPU plus the kNN/weight computation.
+
+    >>> g = KnnGraph(row_ptr, col, k=15, mode=FULL)
+    >>> out = g.run()            # dict of CUDA tensors idx / dist / w
+    >>> row, col, w = g.coo()
+    """
+
+    def __init__(self, row_ptr, col_idx, k: int, mode: int = FULL, flags: int = 0, device: int = 0,
+                 n: int | None = None):
+        if n is None:
+            n = int(row_ptr.shape[0]) - 1
+        nnz = int(col_idx.shape[0])
+        self.n, self.k, self.mode, self.flags, self.device = n, k, mode, flags, device
+        self.h = gumap_knn_create(row_ptr, col_idx, n, nnz, k, mode, flags, device)
+
+    @classmethod
+    def from_graph(cls, g, k: int, mode: int = FULL, flags: int = 0, device: int = 0):
+        return cls(g.row_ptr, g.col, k, mode, flags, device, n=g.n)
+
+    def set_option(self, option: int, value: int):
+        gumap_knn_set_option(self.h, option, value)
+
+    def alloc_outputs(self, n_src: int):
+        dev = torch.device("cuda", self.device)
+        return dict(idx=torch.empty((n_src, self.k), dtype=torch.int32, device=dev),
+                    dist=torch.empty((n_src, self.k), dtype=torch.int16, device=dev),
+                    w=torch.empty((n_src, self.k), dtype=torch.float32, device=dev))
+
+    def run(self, sources=None, stream=None, out=None) -> dict:
+        n_src = self.n if sources is None else int(sources.shape[0])
+        out = out or self.alloc_outputs(n_src)
+        gumap_knn_run(self.h, sources, n_src, out["idx"], out["dist"], out["w"], stream)
+        return out
+
+    def rho_sigma(self, n_src: int | None = None, stream=None):
+        n_src = self.n if n_src is None else n_src
+        dev = torch.device("cuda", self.device)
+        rho = torch.empty(n_src, dtype=torch.float32, device=dev)
+        sigma = torch.empty(n_src, dtype=torch.float32, device=dev)
+        gumap_knn_rho_sigma(self.h, rho, sigma, stream)
+        return rho, sigma
+
+    def coo(self, stream=None):
+        dev = torch.device("cuda", self.device)
+        cap = 2 * self.n * self.k
+        row = torch.empty(cap, dtype=torch.int32, device=dev)
+        col = torch.empty(cap, dtype=torch.int32, device=dev)
+        w = torch.empty(cap, dtype=torch.float32, device=dev)
+        nnz = torch.zeros(1, dtype=torch.int64, device=dev)
+        gumap_knn_coo(self.h, row, col, w, nnz, stream)
+        m = int(nnz.item())
+        return row[:m], col[:m], w[:m]
+
+    def check(self, stream=None):
+        gumap_knn_check(self.h, stream)
+
+    def stats(self) -> dict:
+        return gumap_knn_get_stats(self.h)
+
+    def reset_stats(self):
+        gumap_knn_reset_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            gumap_knn_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dist_u16(t: torch.Tensor) -> np.ndarray:
+    """Host uint16 view of a distance tensor stored as int16."""
+    return t.cpu().numpy().view(np.uint16)

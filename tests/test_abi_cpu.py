@@ -1,0 +1,72 @@
+"""The C-ABI library builds, loads without a GPU and exports every symbol
+that include/*.h declares. No compute call is made here."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2509_19703_gb300 import _build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[\w\s\*]+?\b(gumap_\w+)\s*\(", text, flags=re.M):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return _build.build()
+
+
+def test_header_declares_entry_points():
+    names = declared_symbols()
+    for must in ("gumap_knn_create", "gumap_knn_run", "gumap_knn_destroy", "gumap_status_string"):
+        assert must in names, names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (gumap_\w+)", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, f"declared but not exported: {missing}"
+
+
+def test_library_loads_and_answers_host_only_calls(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    lib.gumap_status_string.restype = ctypes.c_char_p
+    assert lib.gumap_status_string(0) == b"GUMAP_OK"
+    assert lib.gumap_status_string(7) == b"GUMAP_ERR_TIMEOUT"
+    lib.gumap_last_error.restype = ctypes.c_char_p
+    assert isinstance(lib.gumap_last_error(), bytes)
+
+
+def test_binding_argument_checks_without_gpu(lib_path):
+    """Invalid arguments are rejected on the host before any device work."""
+    from paper_2509_19703_gb300 import gumap
+    import numpy as np
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    col = np.array([1, 0], dtype=np.int32)
+    with pytest.raises(gumap.GumapError) as e:
+        gumap.gumap_knn_create(rp, col, 2, 2, k=5)  # k > n - 1
+    assert e.value.status == gumap.ERR_INVALID_ARG
+    with pytest.raises(gumap.GumapError) as e:
+        gumap.gumap_knn_create(rp, col, 2, 2, k=1, mode=7)
+    assert e.value.status == gumap.ERR_INVALID_ARG
+
+
+def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
+    from paper_2509_19703_gb300 import gumap
+    monkeypatch.setattr(gumap, "_lib", None)
+    monkeypatch.setattr(gumap._build, "LIB", str(tmp_path / "absent.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        gumap.load()
