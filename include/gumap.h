@@ -178,6 +178,9 @@ typedef struct {
     int64_t bfs_level_sum;   /* sum over launches of the BFS levels each ran */
     int64_t kernel_launches; /* all library kernel launches since the last reset */
     int64_t device_bytes;    /* device memory held by the handle */
+    double  bfs_init_ms;     /* MS-BFS device time in clearing + level-1 push (device timer) */
+    double  bfs_pull_ms;     /* MS-BFS device time in the pull steps of levels >= 2 */
+    double  bfs_extract_ms;  /* MS-BFS device time in the kNN extraction steps */
 } gumap_knn_stats;
 
 /*

@@ -207,7 +207,8 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
     const int W = S / 32;
     const size_t words = (size_t)h->n * W;
     int rc;
-    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t), "bitsets"))) return rc;
+    const size_t sum_bytes = (size_t)h->n * (W / 4);  // one summary byte per 128-bit group
+    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t) + 2 * sum_bytes, "bitsets"))) return rc;
     if ((rc = ensure(h->act, (size_t)W * 4, "act"))) return rc;
     if ((rc = ensure(h->need, (size_t)W * 4, "need"))) return rc;
     if ((rc = ensure(h->cnt, (size_t)S * 4, "cnt"))) return rc;
@@ -224,6 +225,8 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.F = base;
         a.N = base + words;
         a.V = base + 2 * words;
+        a.sF = reinterpret_cast<uint8_t*>(base + 3 * words);
+        a.sN = a.sF + sum_bytes;
         a.act = static_cast<uint32_t*>(h->act.p);
         a.need = static_cast<uint32_t*>(h->need.p);
         a.cnt = static_cast<int32_t*>(h->cnt.p);
@@ -389,6 +392,11 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
                   float* out_w, void* stream) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
     if (n_src < 0) return fail(GUMAP_ERR_INVALID_ARG, "n_src < 0");
+    if (n_src == 0) {  // nothing to compute; pointers may be NULL
+        h->last_n_src = 0;
+        h->last_union = false;
+        return GUMAP_OK;
+    }
     if (!sources && n_src != h->n) return fail(GUMAP_ERR_INVALID_ARG, "sources == NULL requires n_src == n");
     const bool want_union = !(h->flags & GUMAP_WEIGHTS_DIRECTED);
     if (want_union && sources) return fail(GUMAP_ERR_INVALID_ARG, "union weights need sources == NULL (all vertices)");
@@ -527,6 +535,9 @@ int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
     out->bfs_level_sum = c.level_sum;
     out->kernel_launches = h->kernel_launches;
     out->device_bytes = (int64_t)held_bytes(h);
+    out->bfs_init_ms = (double)c.t_init_ns * 1e-6;
+    out->bfs_pull_ms = (double)c.t_pull_ns * 1e-6;
+    out->bfs_extract_ms = (double)c.t_extract_ns * 1e-6;
     return GUMAP_OK;
 }
 
@@ -542,6 +553,7 @@ int gumap_knn_reset_stats(gumap_knn* h) {
     CK(cudaMemcpy(&c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
     c.levels_max = 0;
     c.level_sum = 0;
+    c.t_init_ns = c.t_pull_ns = c.t_extract_ns = 0;
     CK(cudaMemcpy(h->d_ctr, &c, sizeof(c), cudaMemcpyHostToDevice), "write counters");
     return GUMAP_OK;
 }

@@ -33,6 +33,11 @@ struct DeviceCounters {
     int32_t pad0;
     long long level_sum;       // sum of levels over launches since the last host reset
     unsigned long long coo_nnz;
+    // device time of the MS-BFS phases (globaltimer ns, block 0's view at the
+    // grid barriers), summed over launches since the last host reset
+    unsigned long long t_init_ns;
+    unsigned long long t_pull_ns;
+    unsigned long long t_extract_ns;
 };
 
 // Arguments of one multi-source BFS launch over a block of sources.
@@ -46,6 +51,8 @@ struct MsbfsArgs {
     uint32_t* F;             // frontier  [n][W]
     uint32_t* N;             // next      [n][W]
     uint32_t* V;             // visited   [n][W]
+    uint8_t* sF;             // [n][W/4] 1 if the 128-bit group of F is nonzero
+    uint8_t* sN;             // [n][W/4] same for N
     uint32_t* act;           // [W] bit j: source j still propagates
     uint32_t* need;          // [W] bit j: list of source j still incomplete
     int32_t* cnt;            // [nb] entries found so far

@@ -107,8 +107,8 @@ __device__ __forceinline__ uint4 ldcg4(const uint4* p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------- phases
 
-// Phase 0: clear V and N, prefill the block's output rows with padding,
-// mark valid source bits in act/need.
+// Phase 0: clear V, N and N's summary, prefill the block's output rows with
+// padding, mark valid source bits in act/need.
 __device__ void phase_init(const MsbfsArgs& a) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -120,6 +120,7 @@ __device__ void phase_init(const MsbfsArgs& a) {
         V4[i] = z;
         N4[i] = z;
     }
+    for (long long i = tid; i < words4; i += nthr) a.sN[i] = 0;
     for (long long i = tid; i < a.W; i += nthr) {
         long long lo = i * 32;
         uint32_t m;
@@ -164,9 +165,12 @@ __device__ void phase_seed(const MsbfsArgs& a) {
         const int deg = e1 - e0;
         const uint32_t bit = 1u << (j & 31);
         uint32_t* Ncol = a.N + (j >> 5);
+        uint8_t* Scol = a.sN + (j >> 7);
+        const int G = a.W >> 2;
         for (int e = e0 + lane; e < e1; e += 32) {
-            int u = __ldg(a.col + e);
+            const int u = __ldg(a.col + e);
             atomicOr(Ncol + (size_t)u * a.W, bit);
+            Scol[(size_t)u * G] = 1;
         }
         const int take = deg < a.k ? deg : a.k;
         int32_t* oi = a.out_idx + (size_t)j * a.k;
@@ -188,9 +192,13 @@ __device__ void phase_seed(const MsbfsArgs& a) {
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[1], 1u);
 }
 
-// Pull step of level d (see file comment). Returns nothing; sets lvl_any.
-__device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
-                           int slot) {
+// Pull step of level d (see file comment). Thread (v, g) owns the 128
+// source bits [128 g, 128 g + 128) of vertex v. A neighbour's 16-byte group
+// is loaded only when its summary byte says the group holds a bit, so the
+// sparse levels (the first ones, and the last ones where only a few sources
+// still advance) read little more than the one-byte summaries.
+__device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, const uint8_t* __restrict__ sFc,
+                           uint32_t* __restrict__ Nc, uint8_t* __restrict__ sNc, int slot) {
     const int G = a.W >> 2;
     const long long total = (long long)a.n * G;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -208,24 +216,27 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         uint4 acc = make_uint4(0u, 0u, 0u, 0u);
         if (nz4(todo)) {
             const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
-            int e = e0;
-            // two neighbours per iteration: both loads in flight before the test
-            for (; e + 1 < e1; e += 2) {
-                const int u0 = __ldg(a.col + e), u1 = __ldg(a.col + e + 1);
-                const uint4 f0 = ldcg4(F4 + (size_t)u0 * G + g);
-                const uint4 f1 = ldcg4(F4 + (size_t)u1 * G + g);
-                acc = or4(acc, or4(f0, f1));
+            const uint8_t* sg = sFc + g;
+            const uint4* fg = F4 + g;
+            for (int e = e0; e < e1; e += 4) {
+                int u[4];
+                uint8_t f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u[q] = (e + q < e1) ? __ldg(a.col + e + q) : -1;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) f[q] = u[q] >= 0 ? __ldcg(sg + (size_t)u[q] * G) : (uint8_t)0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (f[q]) acc = or4(acc, ldcg4(fg + (size_t)u[q] * G));
                 if (covers4(acc, todo)) break;
-            }
-            if (e + 1 == e1) {
-                const int u0 = __ldg(a.col + e);
-                acc = or4(acc, ldcg4(F4 + (size_t)u0 * G + g));
             }
             acc = and4(acc, todo);
         }
+        const bool nz = nz4(acc);
         N4[off] = acc;
         V4[off] = vis;
-        any |= nz4(acc) ? 1 : 0;
+        sNc[off] = nz ? 1 : 0;
+        any |= nz ? 1 : 0;
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
 }
@@ -283,36 +294,57 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
 }
 
 __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
+    const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_prev = timer ? globaltimer_ns() : 0ull;
+    unsigned long long t_init = 0, t_pull = 0, t_extract = 0;
+    auto lap = [&](unsigned long long& acc) {
+        if (timer) {
+            const unsigned long long t = globaltimer_ns();
+            acc += t - t_prev;
+            t_prev = t;
+        }
+    };
     phase_init(a);
     if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
     phase_seed(a);
     if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+    lap(t_init);
 
     uint32_t* Fc = a.N;  // level-1 frontier was pushed into N
     uint32_t* Nc = a.F;
+    uint8_t* sFc = a.sN;
+    uint8_t* sNc = a.sF;
     int last = 1;
     bool go = ld_volatile_u32(&a.ctr->lvl_any[1]) != 0u;
     if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) go = false;
     for (int d = 2; go && d <= a.n; ++d) {
         const int need_now = ld_volatile_i32(&a.ctr->n_need);
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr->lvl_any[(d + 1) % 3] = 0u;
-        phase_pull(a, Fc, Nc, d % 3);
+        phase_pull(a, Fc, sFc, Nc, sNc, d % 3);
         if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+        lap(t_pull);
         if (ld_volatile_u32(&a.ctr->lvl_any[d % 3]) == 0u) break;
         last = d;
         if (need_now > 0) {
             phase_extract(a, Nc, d);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+            lap(t_extract);
             if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) break;
         }
         uint32_t* t = Fc;
         Fc = Nc;
         Nc = t;
+        uint8_t* ts = sFc;
+        sFc = sNc;
+        sNc = ts;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (timer) {
         a.ctr->levels = last;
         a.ctr->level_sum += last;
         if (last > a.ctr->levels_max) a.ctr->levels_max = last;
+        a.ctr->t_init_ns += t_init;
+        a.ctr->t_pull_ns += t_pull;
+        a.ctr->t_extract_ns += t_extract;
     }
 }
 

@@ -36,30 +36,50 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const unsigned long long
     hist[(size_t)tid * num_tiles + blockIdx.x] = h[tid];
 }
 
-// Exclusive scan of `len` counts in place with one CTA of 1024 threads:
-// each thread sums a contiguous chunk, the CTA scans the chunk sums, then
-// each thread rewrites its chunk.
+// Exclusive scan of `len` counts in place with one CTA of 1024 threads,
+// 4096 entries per round: each thread scans 4 consecutive entries, warps
+// scan with shuffles, warp totals are scanned by warp 0, and a running carry
+// links the rounds. Every load is coalesced.
 __global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ data, long long len) {
-    __shared__ unsigned int part[1024];
-    const int tid = threadIdx.x;
-    const long long chunk = (len + 1023) / 1024;
-    const long long b = tid * chunk;
-    const long long e = (b + chunk < len) ? b + chunk : len;
-    unsigned int s = 0u;
-    for (long long i = b; i < e; ++i) s += data[i];
-    part[tid] = s;
+    __shared__ unsigned int wsum[32];
+    __shared__ unsigned int carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) carry_s = 0u;
     __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        unsigned int v = tid >= o ? part[tid - o] : 0u;
+    for (long long base = 0; base < len; base += 4096) {
+        const long long i0 = base + 4ll * tid;
+        unsigned int x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = (i0 + q < len) ? data[i0 + q] : 0u;
+        const unsigned int t = x[0] + x[1] + x[2] + x[3];
+        unsigned int inc = t;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned int y = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
         __syncthreads();
-        part[tid] += v;
+        if (warp == 0) {
+            unsigned int w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned int y = __shfl_up_sync(kFull, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;  // inclusive over warps
+        }
         __syncthreads();
-    }
-    unsigned int run = part[tid] - s;  // exclusive prefix of this chunk
-    for (long long i = b; i < e; ++i) {
-        const unsigned int x = data[i];
-        data[i] = run;
-        run += x;
+        const unsigned int carry = carry_s;
+        unsigned int run = carry + (warp > 0 ? wsum[warp - 1] : 0u) + (inc - t);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (i0 + q < len) data[i0 + q] = run;
+            run += x[q];
+        }
+        __syncthreads();
+        if (tid == 0) carry_s = carry + wsum[31];
+        __syncthreads();
     }
 }
 

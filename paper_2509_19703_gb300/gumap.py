@@ -44,7 +44,8 @@ class _Stats(ctypes.Structure):
     _fields_ = [("engine", ctypes.c_int32), ("block_bits", ctypes.c_int32), ("n_blocks", ctypes.c_int32),
                 ("levels_max", ctypes.c_int32), ("bfs_launches", ctypes.c_int64), ("bfs_ms", ctypes.c_double),
                 ("bfs_level_sum", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("device_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("bfs_init_ms", ctypes.c_double),
+                ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double)]
 
 
 def library_path() -> str:
