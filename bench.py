@@ -304,7 +304,9 @@ def run_ours(args):
                 "kernel": "msbfs_kernel", "launches": launches,
                 "avg_launch_ms": bfs_ms / launches if launches else None,
                 "alg_bytes_per_launch": alg / launches if launches else None,
-                "kernel_share_of_step": (bfs_ms / args.steps) / ms if ms else None}
+                "kernel_share_of_step": (bfs_ms / args.steps) / ms if ms else None,
+                "phase_ms_per_step": {ph: sum(st[f"bfs_{ph}_ms"] for st in stats) / args.steps
+                                      for ph in ("init", "pull", "extract")}}
     gpu_launches = sum(st["kernel_launches"] for st in stats)
 
     # end to end through the public API from pinned host buffers

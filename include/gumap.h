@@ -82,6 +82,8 @@ extern "C" {
 #define GUMAP_OPT_BLOCK_BITS  2 /* value: sources per MS-BFS block (multiple of 128), 0 = auto */
 #define GUMAP_OPT_PROFILE     3 /* value: 1 = time each BFS launch with CUDA events       */
 #define GUMAP_OPT_STATE_BYTES 4 /* value: device bytes allowed for MS-BFS bitsets, 0 = auto */
+#define GUMAP_OPT_HEAVY_DEGREE 5 /* value: MS-BFS vertices of larger degree are processed by a whole warp
+                                    (default 64); setting it synchronises the device */
 
 typedef struct gumap_knn gumap_knn;
 

@@ -101,6 +101,9 @@ struct gumap_knn {
     int32_t* d_rp = nullptr;
     int32_t* d_col = nullptr;
     int32_t* d_identity = nullptr;
+    int32_t* d_heavy = nullptr;  // vertices of degree > heavy_deg (MS-BFS warp items)
+    int32_t n_heavy = 0;
+    int32_t heavy_deg = 64;
     DeviceCounters* d_ctr = nullptr;
 
     // options
@@ -200,6 +203,17 @@ int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b) {
     return GUMAP_OK;
 }
 
+// List the vertices whose MS-BFS items are warp-wide (degree > heavy_deg).
+// Synchronous: the count is needed on the host to size the launch.
+int build_heavy(gumap_knn* h) {
+    int32_t* cnt = &h->d_ctr->aux_count;
+    CK(launch_heavy_list(h->d_rp, h->n, h->heavy_deg, h->d_heavy, cnt, 0), "heavy list");
+    int32_t nh = 0;
+    CK(cudaMemcpy(&nh, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost), "heavy count");
+    h->n_heavy = nh;
+    return GUMAP_OK;
+}
+
 int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
               cudaStream_t st) {
     const int S = choose_block_bits(h, n_src);
@@ -207,8 +221,7 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
     const int W = S / 32;
     const size_t words = (size_t)h->n * W;
     int rc;
-    const size_t sum_bytes = (size_t)h->n * (W / 4);  // one summary byte per 128-bit group
-    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t) + 2 * sum_bytes, "bitsets"))) return rc;
+    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t), "bitsets"))) return rc;
     if ((rc = ensure(h->act, (size_t)W * 4, "act"))) return rc;
     if ((rc = ensure(h->need, (size_t)W * 4, "need"))) return rc;
     if ((rc = ensure(h->cnt, (size_t)S * 4, "cnt"))) return rc;
@@ -225,8 +238,9 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.F = base;
         a.N = base + words;
         a.V = base + 2 * words;
-        a.sF = reinterpret_cast<uint8_t*>(base + 3 * words);
-        a.sN = a.sF + sum_bytes;
+        a.heavy = h->d_heavy;
+        a.n_heavy = h->n_heavy;
+        a.heavy_deg = h->heavy_deg;
         a.act = static_cast<uint32_t*>(h->act.p);
         a.need = static_cast<uint32_t*>(h->need.p);
         a.cnt = static_cast<int32_t*>(h->cnt.p);
@@ -307,6 +321,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     cudaFree(h->d_rp);
     cudaFree(h->d_col);
     cudaFree(h->d_identity);
+    cudaFree(h->d_heavy);
     cudaFree(h->d_ctr);
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
@@ -379,6 +394,19 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
             gumap_knn_destroy(h);
             return fail(GUMAP_ERR_INVALID_GRAPH, "invalid CSR (device validation)");
         }
+    }
+    if ((e = cudaMalloc(&h->d_heavy, sizeof(int32_t) * n)) != cudaSuccess) {
+        gumap_knn_destroy(h);
+        return cuda_fail(e, "cudaMalloc");
+    }
+    // A vertex is "heavy" (one warp per item) only when its degree is well
+    // above the graph's mean: on a uniform dense graph every vertex is long
+    // but the thread-per-item pull keeps more loads in flight.
+    h->heavy_deg = (int32_t)std::max<int64_t>(64, 4 * (nnz / std::max<int32_t>(n, 1)));
+    int rc = build_heavy(h);
+    if (rc) {
+        gumap_knn_destroy(h);
+        return rc;
     }
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
         gumap_knn_destroy(h);
@@ -509,6 +537,12 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             if (value < 0) return fail(GUMAP_ERR_INVALID_ARG, "negative budget");
             h->opt_state_bytes = value;
             return GUMAP_OK;
+        case GUMAP_OPT_HEAVY_DEGREE:
+            if (value < 0 || value > 0x7FFFFFFF) return fail(GUMAP_ERR_INVALID_ARG, "bad degree threshold");
+            CK(cudaSetDevice(h->device), "cudaSetDevice");
+            CK(cudaDeviceSynchronize(), "sync");
+            h->heavy_deg = (int32_t)value;
+            return build_heavy(h);
         default:
             return fail(GUMAP_ERR_INVALID_ARG, "unknown option %d", option);
     }

@@ -13,6 +13,13 @@
 // bit is covered (the bottom-up early exit), and a vertex already reached by
 // every active source costs no neighbour loads at all.
 //
+// Work of a level is the set of (vertex v, 128-bit group g) items. Items of
+// vertices with at most `heavy_deg` neighbours are one thread each (the
+// neighbour loop is short). Items of heavier vertices (hubs of scale-free
+// graphs, every vertex of a dense graph) are one warp each, the lanes
+// splitting the neighbour list and OR-reducing with shuffles, so no level
+// waits on one thread walking a hub's adjacency.
+//
 // Level 1 is a push from the sources (their adjacency rows), and its kNN
 // entries are the first k entries of each source's sorted CSR row.
 // For later levels the extraction phase scans each word column of N in
@@ -105,10 +112,21 @@ __device__ __forceinline__ bool covers4(uint4 acc, uint4 todo) { return !nz4(and
 
 __device__ __forceinline__ uint4 ldcg4(const uint4* p) { return __ldcg(p); }
 
+__device__ __forceinline__ uint4 warp_or4(uint4 a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.x |= __shfl_xor_sync(kFull, a.x, o);
+        a.y |= __shfl_xor_sync(kFull, a.y, o);
+        a.z |= __shfl_xor_sync(kFull, a.z, o);
+        a.w |= __shfl_xor_sync(kFull, a.w, o);
+    }
+    return a;
+}
+
 // ---------------------------------------------------------------- phases
 
-// Phase 0: clear V, N and N's summary, prefill the block's output rows with
-// padding, mark valid source bits in act/need.
+// Phase 0: clear V and N, prefill the block's output rows with padding,
+// mark valid source bits in act/need.
 __device__ void phase_init(const MsbfsArgs& a) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
@@ -120,7 +138,6 @@ __device__ void phase_init(const MsbfsArgs& a) {
         V4[i] = z;
         N4[i] = z;
     }
-    for (long long i = tid; i < words4; i += nthr) a.sN[i] = 0;
     for (long long i = tid; i < a.W; i += nthr) {
         long long lo = i * 32;
         uint32_t m;
@@ -165,12 +182,9 @@ __device__ void phase_seed(const MsbfsArgs& a) {
         const int deg = e1 - e0;
         const uint32_t bit = 1u << (j & 31);
         uint32_t* Ncol = a.N + (j >> 5);
-        uint8_t* Scol = a.sN + (j >> 7);
-        const int G = a.W >> 2;
         for (int e = e0 + lane; e < e1; e += 32) {
             const int u = __ldg(a.col + e);
             atomicOr(Ncol + (size_t)u * a.W, bit);
-            Scol[(size_t)u * G] = 1;
         }
         const int take = deg < a.k ? deg : a.k;
         int32_t* oi = a.out_idx + (size_t)j * a.k;
@@ -192,51 +206,78 @@ __device__ void phase_seed(const MsbfsArgs& a) {
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[1], 1u);
 }
 
-// Pull step of level d (see file comment). Thread (v, g) owns the 128
-// source bits [128 g, 128 g + 128) of vertex v. A neighbour's 16-byte group
-// is loaded only when its summary byte says the group holds a bit, so the
-// sparse levels (the first ones, and the last ones where only a few sources
-// still advance) read little more than the one-byte summaries.
-__device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, const uint8_t* __restrict__ sFc,
-                           uint32_t* __restrict__ Nc, uint8_t* __restrict__ sNc, int slot) {
+// Pull step of level d (see file comment).
+__device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
+                           int slot) {
     const int G = a.W >> 2;
-    const long long total = (long long)a.n * G;
+    const int lane = threadIdx.x & 31;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
     uint4* N4 = reinterpret_cast<uint4*>(Nc);
     uint4* V4 = reinterpret_cast<uint4*>(a.V);
     const uint4* act4 = reinterpret_cast<const uint4*>(a.act);
     int any = 0;
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += nthr) {
-        const int v = (int)(t / G);
-        const int g = (int)(t - (long long)v * G);
+
+    // heavy vertices: one warp per (v, g), lanes split the neighbour list
+    const long long heavy_items = (long long)a.n_heavy * G;
+    for (long long it = gtid >> 5; it < heavy_items; it += nthr >> 5) {
+        const int h = (int)(it / G);
+        const int g = (int)(it - (long long)h * G);
+        const int v = __ldg(a.heavy + h);
         const size_t off = (size_t)v * G + g;
         const uint4 vis = or4(ldcg4(V4 + off), ldcg4(F4 + off));
         const uint4 todo = andnot4(ldcg4(act4 + g), vis);
         uint4 acc = make_uint4(0u, 0u, 0u, 0u);
         if (nz4(todo)) {
             const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
-            const uint8_t* sg = sFc + g;
-            const uint4* fg = F4 + g;
-            for (int e = e0; e < e1; e += 4) {
-                int u[4];
-                uint8_t f[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) u[q] = (e + q < e1) ? __ldg(a.col + e + q) : -1;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) f[q] = u[q] >= 0 ? __ldcg(sg + (size_t)u[q] * G) : (uint8_t)0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (f[q]) acc = or4(acc, ldcg4(fg + (size_t)u[q] * G));
+            for (int base = e0; base < e1; base += 64) {
+                const int ea = base + lane, eb = base + 32 + lane;
+                const int ua = ea < e1 ? __ldg(a.col + ea) : -1;
+                const int ub = eb < e1 ? __ldg(a.col + eb) : -1;
+                if (ua >= 0) acc = or4(acc, ldcg4(F4 + (size_t)ua * G + g));
+                if (ub >= 0) acc = or4(acc, ldcg4(F4 + (size_t)ub * G + g));
+                acc = warp_or4(acc);
                 if (covers4(acc, todo)) break;
             }
             acc = and4(acc, todo);
         }
-        const bool nz = nz4(acc);
+        if (lane == 0) {
+            N4[off] = acc;
+            V4[off] = vis;
+            any |= nz4(acc) ? 1 : 0;
+        }
+    }
+
+    // light vertices: one thread per (v, g)
+    const long long total = (long long)a.n * G;
+    for (long long t = gtid; t < total; t += nthr) {
+        const int v = (int)(t / G);
+        const int g = (int)(t - (long long)v * G);
+        const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+        if (e1 - e0 > a.heavy_deg) continue;  // done by the warp loop above
+        const size_t off = (size_t)v * G + g;
+        const uint4 vis = or4(ldcg4(V4 + off), ldcg4(F4 + off));
+        const uint4 todo = andnot4(ldcg4(act4 + g), vis);
+        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+        if (nz4(todo)) {
+            const uint4* fg = F4 + g;
+            for (int e = e0; e < e1; e += 4) {
+                int u[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u[q] = (e + q < e1) ? __ldg(a.col + e + q) : -1;
+                uint4 f[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    f[q] = u[q] >= 0 ? ldcg4(fg + (size_t)u[q] * G) : make_uint4(0u, 0u, 0u, 0u);
+                acc = or4(or4(acc, or4(f[0], f[1])), or4(f[2], f[3]));
+                if (covers4(acc, todo)) break;
+            }
+            acc = and4(acc, todo);
+        }
         N4[off] = acc;
         V4[off] = vis;
-        sNc[off] = nz ? 1 : 0;
-        any |= nz ? 1 : 0;
+        any |= nz4(acc) ? 1 : 0;
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
 }
@@ -258,27 +299,35 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
         uint32_t needw = need0;
         int32_t* oi = a.out_idx + (size_t)j * a.k;
         uint16_t* od = a.out_dist + (size_t)j * a.k;
-        for (int v0 = 0; v0 < a.n; v0 += 32) {
-            const int v = v0 + lane;
-            uint32_t x = (v < a.n) ? __ldcg(Nc + (size_t)v * a.W + w) : 0u;
-            x &= needw;
-            if (__ballot_sync(kFull, x != 0u) == 0u) continue;
-            uint32_t mine = 0u;
+        // four 32-vertex tiles per round, their loads issued together
+        for (int v00 = 0; v00 < a.n && needw != 0u; v00 += 128) {
+            uint32_t xs[4];
 #pragma unroll
-            for (int b = 0; b < 32; ++b) {
-                const uint32_t t = __ballot_sync(kFull, (x >> b) & 1u);
-                if (lane == b) mine = t;
+            for (int q = 0; q < 4; ++q) {
+                const int v = v00 + 32 * q + lane;
+                xs[q] = (v < a.n) ? __ldcg(Nc + (size_t)v * a.W + w) : 0u;
             }
-            if (mine) found = true;
-            while (mine && c < a.k) {
-                const int i = __ffs(mine) - 1;
-                mine &= mine - 1u;
-                oi[c] = v0 + i;
-                od[c] = (uint16_t)d;
-                ++c;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint32_t x = xs[q] & needw;
+                if (__ballot_sync(kFull, x != 0u) == 0u) continue;
+                uint32_t mine = 0u;
+#pragma unroll
+                for (int b = 0; b < 32; ++b) {
+                    const uint32_t t = __ballot_sync(kFull, (x >> b) & 1u);
+                    if (lane == b) mine = t;
+                }
+                if (mine) found = true;
+                const int v0 = v00 + 32 * q;
+                while (mine && c < a.k) {
+                    const int i = __ffs(mine) - 1;
+                    mine &= mine - 1u;
+                    oi[c] = v0 + i;
+                    od[c] = (uint16_t)d;
+                    ++c;
+                }
+                needw = __ballot_sync(kFull, mine_need && c < a.k);
             }
-            needw = __ballot_sync(kFull, mine_need && c < a.k);
-            if (needw == 0u) break;
         }
         // a source is finished when its list is full or its BFS ran dry
         const bool done = mine_need && (c >= a.k || !found);
@@ -312,15 +361,13 @@ __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
 
     uint32_t* Fc = a.N;  // level-1 frontier was pushed into N
     uint32_t* Nc = a.F;
-    uint8_t* sFc = a.sN;
-    uint8_t* sNc = a.sF;
     int last = 1;
     bool go = ld_volatile_u32(&a.ctr->lvl_any[1]) != 0u;
     if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) go = false;
     for (int d = 2; go && d <= a.n; ++d) {
         const int need_now = ld_volatile_i32(&a.ctr->n_need);
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr->lvl_any[(d + 1) % 3] = 0u;
-        phase_pull(a, Fc, sFc, Nc, sNc, d % 3);
+        phase_pull(a, Fc, Nc, d % 3);
         if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
         lap(t_pull);
         if (ld_volatile_u32(&a.ctr->lvl_any[d % 3]) == 0u) break;
@@ -334,9 +381,6 @@ __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
         uint32_t* t = Fc;
         Fc = Nc;
         Nc = t;
-        uint8_t* ts = sFc;
-        sFc = sNc;
-        sNc = ts;
     }
     if (timer) {
         a.ctr->levels = last;
@@ -352,6 +396,16 @@ __global__ void identity_kernel(int32_t* dst, int32_t n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         dst[i] = (int32_t)i;
+}
+
+// Vertices with more than `thr` neighbours, in any order (the pull result
+// does not depend on the order items are processed in).
+__global__ void heavy_list_kernel(const int32_t* __restrict__ rp, int32_t n, int32_t thr, int32_t* heavy,
+                                  int32_t* count) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+         v += (long long)gridDim.x * blockDim.x) {
+        if (rp[v + 1] - rp[v] > thr) heavy[atomicAdd(count, 1)] = (int32_t)v;
+    }
 }
 
 }  // namespace
@@ -374,6 +428,16 @@ cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s) {
     int grid = (int)((n + 255) / 256);
     if (grid > 4096) grid = 4096;
     identity_kernel<<<grid, 256, 0, s>>>(dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_heavy_list(const int32_t* row_ptr, int32_t n, int32_t thr, int32_t* heavy, int32_t* count,
+                              cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess || n <= 0) return e;
+    int grid = (int)((n + 255) / 256);
+    if (grid > 4096) grid = 4096;
+    heavy_list_kernel<<<grid, 256, 0, s>>>(row_ptr, n, thr, heavy, count);
     return cudaGetLastError();
 }
 

@@ -27,11 +27,15 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const unsigned long long
     h[tid] = 0u;
     __syncthreads();
     const long long base = (long long)blockIdx.x * kTile;
-#pragma unroll 4
-    for (int c = 0; c < kItems; ++c) {
+    unsigned int dg[kItems];
+#pragma unroll
+    for (int c = 0; c < kItems; ++c) {  // all loads in flight before the counting
         const long long i = base + c * kThreads + tid;
-        if (i < count) atomicAdd(&h[(unsigned)(keys[i] >> shift) & 0xFFu], 1u);
+        dg[c] = i < count ? (unsigned)(__ldcs(keys + i) >> shift) & 0xFFu : 256u;
     }
+#pragma unroll
+    for (int c = 0; c < kItems; ++c)
+        if (dg[c] < 256u) atomicAdd(&h[dg[c]], 1u);
     __syncthreads();
     hist[(size_t)tid * num_tiles + blockIdx.x] = h[tid];
 }
@@ -99,17 +103,22 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const unsigned long l
     __syncthreads();
     const unsigned lt = (1u << lane) - 1u;
     const long long base = (long long)blockIdx.x * kTile;
+    // the tile's keys and values are loaded up front: one memory latency, not 16
+    unsigned long long keys[kItems];
+    float vals[kItems];
+#pragma unroll
+    for (int c = 0; c < kItems; ++c) {
+        const long long i = base + c * kThreads + tid;
+        keys[c] = i < count ? __ldcs(kin + i) : 0ull;
+        vals[c] = i < count ? __ldcs(vin + i) : 0.0f;
+    }
+#pragma unroll
     for (int c = 0; c < kItems; ++c) {
         const long long i = base + c * kThreads + tid;
         const bool valid = i < count;
-        unsigned long long key = 0ull;
-        float val = 0.0f;
-        int d = 256;  // invalid lanes form their own group
-        if (valid) {
-            key = kin[i];
-            val = vin[i];
-            d = (int)((key >> shift) & 0xFFull);
-        }
+        const unsigned long long key = keys[c];
+        const float val = vals[c];
+        const int d = valid ? (int)((key >> shift) & 0xFFull) : 256;  // invalid lanes group apart
         const unsigned peers = __match_any_sync(kFull, d);
         const unsigned rank = __popc(peers & lt);
         if (valid && rank == 0u) wcnt[warp][d] = __popc(peers);

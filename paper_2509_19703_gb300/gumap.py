@@ -22,7 +22,7 @@ from . import _build
 FULL, PARTIAL = 0, 1
 WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE = 0x0, 0x1, 0x2
 ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER = 0, 1, 2, 3
-OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES = 1, 2, 3, 4
+OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
 MAX_K = 256
 DIST_INF = 0xFFFF
 

@@ -74,6 +74,20 @@ def test_block_tiling_ragged(bits):
     assert_parity(run_gpu(g, 15, "partial", engine=MSBFS, block_bits=bits), ref, f"partial bits={bits}")
 
 
+@pytest.mark.parametrize("heavy", [0, 3, 1 << 30])
+def test_heavy_threshold(heavy):
+    """Warp-per-item (heavy) and thread-per-item (light) pulls agree."""
+    g = gg.disjoint_union([gg.barabasi_albert(1500, 3, 64), gg.star(200), gg.gnp(300, 0.05, 65)], "hv")
+    ref = oracle_ref(g, 15, "full")
+    with gumap.KnnGraph.from_graph(g, 15) as kg:
+        kg.set_option(gumap.OPT_HEAVY_DEGREE, heavy)
+        kg.set_option(gumap.OPT_BLOCK_BITS, 512)
+        out = kg.run()
+        kg.check()
+        assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
+        assert float(np.max(np.abs(out["w"].cpu().numpy() - ref["w"]))) <= 1e-5
+
+
 @pytest.mark.parametrize("mode", ["full", "partial"])
 def test_explicit_sources_with_duplicates(mode):
     g = gg.barabasi_albert(2000, 3, 62)
