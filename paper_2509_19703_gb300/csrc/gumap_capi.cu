@@ -101,9 +101,10 @@ struct gumap_knn {
     int32_t* d_rp = nullptr;
     int32_t* d_col = nullptr;
     int32_t* d_identity = nullptr;
-    int32_t* d_heavy = nullptr;  // vertices of degree > heavy_deg (MS-BFS warp items)
+    int32_t* d_order = nullptr;  // MS-BFS processing order (heavy vertices first)
     int32_t n_heavy = 0;
     int32_t heavy_deg = 64;
+    std::vector<int32_t> deg;    // host copy of the vertex degrees
     DeviceCounters* d_ctr = nullptr;
 
     // options
@@ -203,14 +204,21 @@ int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b) {
     return GUMAP_OK;
 }
 
-// List the vertices whose MS-BFS items are warp-wide (degree > heavy_deg).
-// Synchronous: the count is needed on the host to size the launch.
-int build_heavy(gumap_knn* h) {
-    int32_t* cnt = &h->d_ctr->aux_count;
-    CK(launch_heavy_list(h->d_rp, h->n, h->heavy_deg, h->d_heavy, cnt, 0), "heavy list");
+// Processing order of the MS-BFS pull: vertices of degree > heavy_deg
+// (warp-wide items) then the rest, each by decreasing degree (a counting
+// sort on the host degrees, stable in vertex id). Synchronous upload.
+int build_order(gumap_knn* h) {
+    const int32_t n = h->n;
+    int32_t maxd = 0;
+    for (int32_t v = 0; v < n; ++v) maxd = std::max(maxd, h->deg[v]);
+    std::vector<int32_t> start((size_t)maxd + 2, 0), order((size_t)n);
+    for (int32_t v = 0; v < n; ++v) start[(size_t)(maxd - h->deg[v]) + 1]++;
+    for (size_t i = 1; i < start.size(); ++i) start[i] += start[i - 1];
+    for (int32_t v = 0; v < n; ++v) order[(size_t)start[(size_t)(maxd - h->deg[v])]++] = v;
     int32_t nh = 0;
-    CK(cudaMemcpy(&nh, cnt, sizeof(int32_t), cudaMemcpyDeviceToHost), "heavy count");
+    while (nh < n && h->deg[order[(size_t)nh]] > h->heavy_deg) ++nh;
     h->n_heavy = nh;
+    CK(cudaMemcpy(h->d_order, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice), "order upload");
     return GUMAP_OK;
 }
 
@@ -238,9 +246,10 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.F = base;
         a.N = base + words;
         a.V = base + 2 * words;
-        a.heavy = h->d_heavy;
+        a.heavy = h->d_order;
         a.n_heavy = h->n_heavy;
-        a.heavy_deg = h->heavy_deg;
+        a.light = h->d_order + h->n_heavy;
+        a.n_light = h->n - h->n_heavy;
         a.act = static_cast<uint32_t*>(h->act.p);
         a.need = static_cast<uint32_t*>(h->need.p);
         a.cnt = static_cast<int32_t*>(h->cnt.p);
@@ -321,7 +330,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     cudaFree(h->d_rp);
     cudaFree(h->d_col);
     cudaFree(h->d_identity);
-    cudaFree(h->d_heavy);
+    cudaFree(h->d_order);
     cudaFree(h->d_ctr);
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
@@ -395,15 +404,25 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
             return fail(GUMAP_ERR_INVALID_GRAPH, "invalid CSR (device validation)");
         }
     }
-    if ((e = cudaMalloc(&h->d_heavy, sizeof(int32_t) * n)) != cudaSuccess) {
+    if ((e = cudaMalloc(&h->d_order, sizeof(int32_t) * n)) != cudaSuccess) {
         gumap_knn_destroy(h);
         return cuda_fail(e, "cudaMalloc");
+    }
+    {
+        std::vector<int32_t> rp_host((size_t)n + 1);
+        if ((e = cudaMemcpy(rp_host.data(), h->d_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost)) !=
+            cudaSuccess) {
+            gumap_knn_destroy(h);
+            return cuda_fail(e, "row_ptr readback");
+        }
+        h->deg.resize((size_t)n);
+        for (int32_t v = 0; v < n; ++v) h->deg[(size_t)v] = rp_host[(size_t)v + 1] - rp_host[(size_t)v];
     }
     // A vertex is "heavy" (one warp per item) only when its degree is well
     // above the graph's mean: on a uniform dense graph every vertex is long
     // but the thread-per-item pull keeps more loads in flight.
     h->heavy_deg = (int32_t)std::max<int64_t>(64, 4 * (nnz / std::max<int32_t>(n, 1)));
-    int rc = build_heavy(h);
+    int rc = build_order(h);
     if (rc) {
         gumap_knn_destroy(h);
         return rc;
@@ -542,7 +561,7 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             CK(cudaSetDevice(h->device), "cudaSetDevice");
             CK(cudaDeviceSynchronize(), "sync");
             h->heavy_deg = (int32_t)value;
-            return build_heavy(h);
+            return build_order(h);
         default:
             return fail(GUMAP_ERR_INVALID_ARG, "unknown option %d", option);
     }

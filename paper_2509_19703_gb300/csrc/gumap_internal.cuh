@@ -30,7 +30,7 @@ struct DeviceCounters {
     uint32_t lvl_any[3];       // "some vertex was reached at level d" in slot d % 3
     int32_t levels;            // deepest level reached by the last MS-BFS launch
     int32_t levels_max;        // max over launches since the last host reset
-    int32_t aux_count;         // scratch counter of the set-up kernels (heavy-vertex list)
+    int32_t aux_count;         // scratch counter of the set-up kernels
     long long level_sum;       // sum of levels over launches since the last host reset
     unsigned long long coo_nnz;
     // device time of the MS-BFS phases (globaltimer ns, block 0's view at the
@@ -51,9 +51,13 @@ struct MsbfsArgs {
     uint32_t* F;             // frontier  [n][W]
     uint32_t* N;             // next      [n][W]
     uint32_t* V;             // visited   [n][W]
-    const int32_t* heavy;    // vertices with more than heavy_deg neighbours
+    // Processing order of the pull: vertices of degree above the heavy
+    // threshold (one warp per item), then the rest (one thread per item),
+    // each list by decreasing degree so the longest items start first.
+    const int32_t* heavy;
     int32_t n_heavy;
-    int32_t heavy_deg;       // degree above which a vertex's items are one warp each
+    const int32_t* light;
+    int32_t n_light;
     uint32_t* act;           // [W] bit j: source j still propagates
     uint32_t* need;          // [W] bit j: list of source j still incomplete
     int32_t* cnt;            // [nb] entries found so far
@@ -81,8 +85,6 @@ struct FrontierArgs {
 int msbfs_max_blocks_per_sm(int block_threads);
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s);
-cudaError_t launch_heavy_list(const int32_t* row_ptr, int32_t n, int32_t thr, int32_t* heavy, int32_t* count,
-                              cudaStream_t s);
 
 // ---- frontier.cu
 cudaError_t launch_frontier(const FrontierArgs& a, cudaStream_t s);

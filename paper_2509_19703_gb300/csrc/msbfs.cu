@@ -14,11 +14,13 @@
 // every active source costs no neighbour loads at all.
 //
 // Work of a level is the set of (vertex v, 128-bit group g) items. Items of
-// vertices with at most `heavy_deg` neighbours are one thread each (the
-// neighbour loop is short). Items of heavier vertices (hubs of scale-free
-// graphs, every vertex of a dense graph) are one warp each, the lanes
-// splitting the neighbour list and OR-reducing with shuffles, so no level
-// waits on one thread walking a hub's adjacency.
+// vertices of ordinary degree are one thread each (the neighbour loop is
+// short). Items of vertices whose degree is far above the mean (hubs of
+// scale-free graphs) are one warp each, the lanes splitting the neighbour
+// list and OR-reducing with shuffles, so no level waits on one thread
+// walking a hub's adjacency. Both lists run in decreasing degree, so the
+// longest items start first and the short ones fill the tail before the
+// grid barrier.
 //
 // Level 1 is a push from the sources (their adjacency rows), and its kNN
 // entries are the first k entries of each source's sorted CSR row.
@@ -249,28 +251,29 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         }
     }
 
-    // light vertices: one thread per (v, g)
-    const long long total = (long long)a.n * G;
+    // light vertices: one thread per (v, g), eight neighbour loads in flight
+    const long long total = (long long)a.n_light * G;
     for (long long t = gtid; t < total; t += nthr) {
-        const int v = (int)(t / G);
-        const int g = (int)(t - (long long)v * G);
+        const int li = (int)(t / G);
+        const int g = (int)(t - (long long)li * G);
+        const int v = __ldg(a.light + li);
         const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
-        if (e1 - e0 > a.heavy_deg) continue;  // done by the warp loop above
         const size_t off = (size_t)v * G + g;
         const uint4 vis = or4(ldcg4(V4 + off), ldcg4(F4 + off));
         const uint4 todo = andnot4(ldcg4(act4 + g), vis);
         uint4 acc = make_uint4(0u, 0u, 0u, 0u);
         if (nz4(todo)) {
             const uint4* fg = F4 + g;
-            for (int e = e0; e < e1; e += 4) {
-                int u[4];
+            for (int e = e0; e < e1; e += 8) {
+                int u[8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) u[q] = (e + q < e1) ? __ldg(a.col + e + q) : -1;
-                uint4 f[4];
+                for (int q = 0; q < 8; ++q) u[q] = (e + q < e1) ? __ldg(a.col + e + q) : -1;
+                uint4 f[8];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
+                for (int q = 0; q < 8; ++q)
                     f[q] = u[q] >= 0 ? ldcg4(fg + (size_t)u[q] * G) : make_uint4(0u, 0u, 0u, 0u);
-                acc = or4(or4(acc, or4(f[0], f[1])), or4(f[2], f[3]));
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc = or4(acc, f[q]);
                 if (covers4(acc, todo)) break;
             }
             acc = and4(acc, todo);
@@ -398,16 +401,6 @@ __global__ void identity_kernel(int32_t* dst, int32_t n) {
         dst[i] = (int32_t)i;
 }
 
-// Vertices with more than `thr` neighbours, in any order (the pull result
-// does not depend on the order items are processed in).
-__global__ void heavy_list_kernel(const int32_t* __restrict__ rp, int32_t n, int32_t thr, int32_t* heavy,
-                                  int32_t* count) {
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (long long)gridDim.x * blockDim.x) {
-        if (rp[v + 1] - rp[v] > thr) heavy[atomicAdd(count, 1)] = (int32_t)v;
-    }
-}
-
 }  // namespace
 
 int msbfs_max_blocks_per_sm(int block_threads) {
@@ -428,16 +421,6 @@ cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s) {
     int grid = (int)((n + 255) / 256);
     if (grid > 4096) grid = 4096;
     identity_kernel<<<grid, 256, 0, s>>>(dst, n);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_heavy_list(const int32_t* row_ptr, int32_t n, int32_t thr, int32_t* heavy, int32_t* count,
-                              cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), s);
-    if (e != cudaSuccess || n <= 0) return e;
-    int grid = (int)((n + 255) / 256);
-    if (grid > 4096) grid = 4096;
-    heavy_list_kernel<<<grid, 256, 0, s>>>(row_ptr, n, thr, heavy, count);
     return cudaGetLastError();
 }
 
