@@ -17,7 +17,7 @@
  *       h_ij = exp(-(d_ij - rho_i) / sigma_i)   (Section 2.1)
  *     with sigma_i solving sum_j exp(-max(0, d_ij - rho_i)/sigma_i) = log2 k;
  *   - the fuzzy union w_ij = a_ij + a_ji - a_ij * a_ji (the symmetrisation of
- *     the UMAP implementation the paper builds on, Section 5.1.1).
+ *     the UMAP implementation the paper builds on, Section 4.1.1).
  * Floating point is FP64 throughout.
  *
  * Readings taken where the paper is silent or garbled:

@@ -1,6 +1,6 @@
 // UMAP fuzzy weights of the kNN lists (Section 2.1, h_ij) and their fuzzy
 // union (the symmetrisation of the UMAP implementation the paper builds on,
-// Section 5.1.1).
+// Section 4.1.1).
 //
 // smooth_knn: one warp per row. rho_i is the smallest valid distance of the
 // row; sigma_i solves f(sigma) = sum_j exp(-max(0, d_ij - rho_i)/sigma) = T

@@ -3,7 +3,7 @@ tests/bench and by the CPU oracle's tests.
 
 The module holds none of the method's arithmetic: it only draws random graphs
 and lays them out as CSR. The generators stand in for the paper's datasets
-(Section 5.1.2, Table 2: scale-free, GION and mesh graphs), which are not
+(Section 4.1.2, Table 2: scale-free, GION and mesh graphs), which are not
 available: Barabasi-Albert for scale-free, grids for meshes, G(n, p) and
 uniform random trees for the dense and the large-diameter ends.
 

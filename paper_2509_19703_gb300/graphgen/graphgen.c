@@ -6,7 +6,7 @@
  * distances, no weights): only random-graph models and a CSR builder.
  *
  * The paper evaluates on real scale-free, GION (large-diameter RNA) and mesh
- * graphs (Section 5.1.2, Table 2), which are not available here. These models
+ * graphs (Section 4.1.2, Table 2), which are not available here. These models
  * stand in for them: Barabasi-Albert for scale-free, 2-D grids for meshes,
  * G(n,p) and uniform random trees to bracket the dense and the large-diameter
  * ends. The paper uses the largest connected component of each graph; every
