@@ -17,7 +17,7 @@
  *       sum_j exp(-max(0, d_ij - rho_i) / sigma_i) = log2 k, and the directed
  *       similarity a_ij = exp(-max(0, d_ij - rho_i) / sigma_i) (Section 2.1,
  *       h_ij), then the fuzzy union w_ij = a_ij + a_ji - a_ij a_ji of the
- *       UMAP implementation the paper builds on (Section 5.1.1).
+ *       UMAP implementation the paper builds on (Section 4.1.1).
  *
  * Conventions shared by every call:
  *   - Vertex ids are int32 in [0, n). Distances are hop counts stored as
@@ -148,7 +148,7 @@ int gumap_knn_rho_sigma(gumap_knn *h, float *rho, float *sigma, void *stream);
 
 /*
  * gumap_knn_coo - copy the symmetric fuzzy-union graph of the last run as a
- * COO sorted by (row, col) (the union of Section 5.1.1's UMAP
+ * COO sorted by (row, col) (the union of Section 4.1.1's UMAP
  * implementation; every pair appears once, w_ij = w_ji).
  *
  *   row, col  device int32[2 * n * k] (capacity bound; may be NULL to skip)
@@ -194,6 +194,39 @@ int gumap_knn_reset_stats(gumap_knn *h);
 
 /* gumap_knn_destroy - free everything the handle owns (synchronises the device). NULL is allowed. */
 int gumap_knn_destroy(gumap_knn *h);
+
+/*
+ * gumap_knn_run_noalloc - kNN lists of every vertex (the same rows as
+ * gumap_knn_run's out_idx / out_dist for sources == NULL) computed without
+ * allocating anything. The paper has no counterpart: this entry point exists
+ * for callers that cannot call cudaMalloc where they need the lists, such as
+ * code inside a framework that owns all device memory (a caching allocator
+ * or a fixed budget) or a latency-bound loop that cannot afford cudaMalloc's
+ * device synchronisation.
+ *
+ *   row_ptr, col_idx  device CSR (int32[n + 1], int32[nnz]) obeying the
+ *                     gumap_knn_create rules; NOT validated here (validation
+ *                     would need a synchronisation), so an invalid graph gives
+ *                     undefined results.
+ *   n, nnz, k, mode   as for gumap_knn_create (2 <= n; 1 <= k <= min(n-1, 256)).
+ *   out_idx, out_dist device int32[n][k] / uint16[n][k], caller-owned.
+ *   status_out        optional device int32[1]: receives GUMAP_OK or the
+ *                     device status (GUMAP_ERR_TIMEOUT) when the work ends.
+ *   stream            cudaStream_t; the call is asynchronous on it.
+ *
+ * All scratch comes from one 16 MiB file-scope device array inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits. The call rejects graphs whose scratch would not fit (about
+ * 3 * 16 + 4 bytes per vertex at the narrowest source block, i.e. n up to
+ * roughly 320,000) with GUMAP_ERR_TOO_LARGE, and never calls cudaMalloc,
+ * cudaFree or any allocating routine. The first call on a device looks up the
+ * array's device address (make that first call before any stream capture).
+ * Every call reuses the array and clears what must start at zero; calls whose
+ * GPU work overlaps (other streams, other threads) race on it. Errors:
+ * INVALID_ARG, TOO_LARGE, CUDA.
+ */
+int gumap_knn_run_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int64_t nnz, int32_t k,
+                          int mode, int32_t *out_idx, uint16_t *out_dist, int32_t *status_out, void *stream);
 
 /* Static string for a status code (never NULL). */
 const char *gumap_status_string(int status);

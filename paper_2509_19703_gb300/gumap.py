@@ -73,6 +73,7 @@ def load():
                 "gumap_knn_get_stats": [vp, ctypes.POINTER(_Stats)],
                 "gumap_knn_reset_stats": [vp],
                 "gumap_knn_destroy": [vp],
+                "gumap_knn_run_noalloc": [vp, vp, i32, i64, i32, ctypes.c_int, vp, vp, vp, vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -180,6 +181,19 @@ def gumap_knn_reset_stats(h):
 
 def gumap_knn_destroy(h):
     _check(load().gumap_knn_destroy(h), "gumap_knn_destroy")
+
+
+def gumap_knn_run_noalloc(row_ptr, col_idx, n: int, nnz: int, k: int, mode: int, out_idx, out_dist,
+                          status=None, stream=None):
+    """kNN lists of every vertex with no allocation inside the library (for
+    callers that cannot allocate device memory at the point of the call: the
+    scratch is a fixed array compiled into the library). row_ptr/col_idx are
+    CUDA int32 tensors; outputs CUDA int32 / int16 tensors of shape [n, k];
+    status an optional CUDA int32 tensor of one element."""
+    _check(load().gumap_knn_run_noalloc(_dptr(row_ptr, torch.int32, "row_ptr"), _dptr(col_idx, torch.int32, "col_idx"),
+                                        int(n), int(nnz), int(k), int(mode), _dptr(out_idx, torch.int32, "out_idx"),
+                                        _dptr(out_dist, torch.int16, "out_dist"), _dptr(status, torch.int32, "status"),
+                                        _stream(stream)), "gumap_knn_run_noalloc")
 
 
 # ---------------------------------------------------------------- wrapper
