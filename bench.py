@@ -55,6 +55,8 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample budget")
+    p.add_argument("--only", choices=["ba20k", "er5k"], default=None,
+                   help="run one of the two graphs (for profiler captures; not a bench line)")
     return p.parse_args()
 
 
@@ -63,9 +65,10 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def build_graphs():
+def build_graphs(only=None):
     from paper_2509_19703_gb300 import graphgen as gg
-    return [gg.config_ba20k(), gg.config_er5k()]
+    makers = {"ba20k": gg.config_ba20k, "er5k": gg.config_er5k}
+    return [m() for name, m in makers.items() if only in (None, name)]
 
 
 def component_work(g):
@@ -211,7 +214,7 @@ def run_reference(args):
     rank, world, _ = dist_info()
     if rank != 0:
         return
-    graphs = build_graphs()
+    graphs = build_graphs(args.only)
     works = [component_work(g) for g in graphs]
     budget = max(0.2, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
@@ -247,7 +250,7 @@ def run_ours(args):
         if world > 1:
             dist.barrier()
 
-    graphs = build_graphs()
+    graphs = build_graphs(args.only)
     works = [component_work(g) for g in graphs]
     work_per_step = int(sum(int(w.sum()) for w in works))
     kgs = [gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=gumap.FULL) for g in graphs]
