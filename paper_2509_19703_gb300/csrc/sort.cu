@@ -3,10 +3,11 @@
 // the key of entry (i, j) is (i << B) | j with B = ceil(log2 n).
 //
 // Each pass: (1) a tile histogram of the digit (256 bins per 4096-key tile,
-// stored digit-major), (2) one exclusive scan over that table, giving every
-// (digit, tile) its output start, (3) a stable scatter: inside a tile the
-// keys are ranked in input order with warp match/ballot ranks plus per-warp
-// digit counts in shared memory.
+// stored digit-major), (2) one CTA per digit scans that digit's tile counts
+// and records the digit total, (3) a stable scatter: each tile adds the
+// prefix of the digit totals to its tile offsets, then ranks its keys in
+// input order with warp match/ballot ranks plus per-warp digit counts in
+// shared memory.
 #include "gumap_internal.cuh"
 
 namespace gumap {
@@ -40,13 +41,16 @@ __global__ void __launch_bounds__(kThreads) hist_kernel(const unsigned long long
     hist[(size_t)tid * num_tiles + blockIdx.x] = h[tid];
 }
 
-// Exclusive scan of `len` counts in place with one CTA of 1024 threads,
-// 4096 entries per round: each thread scans 4 consecutive entries, warps
-// scan with shuffles, warp totals are scanned by warp 0, and a running carry
-// links the rounds. Every load is coalesced.
-__global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ data, long long len) {
+// One CTA per digit: exclusive scan, in place, of that digit's per-tile
+// counts (the tile offsets within the digit's output range), and the digit's
+// total into totals[digit]. 4096 entries per round: each thread scans 4
+// consecutive entries, warps scan with shuffles, warp totals are scanned by
+// warp 0, a running carry links the rounds. Every load is coalesced.
+__global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ hist, long long len,
+                                                    unsigned int* __restrict__ totals) {
     __shared__ unsigned int wsum[32];
     __shared__ unsigned int carry_s;
+    unsigned int* data = hist + (size_t)blockIdx.x * len;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) carry_s = 0u;
     __syncthreads();
@@ -85,23 +89,38 @@ __global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ d
         if (tid == 0) carry_s = carry + wsum[31];
         __syncthreads();
     }
+    if (tid == 0) totals[blockIdx.x] = carry_s;
 }
 
 __global__ void __launch_bounds__(kThreads) scatter_kernel(const unsigned long long* __restrict__ kin,
                                                            const float* __restrict__ vin,
                                                            unsigned long long* __restrict__ kout,
                                                            float* __restrict__ vout, long long count, int shift,
-                                                           int num_tiles, const unsigned int* __restrict__ offs) {
+                                                           int num_tiles, const unsigned int* __restrict__ offs,
+                                                           const unsigned int* __restrict__ totals) {
     __shared__ unsigned int run[256];
     __shared__ unsigned int wcnt[kWarps][256];
+    __shared__ unsigned int wtot[kWarps];
     const int tid = threadIdx.x;
     const int warp = tid >> 5;
     const int lane = tid & 31;
-    run[tid] = offs[(size_t)tid * num_tiles + blockIdx.x];
+    const unsigned lt = (1u << lane) - 1u;
+    // start of digit tid's output range: exclusive prefix of the digit totals
+    const unsigned int tot = totals[tid];
+    unsigned int inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int y = __shfl_up_sync(kFull, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) wtot[warp] = inc;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0u;
     __syncthreads();
-    const unsigned lt = (1u << lane) - 1u;
+    unsigned int before = inc - tot;
+    for (int w = 0; w < warp; ++w) before += wtot[w];
+    run[tid] = before + offs[(size_t)tid * num_tiles + blockIdx.x];
+    __syncthreads();
     const long long base = (long long)blockIdx.x * kTile;
     // the tile's keys and values are loaded up front: one memory latency, not 16
     unsigned long long keys[kItems];
@@ -145,7 +164,7 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const unsigned long l
 
 size_t radix_sort_temp_bytes(long long count) {
     const long long tiles = (count + kTile - 1) / kTile;
-    return (size_t)(256 * (tiles > 0 ? tiles : 1)) * sizeof(unsigned int);
+    return (size_t)(256 * (tiles > 0 ? tiles : 1) + 256) * sizeof(unsigned int);  // + digit totals
 }
 
 cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned long long* keys_tmp, float* vals_tmp,
@@ -158,12 +177,13 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned lon
     const long long tiles = (count + kTile - 1) / kTile;
     if (temp_bytes < radix_sort_temp_bytes(count)) return cudaErrorInvalidValue;
     unsigned int* hist = static_cast<unsigned int*>(temp);
+    unsigned int* totals = hist + 256 * tiles;
     unsigned long long *ka = keys, *kb = keys_tmp;
     float *va = vals, *vb = vals_tmp;
     for (int shift = 0; shift < bits; shift += 8) {
         hist_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, count, shift, (int)tiles, hist);
-        scan_kernel<<<1, 1024, 0, s>>>(hist, 256 * tiles);
-        scatter_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, va, kb, vb, count, shift, (int)tiles, hist);
+        scan_kernel<<<256, 1024, 0, s>>>(hist, tiles, totals);
+        scatter_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, va, kb, vb, count, shift, (int)tiles, hist, totals);
         if (launches) *launches += 3;
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
