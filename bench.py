@@ -57,6 +57,9 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample budget")
     p.add_argument("--only", choices=["ba20k", "er5k"], default=None,
                    help="run one of the two graphs (for profiler captures; not a bench line)")
+    p.add_argument("--workload", choices=["config2", "batch"], default="config2",
+                   help="config2: the headline line; batch: the 2000-graph batching comparison")
+    p.add_argument("--batch-graphs", type=int, default=2000)
     return p.parse_args()
 
 
@@ -370,9 +373,77 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch_workload(args):
+    """Batching (the 2000-graph mix, k = 15): graphs/s of one persistent
+    launch per step (gumap_batch_create) against one handle and one run per
+    graph on the same GPU and stream. Prints its own JSON line."""
+    import torch
+
+    from paper_2509_19703_gb300 import graphgen as gg
+    from paper_2509_19703_gb300 import gumap
+
+    torch.cuda.set_device(0)
+    items = gg.batch_mix(count=args.batch_graphs, base_seed=4)
+    graphs = [it.graph for it in items]
+    modes = [gumap.FULL if it.mode == "full" else gumap.PARTIAL for it in items]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def timed(fn, steps):
+        ts = []
+        for s in range(steps):
+            flush.fill_(s & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    kb, _ = gumap.KnnGraph.batch(graphs, K_NEIGHBOURS, modes)
+    out = kb.alloc_outputs(kb.n)
+    for _ in range(args.warmup):
+        kb.run(out=out)
+    kb.check()
+    kb.reset_stats()
+    ms_batch = timed(lambda: kb.run(out=out), args.steps)
+    st = kb.stats()
+    kb.check()
+    kb.close()
+
+    singles = [gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=m) for g, m in zip(graphs, modes)]
+    souts = [s.alloc_outputs(g.n) for s, g in zip(singles, graphs)]
+
+    def run_all():
+        for s, o in zip(singles, souts):
+            s.run(out=o)
+
+    for _ in range(max(1, args.warmup // 2)):
+        run_all()
+    ms_single = timed(run_all, max(1, min(args.steps, 5)))
+    for s in singles:
+        s.check()
+        s.close()
+    n_total = sum(g.n for g in graphs)
+    line = {"metric": "batched graphs/s (2000-graph mix, k=15) vs one launch per graph",
+            "value": len(graphs) / (ms_batch * 1e-3), "unit": "graphs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_batch, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 bitsets / f32 weights", "data": "synthetic",
+            "config": {"workload": "config 4: 2000 seeded graphs, n log-uniform in [100, 20000], grid / BA 2..8 / "
+                                   "G(n,p) mean degree 4..40 / random tree, full or partial 50/50, k=15",
+                       "graphs": len(graphs), "vertices": n_total, "units": st["n_blocks"],
+                       "l2": "flushed (512 MB write) before each timed step"},
+            "one_launch_per_graph": {"graphs_per_s": len(graphs) / (ms_single * 1e-3), "ms_per_step": ms_single},
+            "speedup_vs_one_launch_per_graph": ms_single / ms_batch,
+            "gpu_launches": st["kernel_launches"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.impl == "reference":
+    if args.workload == "batch":
+        run_batch_workload(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -76,6 +76,7 @@ extern "C" {
 #define GUMAP_ENGINE_MSBFS    1 /* bit-parallel multi-source BFS, bitsets in global memory (L2) */
 #define GUMAP_ENGINE_MSBFS_SM 2 /* bit-parallel multi-source BFS, bitsets in one CTA's shared memory */
 #define GUMAP_ENGINE_FRONTIER 3 /* partial form only: warp per source, bounded merge of sorted rows */
+#define GUMAP_ENGINE_BATCH    4 /* batch handles: one persistent launch, one CTA per (graph, source block) */
 
 /* --------------------------------------------------------------- options */
 #define GUMAP_OPT_ENGINE      1 /* value: GUMAP_ENGINE_*                                 */
@@ -110,6 +111,35 @@ typedef struct gumap_knn gumap_knn;
  */
 int gumap_knn_create(gumap_knn **h, const int32_t *row_ptr, const int32_t *col_idx, int32_t n,
                      int64_t nnz, int32_t k, int mode, uint32_t flags, int device);
+
+/*
+ * gumap_batch_create - one handle over many independent graphs, run in one
+ * persistent launch (the method of Algorithm 1 / Algorithm 4 applied to each
+ * graph; the graphs are laid side by side as a disjoint union).
+ *
+ *   n_graphs        number of graphs, >= 1.
+ *   vertex_offsets  host int32[n_graphs + 1]: graph g owns vertices
+ *                   [vertex_offsets[g], vertex_offsets[g + 1]) of the union;
+ *                   vertex_offsets[0] = 0, strictly increasing (no empty graph).
+ *   row_ptr,col_idx host CSR of the union with global ids (every rule of
+ *                   gumap_knn_create, and no edge between two graphs).
+ *   k               1 <= k <= min(N - 1, GUMAP_MAX_K), N = vertex_offsets[n_graphs];
+ *                   a graph with fewer than k + 1 vertices gets padded rows.
+ *   modes           host int32[n_graphs]: GUMAP_FULL or GUMAP_PARTIAL per graph.
+ *   flags           GUMAP_WEIGHTS_* (the CSR must be on the host).
+ *
+ * gumap_knn_run(h, NULL, N, ...) then writes the rows of every vertex of
+ * every graph (row = global vertex id; neighbour ids are global ids), the
+ * weights and, for union weights, the COO of the union (each graph's COO is
+ * a contiguous run). Each graph's rows are identical to what a handle of
+ * that graph alone produces (after shifting ids). A graph must fit the
+ * engine's per-CTA shared memory (about 27,000 vertices); larger graphs get
+ * GUMAP_ERR_TOO_LARGE and belong in their own handle. The call synchronises
+ * once. Errors: INVALID_ARG, INVALID_GRAPH, TOO_LARGE, OOM, CUDA.
+ */
+int gumap_batch_create(gumap_knn **h, int32_t n_graphs, const int32_t *vertex_offsets, const int32_t *row_ptr,
+                       const int32_t *col_idx, int64_t nnz, int32_t k, const int32_t *modes, uint32_t flags,
+                       int device);
 
 /*
  * gumap_knn_run - compute the kNN lists and weights of a set of sources

@@ -131,6 +131,16 @@ struct gumap_knn {
     int last_block_bits = 0;
     int last_blocks = 0;
 
+    // batched engine (handles made by gumap_batch_create)
+    bool batch = false;
+    int32_t n_graphs = 0;
+    BatchUnit* d_units = nullptr;
+    int32_t n_units = 0;
+    size_t batch_smem = 0;
+    int batch_grid = 0;
+    long long vslab_words = 0;
+    DevBuf vslab;
+
     // stats
     int64_t bfs_launches = 0;
     int64_t kernel_launches = 0;
@@ -187,6 +197,7 @@ int choose_block_bits(const gumap_knn* h, int32_t n_src) {
 
 int pick_engine(const gumap_knn* h) {
     if (h->opt_engine != GUMAP_ENGINE_AUTO) return h->opt_engine;
+    if (h->batch) return GUMAP_ENGINE_BATCH;
     return h->mode == GUMAP_PARTIAL ? GUMAP_ENGINE_FRONTIER : GUMAP_ENGINE_MSBFS;
 }
 
@@ -274,6 +285,34 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
     return GUMAP_OK;
 }
 
+int run_batch(gumap_knn* h, int32_t* out_idx, uint16_t* out_dist, cudaStream_t st) {
+    BatchArgs a{};
+    a.row_ptr = h->d_rp;
+    a.col = h->d_col;
+    a.units = h->d_units;
+    a.n_units = h->n_units;
+    a.k = h->k;
+    a.out_idx = out_idx;
+    a.out_dist = out_dist;
+    a.vslab = static_cast<uint32_t*>(h->vslab.p);
+    a.vslab_words = h->vslab_words;
+    a.next_unit = &h->d_ctr->aux_count;
+    a.ctr = h->d_ctr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc;
+    if (h->opt_profile) {
+        if ((rc = next_event_pair(h, &e0, &e1))) return rc;
+        CK(cudaEventRecord(e0, st), "cudaEventRecord");
+    }
+    CK(launch_batch(a, h->batch_grid, h->batch_smem, st), "batch launch");
+    if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
+    h->bfs_launches++;
+    h->kernel_launches++;
+    h->last_block_bits = 0;
+    h->last_blocks = h->n_units;
+    return GUMAP_OK;
+}
+
 int run_frontier(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
                  cudaStream_t st) {
     FrontierArgs a{};
@@ -331,6 +370,8 @@ int gumap_knn_destroy(gumap_knn* h) {
     cudaFree(h->d_col);
     cudaFree(h->d_identity);
     cudaFree(h->d_order);
+    cudaFree(h->d_units);
+    release(h->vslab);
     cudaFree(h->d_ctr);
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
@@ -435,6 +476,109 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     return GUMAP_OK;
 }
 
+int gumap_batch_create(gumap_knn** out, int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr,
+                       const int32_t* col_idx, int64_t nnz, int32_t k, const int32_t* modes, uint32_t flags,
+                       int device) {
+    if (!out) return fail(GUMAP_ERR_INVALID_ARG, "h is NULL");
+    *out = nullptr;
+    if (n_graphs < 1 || !vertex_offsets || !modes) return fail(GUMAP_ERR_INVALID_ARG, "bad graph list");
+    if (flags & GUMAP_CSR_ON_DEVICE) return fail(GUMAP_ERR_INVALID_ARG, "batch CSR must be on the host");
+    if (vertex_offsets[0] != 0) return fail(GUMAP_ERR_INVALID_ARG, "vertex_offsets[0] != 0");
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        if (vertex_offsets[g + 1] <= vertex_offsets[g]) return fail(GUMAP_ERR_INVALID_ARG, "graph %d is empty", g);
+        if (modes[g] != GUMAP_FULL && modes[g] != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "bad mode of graph %d", g);
+    }
+    const int32_t n = vertex_offsets[n_graphs];
+    gumap_knn* h = nullptr;
+    int rc = gumap_knn_create(&h, row_ptr, col_idx, n, nnz, k, GUMAP_FULL, flags, device);
+    if (rc) return rc;
+    // no edge may leave its graph (rows are sorted: checking each row's ends suffices)
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const int32_t lo = vertex_offsets[g], hi = vertex_offsets[g + 1];
+        for (int32_t v = lo; v < hi; ++v) {
+            if (row_ptr[v + 1] > row_ptr[v] && (col_idx[row_ptr[v]] < lo || col_idx[row_ptr[v + 1] - 1] >= hi)) {
+                gumap_knn_destroy(h);
+                return fail(GUMAP_ERR_INVALID_GRAPH, "an edge of vertex %d leaves its graph %d", v, g);
+            }
+        }
+    }
+    // units: per graph, the widest source block whose bitsets fit the CTA's
+    // shared memory (all three, else frontier + next with visited in global)
+    const size_t budget = 220000;
+    std::vector<BatchUnit> units;
+    std::vector<long long> cost;
+    size_t smem = 0;
+    long long slab = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const int32_t lo = vertex_offsets[g], ng = vertex_offsets[g + 1] - lo;
+        const int32_t wmax = std::min<int32_t>(kMaxBatchW, (ng + 31) / 32);
+        int32_t W = 0, vg = 0;
+        for (int32_t w = wmax; w >= 1 && !W; --w)
+            if (4ull * (3ull * ng * w + 34ull * w) <= budget) W = w;
+        if (!W) {
+            vg = 1;
+            for (int32_t w = wmax; w >= 1 && !W; --w)
+                if (4ull * (2ull * ng * w + 34ull * w) <= budget) W = w;
+        }
+        if (!W) {
+            gumap_knn_destroy(h);
+            return fail(GUMAP_ERR_TOO_LARGE, "graph %d (%d vertices) does not fit the batched engine", g, ng);
+        }
+        const size_t need = 4ull * ((vg ? 2ull : 3ull) * ng * W + 34ull * W);
+        smem = std::max(smem, need);
+        if (vg) slab = std::max<long long>(slab, (long long)ng * W);
+        const long long edges = (long long)row_ptr[lo + ng] - row_ptr[lo];
+        for (int32_t s = 0; s < ng; s += 32 * W) {
+            BatchUnit u{};
+            u.v0 = lo;
+            u.n = ng;
+            u.s_lo = s;
+            u.nb = std::min<int32_t>(32 * W, ng - s);
+            u.W = W;
+            u.partial = modes[g] == GUMAP_PARTIAL ? 1 : 0;
+            u.v_global = vg;
+            units.push_back(u);
+            cost.push_back((edges + ng) * W);
+        }
+    }
+    // longest units first, so the queue's tail is made of short ones
+    std::vector<size_t> ord(units.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    std::vector<BatchUnit> sorted(units.size());
+    for (size_t i = 0; i < ord.size(); ++i) sorted[i] = units[ord[i]];
+    cudaError_t e;
+    if ((e = batch_prepare(smem)) != cudaSuccess) {
+        gumap_knn_destroy(h);
+        return cuda_fail(e, "batch kernel attributes");
+    }
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_ptr(), batch_threads(), smem)) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        gumap_knn_destroy(h);
+        return e != cudaSuccess ? cuda_fail(e, "batch occupancy") : fail(GUMAP_ERR_CUDA, "batch kernel cannot be resident");
+    }
+    h->batch_grid = h->num_sms * per_sm;
+    h->batch_smem = smem;
+    h->vslab_words = slab;
+    if (slab > 0 && (rc = ensure(h->vslab, (size_t)slab * 4 * h->batch_grid, "batch slab"))) {
+        gumap_knn_destroy(h);
+        return rc;
+    }
+    if ((e = cudaMalloc(&h->d_units, sizeof(BatchUnit) * sorted.size())) != cudaSuccess ||
+        (e = cudaMemcpy(h->d_units, sorted.data(), sizeof(BatchUnit) * sorted.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess) {
+        gumap_knn_destroy(h);
+        return cuda_fail(e, "batch units");
+    }
+    h->n_units = (int32_t)sorted.size();
+    h->batch = true;
+    h->n_graphs = n_graphs;
+    *out = h;
+    return GUMAP_OK;
+}
+
 int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
                   float* out_w, void* stream) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
@@ -468,6 +612,9 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
     } else if (engine == GUMAP_ENGINE_FRONTIER) {
         if (h->mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
         rc = run_frontier(h, src, n_src, out_idx, out_dist, st);
+    } else if (engine == GUMAP_ENGINE_BATCH) {
+        if (!h->batch || sources) return fail(GUMAP_ERR_INVALID_ARG, "the batched engine needs a batch handle and sources == NULL");
+        rc = run_batch(h, out_idx, out_dist, st);
     } else {
         return fail(GUMAP_ERR_INVALID_ARG, "engine %d not available", engine);
     }
@@ -540,7 +687,10 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
     switch (option) {
         case GUMAP_OPT_ENGINE:
-            if (value < GUMAP_ENGINE_AUTO || value > GUMAP_ENGINE_FRONTIER) return fail(GUMAP_ERR_INVALID_ARG, "bad engine");
+            if (value < GUMAP_ENGINE_AUTO || value > GUMAP_ENGINE_BATCH || value == GUMAP_ENGINE_MSBFS_SM)
+                return fail(GUMAP_ERR_INVALID_ARG, "bad engine");
+            if (value == GUMAP_ENGINE_BATCH && !h->batch)
+                return fail(GUMAP_ERR_INVALID_ARG, "the batched engine needs a handle from gumap_batch_create");
             if (value == GUMAP_ENGINE_FRONTIER && h->mode != GUMAP_PARTIAL)
                 return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
             h->opt_engine = (int)value;

@@ -81,6 +81,40 @@ struct FrontierArgs {
     int32_t* status;         // set to kStatusBadSource for a source outside [0, n)
 };
 
+// One unit of the batched engine: a block of sources of one graph of the
+// batch (a disjoint union; the graph occupies vertices [v0, v0 + n)).
+constexpr int kMaxBatchW = 64;  // at most 64 words (2048 sources) per unit
+struct BatchUnit {
+    int32_t v0;        // first vertex of the graph
+    int32_t n;         // vertices of the graph
+    int32_t s_lo;      // first source of the unit (graph-local id)
+    int32_t nb;        // sources in the unit (<= 32 * W)
+    int32_t W;         // words per bitset row
+    int32_t partial;   // 1: partial form for this graph
+    int32_t v_global;  // 1: visited bitset in the CTA's global slab
+    int32_t pad;
+};
+
+struct BatchArgs {
+    const int32_t* row_ptr;  // CSR of the disjoint union (global ids)
+    const int32_t* col;
+    const BatchUnit* units;
+    int32_t n_units;
+    int32_t k;
+    int32_t* out_idx;        // [N][k], row = global vertex id
+    uint16_t* out_dist;
+    uint32_t* vslab;         // per CTA: vslab + blockIdx.x * vslab_words
+    long long vslab_words;
+    int32_t* next_unit;      // work-queue counter, zeroed before the launch
+    DeviceCounters* ctr;
+};
+
+// ---- batch.cu
+cudaError_t batch_prepare(size_t smem_bytes);
+int batch_threads();
+const void* batch_kernel_ptr();
+cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem_bytes, cudaStream_t s);
+
 // ---- msbfs.cu
 int msbfs_max_blocks_per_sm(int block_threads);
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);

@@ -21,7 +21,7 @@ from . import _build
 # modes, flags, engines, options (mirror include/gumap.h)
 FULL, PARTIAL = 0, 1
 WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE = 0x0, 0x1, 0x2
-ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER = 0, 1, 2, 3
+ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER, ENGINE_BATCH = 0, 1, 2, 3, 4
 OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
 MAX_K = 256
 DIST_INF = 0xFFFF
@@ -74,6 +74,7 @@ def load():
                 "gumap_knn_reset_stats": [vp],
                 "gumap_knn_destroy": [vp],
                 "gumap_knn_run_noalloc": [vp, vp, i32, i64, i32, ctypes.c_int, vp, vp, vp, vp],
+                "gumap_batch_create": [ctypes.POINTER(vp), i32, vp, vp, vp, i64, i32, vp, u32, ctypes.c_int],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -139,6 +140,20 @@ def gumap_knn_create(row_ptr, col_idx, n: int, nnz: int, k: int, mode: int = FUL
     h = ctypes.c_void_p()
     _check(lib.gumap_knn_create(ctypes.byref(h), rp, col, int(n), int(nnz), int(k), int(mode), int(flags),
                                 int(device)), "gumap_knn_create")
+    return h
+
+
+def gumap_batch_create(n_graphs: int, vertex_offsets, row_ptr, col_idx, nnz: int, k: int, modes, flags: int = 0,
+                       device: int = 0):
+    """Handle over many graphs laid side by side (host arrays, global ids)."""
+    offs = np.ascontiguousarray(vertex_offsets, dtype=np.int32)
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col_idx, dtype=np.int32)
+    md = np.ascontiguousarray(modes, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().gumap_batch_create(ctypes.byref(h), int(n_graphs), offs.ctypes.data, rp.ctypes.data,
+                                     col.ctypes.data if col.size else None, int(nnz), int(k), md.ctypes.data,
+                                     int(flags), int(device)), "gumap_batch_create")
     return h
 
 
@@ -217,6 +232,26 @@ class KnnGraph:
     @classmethod
     def from_graph(cls, g, k: int, mode: int = FULL, flags: int = 0, device: int = 0):
         return cls(g.row_ptr, g.col, k, mode, flags, device, n=g.n)
+
+    @classmethod
+    def batch(cls, graphs, k: int, modes, flags: int = 0, device: int = 0):
+        """One handle over many graphs (gumap_batch_create). Rows of the
+        result are the vertices of all graphs in order; ids are global
+        (graph g's vertex v is offsets[g] + v). Returns (handle, offsets)."""
+        offs = np.zeros(len(graphs) + 1, dtype=np.int64)
+        rps, cols, eoff = [], [], 0
+        for i, g in enumerate(graphs):
+            offs[i + 1] = offs[i] + g.n
+            rps.append(g.row_ptr[:-1].astype(np.int64) + eoff)
+            cols.append(g.col.astype(np.int64) + offs[i])
+            eoff += g.nnz
+        rp = np.concatenate(rps + [np.array([eoff])]).astype(np.int32)
+        col = np.concatenate(cols).astype(np.int32) if eoff else np.zeros(0, np.int32)
+        self = cls.__new__(cls)
+        self.n, self.k, self.mode, self.flags, self.device = int(offs[-1]), k, FULL, flags, device
+        self.h = gumap_batch_create(len(graphs), offs.astype(np.int32), rp, col, int(eoff), k,
+                                    np.asarray(modes, dtype=np.int32), flags, device)
+        return self, offs
 
     def set_option(self, option: int, value: int):
         gumap_knn_set_option(self.h, option, value)
