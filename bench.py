@@ -57,9 +57,13 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample budget")
     p.add_argument("--only", choices=["ba20k", "er5k"], default=None,
                    help="run one of the two graphs (for profiler captures; not a bench line)")
-    p.add_argument("--workload", choices=["config2", "batch"], default="config2",
-                   help="config2: the headline line; batch: the 2000-graph batching comparison")
+    p.add_argument("--workload", choices=["config2", "batch", "serve"], default="config2",
+                   help="config2: the headline line; batch: the 2000-graph batching comparison; "
+                        "serve: the request-stream latency sweep")
     p.add_argument("--batch-graphs", type=int, default=2000)
+    p.add_argument("--serve-requests", type=int, default=1000)
+    p.add_argument("--serve-n-cap", type=int, default=200000)
+    p.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 0.9])
     return p.parse_args()
 
 
@@ -439,9 +443,118 @@ def run_batch_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def serve_requests(count, seed, n_cap):
+    """Config 5 request stream: n lognormal (median 5000, sigma_ln 1.0) clamped
+    to [64, n_cap]; BA (4 edges per vertex) / grid / G(n, p) (mean degree 10)
+    in thirds; 70 % partial, 30 % full; k uniform in {15, 30}."""
+    import math
+
+    from paper_2509_19703_gb300 import graphgen as gg
+    u = gg.uniform(seed, 5 * count)
+    out = []
+    for i in range(count):
+        u1, u2, u3, u4, u5 = u[5 * i:5 * i + 5]
+        z = math.sqrt(-2.0 * math.log(max(u1, 1e-300))) * math.cos(2.0 * math.pi * u2)  # Box-Muller
+        n = int(min(max(5000.0 * math.exp(z), 64), n_cap))
+        kind = min(int(u3 * 3), 2)
+        s = seed * 10**6 + i
+        if kind == 0:
+            g = gg.barabasi_albert(n, 4, s)
+        elif kind == 1:
+            w = max(2, int(round(math.sqrt(n))))
+            g = gg.grid(w, max(2, int(round(n / w))))
+        else:
+            g = gg.gnp(n, min(1.0, 10.0 / n), s)
+        k = 15 if u4 < 0.5 else 30
+        out.append((g, min(k, g.n - 1), 1 if u5 < 0.7 else 0))  # 1 = partial
+    return out
+
+
+def run_serve_workload(args):
+    """Serving: a Poisson stream of config-5 requests through gumap_server_*;
+    saturated graphs/s, then p50/p99 latency (submit to completion, server
+    clock) at offered rates below saturation; against the same requests run
+    one handle at a time."""
+    import numpy as np
+    import torch
+
+    from paper_2509_19703_gb300 import graphgen as gg
+    from paper_2509_19703_gb300 import gumap
+
+    torch.cuda.set_device(0)
+    reqs = serve_requests(args.serve_requests, 5, args.serve_n_cap)
+    budget = 64 << 30
+
+    def run_stream(rate):
+        s = gumap.gumap_server_create(0, budget)
+        rng = np.random.default_rng(55)
+        gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+        ids = []
+        t_start = time.perf_counter()
+        t_next = t_start
+        for (g, k, m), gap in zip(reqs, gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                pass
+            while True:
+                try:
+                    ids.append(gumap.gumap_serve_submit(s, g.row_ptr, g.col, g.n, g.nnz, k, m))
+                    break
+                except gumap.GumapError as e:
+                    if e.status != gumap.ERR_AGAIN:
+                        raise
+                    time.sleep(0.0005)
+        lat, t_first, t_last, batched = [], None, 0.0, []
+        for rid in ids:
+            st, r = gumap.gumap_serve_wait(s, rid, 600.0)
+            assert st == gumap.OK, gumap.gumap_status_string(st)
+            lat.append(r["t_done"] - r["t_submit"])
+            t_first = r["t_submit"] if t_first is None else min(t_first, r["t_submit"])
+            t_last = max(t_last, r["t_done"])
+            batched.append(r["batch_graphs"])
+            gumap.gumap_serve_release(s, rid)
+        stats = gumap.gumap_server_get_stats(s)
+        gumap.gumap_server_destroy(s)
+        lat = np.array(lat)
+        return {"graphs_per_s": len(ids) / (t_last - t_first), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3), "launches": stats["launches"],
+                "mean_graphs_per_launch": float(np.mean(batched)),
+                "arena_peak_gb": stats["arena_peak_bytes"] / 2**30}
+
+    run_stream(0)  # warm-up (module loading, allocator)
+    sat = run_stream(0)
+    points = []
+    for frac in args.serve_rates:
+        p = run_stream(frac * sat["graphs_per_s"])
+        p["offered_rate_frac"] = frac
+        points.append(p)
+
+    # baseline: the same requests, one handle and one synchronous run each
+    t0 = time.perf_counter()
+    for g, k, m in reqs:
+        with gumap.KnnGraph.from_graph(g, k, mode=m) as kg:
+            kg.run()
+            kg.check()
+    single = len(reqs) / (time.perf_counter() - t0)
+    line = {"metric": "served graphs/s with p50/p99 latency (config-5 request stream)",
+            "value": sat["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1, "steps": len(reqs), "warmup": 1,
+            "ms_per_step": 1e3 / sat["graphs_per_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 bitsets / f32 weights", "data": "synthetic",
+            "config": {"workload": "config 5: Poisson stream, n lognormal median 5000 sigma_ln 1.0 clamped "
+                                   f"[64, {args.serve_n_cap}], BA/grid/G(n,p) thirds, 70% partial / 30% full, "
+                                   "k in {15, 30}, 64 GiB budget", "requests": len(reqs),
+                       "vertices": int(sum(g.n for g, _, _ in reqs))},
+            "saturated": sat, "latency_sweep": points,
+            "one_handle_per_request_graphs_per_s": single,
+            "speedup_vs_one_handle_per_request": sat["graphs_per_s"] / single}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
-    if args.workload == "batch":
+    if args.workload == "serve":
+        run_serve_workload(args)
+    elif args.workload == "batch":
         run_batch_workload(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -258,6 +258,85 @@ int gumap_knn_destroy(gumap_knn *h);
 int gumap_knn_run_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int64_t nnz, int32_t k,
                           int mode, int32_t *out_idx, uint16_t *out_dist, int32_t *status_out, void *stream);
 
+/* ------------------------------------------------------------ serving -- */
+/*
+ * A server computes the same rows as gumap_knn_run (kNN lists of every vertex
+ * and their weights, Algorithm 1 / Algorithm 4, Section 2.1) for a stream of
+ * independent graph requests. A native scheduler thread admits requests
+ * while their device memory fits a fixed budget (one arena allocated at
+ * creation, so nothing is allocated while serving), groups waiting small
+ * graphs of equal k into one batched launch (gumap_batch_create's engine),
+ * runs large graphs alone, and keeps several launches in flight on separate
+ * streams, so requests that arrive while others run are admitted as soon as
+ * a stream and memory free up and their work overlaps on the device. Results
+ * stay resident in the arena until released. All calls are thread-safe.
+ */
+typedef struct gumap_server gumap_server;
+
+typedef struct {
+    int32_t n_streams;          /* launches in flight at once (default 4)                      */
+    int32_t max_batch_graphs;   /* graphs per batched launch (default 512)                     */
+    int64_t max_batch_vertices; /* vertices per batched launch (default 4,000,000)             */
+    int32_t max_queue;          /* waiting requests beyond which submit returns AGAIN (65536)  */
+    int64_t staging_bytes;      /* pinned host staging for uploads (default 512 MiB)            */
+    uint32_t flags;             /* GUMAP_WEIGHTS_* applied to every request (default union)    */
+} gumap_server_opts;
+
+typedef struct {
+    int32_t status;             /* GUMAP_OK, GUMAP_PENDING or the request's error              */
+    int32_t n, k;
+    const int32_t *idx;         /* device int32[n][k], ids local to the request's graph        */
+    const uint16_t *dist;       /* device uint16[n][k]                                          */
+    const float *w;             /* device float[n][k]                                           */
+    double t_submit, t_start, t_done; /* seconds on the server clock (gumap_server_clock)      */
+    int32_t batch_graphs;       /* requests that shared this request's launch                   */
+    int32_t engine;             /* GUMAP_ENGINE_* that ran it                                   */
+} gumap_result;
+
+typedef struct {
+    int64_t submitted, completed, failed, released, launches, pending, running;
+    int64_t arena_bytes, arena_used_bytes, arena_peak_bytes;
+} gumap_server_stats;
+
+/*
+ * gumap_server_create - start a server on `device` whose requests may hold
+ * at most hbm_budget_bytes of device memory (allocated once, here).
+ * opts may be NULL (defaults). Errors: INVALID_ARG, OOM, CUDA.
+ */
+int gumap_server_create(gumap_server **s, int device, uint64_t hbm_budget_bytes, const gumap_server_opts *opts);
+
+/*
+ * gumap_serve_submit - queue one graph (host CSR obeying the gumap_knn_create
+ * rules; validated and copied before returning, so the caller may free it).
+ * k and mode as for gumap_knn_create. Non-blocking. Errors: INVALID_ARG,
+ * INVALID_GRAPH, AGAIN (queue full: retry), TOO_LARGE (the request alone can
+ * never fit the budget).
+ */
+int gumap_serve_submit(gumap_server *s, const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int64_t nnz,
+                       int32_t k, int mode, uint64_t *req_id);
+
+/* gumap_serve_poll - GUMAP_PENDING, GUMAP_OK (out filled) or an error; non-blocking. */
+int gumap_serve_poll(gumap_server *s, uint64_t req_id, gumap_result *out);
+
+/* gumap_serve_wait - like poll, but blocks up to timeout_s seconds (GUMAP_PENDING if still running). */
+int gumap_serve_wait(gumap_server *s, uint64_t req_id, gumap_result *out, double timeout_s);
+
+/* gumap_serve_read - copy a finished request's rows into caller buffers (device or host memory;
+ * any may be NULL) on `stream`, asynchronously. Errors: UNKNOWN_REQUEST, PENDING, the request's error. */
+int gumap_serve_read(gumap_server *s, uint64_t req_id, int32_t *idx, uint16_t *dist, float *w, void *stream);
+
+/* gumap_serve_release - the request's result may be dropped; its memory returns to the budget once
+ * every request of its launch is released. Errors: UNKNOWN_REQUEST. */
+int gumap_serve_release(gumap_server *s, uint64_t req_id);
+
+/* Seconds since the server started (the clock of gumap_result's timestamps). */
+double gumap_server_clock(gumap_server *s);
+
+int gumap_server_get_stats(gumap_server *s, gumap_server_stats *out);
+
+/* gumap_server_destroy - stop the scheduler (finishing launched work), free everything. NULL allowed. */
+int gumap_server_destroy(gumap_server *s);
+
 /* Static string for a status code (never NULL). */
 const char *gumap_status_string(int status);
 

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libgumap.so")
 
 SOURCES = ["gumap_capi.cu", "msbfs.cu", "frontier.cu", "weights.cu", "sort.cu", "validate.cu", "noalloc.cu",
-           "batch.cu"]
+           "batch.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
-        "-Xlinker", "-rpath," + _cuda_lib_dir(nvcc)]
+        "-lpthread", "-Xlinker", "-rpath," + _cuda_lib_dir(nvcc)]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")

@@ -58,8 +58,10 @@ int key_bits_for(int32_t n) {
     return b;
 }
 
+}  // namespace
+
 // Host-side CSR validation (same rules as the device validator).
-bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, std::string& why) {
+bool gumap::host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, std::string& why) {
     if (rp[0] != 0) { why = "row_ptr[0] != 0"; return false; }
     if ((int64_t)rp[n] != nnz) { why = "row_ptr[n] != nnz"; return false; }
     for (int32_t u = 0; u < n; ++u)
@@ -80,6 +82,57 @@ bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, 
     }
     return true;
 }
+
+// Units of the batched engine for graphs laid side by side: per graph, the
+// widest source block whose bitsets fit a CTA's shared memory (all three,
+// else frontier + next with the visited bitset in a global slab), ordered
+// longest first so the work queue's tail is short. Returns -1, or the index
+// of a graph too large for the engine.
+int32_t gumap::plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr,
+                          const int32_t* modes, std::vector<BatchUnit>& units_out, size_t& smem,
+                          long long& slab) {
+    std::vector<BatchUnit> units;
+    std::vector<long long> cost;
+    smem = 0;
+    slab = 0;
+    for (int32_t g = 0; g < n_graphs; ++g) {
+        const int32_t lo = vertex_offsets[g], ng = vertex_offsets[g + 1] - lo;
+        const int32_t wmax = std::min<int32_t>(kMaxBatchW, (ng + 31) / 32);
+        int32_t W = 0, vg = 0;
+        for (int32_t w = wmax; w >= 1 && !W; --w)
+            if (4ull * (3ull * ng * w + 34ull * w) <= kBatchSmemBudget) W = w;
+        if (!W) {
+            vg = 1;
+            for (int32_t w = wmax; w >= 1 && !W; --w)
+                if (4ull * (2ull * ng * w + 34ull * w) <= kBatchSmemBudget) W = w;
+        }
+        if (!W) return g;
+        const size_t need = 4ull * ((vg ? 2ull : 3ull) * ng * W + 34ull * W);
+        smem = std::max(smem, need);
+        if (vg) slab = std::max<long long>(slab, (long long)ng * W);
+        const long long edges = (long long)row_ptr[lo + ng] - row_ptr[lo];
+        for (int32_t s = 0; s < ng; s += 32 * W) {
+            BatchUnit u{};
+            u.v0 = lo;
+            u.n = ng;
+            u.s_lo = s;
+            u.nb = std::min<int32_t>(32 * W, ng - s);
+            u.W = W;
+            u.partial = modes[g] == GUMAP_PARTIAL ? 1 : 0;
+            u.v_global = vg;
+            units.push_back(u);
+            cost.push_back((edges + ng) * W);
+        }
+    }
+    std::vector<size_t> ord(units.size());
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    units_out.resize(units.size());
+    for (size_t i = 0; i < ord.size(); ++i) units_out[i] = units[ord[i]];
+    return -1;
+}
+
+namespace {
 
 struct DevBuf {
     void* p = nullptr;
@@ -502,51 +555,15 @@ int gumap_batch_create(gumap_knn** out, int32_t n_graphs, const int32_t* vertex_
             }
         }
     }
-    // units: per graph, the widest source block whose bitsets fit the CTA's
-    // shared memory (all three, else frontier + next with visited in global)
-    const size_t budget = 220000;
-    std::vector<BatchUnit> units;
-    std::vector<long long> cost;
+    std::vector<BatchUnit> sorted;
     size_t smem = 0;
     long long slab = 0;
-    for (int32_t g = 0; g < n_graphs; ++g) {
-        const int32_t lo = vertex_offsets[g], ng = vertex_offsets[g + 1] - lo;
-        const int32_t wmax = std::min<int32_t>(kMaxBatchW, (ng + 31) / 32);
-        int32_t W = 0, vg = 0;
-        for (int32_t w = wmax; w >= 1 && !W; --w)
-            if (4ull * (3ull * ng * w + 34ull * w) <= budget) W = w;
-        if (!W) {
-            vg = 1;
-            for (int32_t w = wmax; w >= 1 && !W; --w)
-                if (4ull * (2ull * ng * w + 34ull * w) <= budget) W = w;
-        }
-        if (!W) {
-            gumap_knn_destroy(h);
-            return fail(GUMAP_ERR_TOO_LARGE, "graph %d (%d vertices) does not fit the batched engine", g, ng);
-        }
-        const size_t need = 4ull * ((vg ? 2ull : 3ull) * ng * W + 34ull * W);
-        smem = std::max(smem, need);
-        if (vg) slab = std::max<long long>(slab, (long long)ng * W);
-        const long long edges = (long long)row_ptr[lo + ng] - row_ptr[lo];
-        for (int32_t s = 0; s < ng; s += 32 * W) {
-            BatchUnit u{};
-            u.v0 = lo;
-            u.n = ng;
-            u.s_lo = s;
-            u.nb = std::min<int32_t>(32 * W, ng - s);
-            u.W = W;
-            u.partial = modes[g] == GUMAP_PARTIAL ? 1 : 0;
-            u.v_global = vg;
-            units.push_back(u);
-            cost.push_back((edges + ng) * W);
-        }
+    const int32_t big = plan_batch(n_graphs, vertex_offsets, row_ptr, modes, sorted, smem, slab);
+    if (big >= 0) {
+        gumap_knn_destroy(h);
+        return fail(GUMAP_ERR_TOO_LARGE, "graph %d (%d vertices) does not fit the batched engine", big,
+                    vertex_offsets[big + 1] - vertex_offsets[big]);
     }
-    // longest units first, so the queue's tail is made of short ones
-    std::vector<size_t> ord(units.size());
-    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
-    std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
-    std::vector<BatchUnit> sorted(units.size());
-    for (size_t i = 0; i < ord.size(); ++i) sorted[i] = units[ord[i]];
     cudaError_t e;
     if ((e = batch_prepare(smem)) != cudaSuccess) {
         gumap_knn_destroy(h);

@@ -3,6 +3,9 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
+#include <vector>
+
 #include <cuda_runtime.h>
 
 namespace gumap {
@@ -108,6 +111,15 @@ struct BatchArgs {
     int32_t* next_unit;      // work-queue counter, zeroed before the launch
     DeviceCounters* ctr;
 };
+
+// Shared-memory bytes a batched unit may use (the rest of the 227 KB holds
+// the kernel's static shared arrays).
+constexpr size_t kBatchSmemBudget = 220000;
+
+// ---- gumap_capi.cu (host helpers shared with the server)
+bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, std::string& why);
+int32_t plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr, const int32_t* modes,
+                   std::vector<BatchUnit>& units, size_t& smem, long long& slab);
 
 // ---- batch.cu
 cudaError_t batch_prepare(size_t smem_bytes);

@@ -48,6 +48,25 @@ class _Stats(ctypes.Structure):
                 ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double)]
 
 
+class _ServerOpts(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_int32), ("max_batch_graphs", ctypes.c_int32),
+                ("max_batch_vertices", ctypes.c_int64), ("max_queue", ctypes.c_int32),
+                ("staging_bytes", ctypes.c_int64), ("flags", ctypes.c_uint32)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("n", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("idx", ctypes.c_void_p), ("dist", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("batch_graphs", ctypes.c_int32), ("engine", ctypes.c_int32)]
+
+
+class _ServerStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "failed", "released", "launches",
+                                              "pending", "running", "arena_bytes", "arena_used_bytes",
+                                              "arena_peak_bytes")]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -75,6 +94,15 @@ def load():
                 "gumap_knn_destroy": [vp],
                 "gumap_knn_run_noalloc": [vp, vp, i32, i64, i32, ctypes.c_int, vp, vp, vp, vp],
                 "gumap_batch_create": [ctypes.POINTER(vp), i32, vp, vp, vp, i64, i32, vp, u32, ctypes.c_int],
+                "gumap_server_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_uint64,
+                                        ctypes.POINTER(_ServerOpts)],
+                "gumap_serve_submit": [vp, vp, vp, i32, i64, i32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
+                "gumap_serve_poll": [vp, ctypes.c_uint64, ctypes.POINTER(_Result)],
+                "gumap_serve_wait": [vp, ctypes.c_uint64, ctypes.POINTER(_Result), ctypes.c_double],
+                "gumap_serve_read": [vp, ctypes.c_uint64, vp, vp, vp, vp],
+                "gumap_serve_release": [vp, ctypes.c_uint64],
+                "gumap_server_get_stats": [vp, ctypes.POINTER(_ServerStats)],
+                "gumap_server_destroy": [vp],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -84,6 +112,8 @@ def load():
             lib.gumap_status_string.restype = ctypes.c_char_p
             lib.gumap_last_error.argtypes = []
             lib.gumap_last_error.restype = ctypes.c_char_p
+            lib.gumap_server_clock.argtypes = [vp]
+            lib.gumap_server_clock.restype = ctypes.c_double
             _lib = lib
     return _lib
 
@@ -209,6 +239,74 @@ def gumap_knn_run_noalloc(row_ptr, col_idx, n: int, nnz: int, k: int, mode: int,
                                         int(n), int(nnz), int(k), int(mode), _dptr(out_idx, torch.int32, "out_idx"),
                                         _dptr(out_dist, torch.int16, "out_dist"), _dptr(status, torch.int32, "status"),
                                         _stream(stream)), "gumap_knn_run_noalloc")
+
+
+# ---------------------------------------------------------------- serving
+
+def gumap_server_create(device: int = 0, hbm_budget_bytes: int = 64 << 30, **opts):
+    o = _ServerOpts(n_streams=opts.get("n_streams", 0), max_batch_graphs=opts.get("max_batch_graphs", 0),
+                    max_batch_vertices=opts.get("max_batch_vertices", 0), max_queue=opts.get("max_queue", 0),
+                    staging_bytes=opts.get("staging_bytes", 0), flags=opts.get("flags", 0))
+    s = ctypes.c_void_p()
+    _check(load().gumap_server_create(ctypes.byref(s), int(device), int(hbm_budget_bytes), ctypes.byref(o)),
+           "gumap_server_create")
+    return s
+
+
+def gumap_serve_submit(s, row_ptr, col_idx, n: int, nnz: int, k: int, mode: int = PARTIAL) -> int:
+    """Queue one graph (host arrays, copied before return); returns the request id.
+    Raises GumapError with status ERR_AGAIN when the queue is full."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col_idx, dtype=np.int32)
+    rid = ctypes.c_uint64()
+    _check(load().gumap_serve_submit(s, rp.ctypes.data, col.ctypes.data if col.size else None, int(n), int(nnz),
+                                     int(k), int(mode), ctypes.byref(rid)), "gumap_serve_submit")
+    return int(rid.value)
+
+
+def _result_dict(r: _Result) -> dict:
+    return {f: getattr(r, f) for f, _ in _Result._fields_}
+
+
+def gumap_serve_poll(s, req_id: int):
+    """(status, result dict); status is OK, PENDING or the request's error."""
+    r = _Result()
+    st = load().gumap_serve_poll(s, int(req_id), ctypes.byref(r))
+    if st not in (OK, PENDING) and st == ERR_UNKNOWN_REQUEST:
+        _check(st, "gumap_serve_poll")
+    return st, _result_dict(r)
+
+
+def gumap_serve_wait(s, req_id: int, timeout_s: float = 60.0):
+    r = _Result()
+    st = load().gumap_serve_wait(s, int(req_id), ctypes.byref(r), float(timeout_s))
+    if st == ERR_UNKNOWN_REQUEST:
+        _check(st, "gumap_serve_wait")
+    return st, _result_dict(r)
+
+
+def gumap_serve_read(s, req_id: int, idx=None, dist=None, w=None, stream=None):
+    """Copy a finished request's rows into CUDA tensors (int32 / int16 / float32, [n, k])."""
+    _check(load().gumap_serve_read(s, int(req_id), _dptr(idx, torch.int32, "idx"), _dptr(dist, torch.int16, "dist"),
+                                   _dptr(w, torch.float32, "w"), _stream(stream)), "gumap_serve_read")
+
+
+def gumap_serve_release(s, req_id: int):
+    _check(load().gumap_serve_release(s, int(req_id)), "gumap_serve_release")
+
+
+def gumap_server_clock(s) -> float:
+    return float(load().gumap_server_clock(s))
+
+
+def gumap_server_get_stats(s) -> dict:
+    st = _ServerStats()
+    _check(load().gumap_server_get_stats(s, ctypes.byref(st)), "gumap_server_get_stats")
+    return {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+
+
+def gumap_server_destroy(s):
+    _check(load().gumap_server_destroy(s), "gumap_server_destroy")
 
 
 # ---------------------------------------------------------------- wrapper
