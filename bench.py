@@ -72,6 +72,23 @@ def dist_info():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(ms: float, world: int, device: str = "cpu") -> float:
+    """The step time of the whole job: the slowest rank's (replicas run the
+    same step on every GPU; the value counts the work of all ranks)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(work_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job GTEPS: every rank's work over the slowest rank's time."""
+    return world * work_per_rank / (ms * 1e-3) / 1e9
+
+
 def build_graphs(only=None):
     from paper_2509_19703_gb300 import graphgen as gg
     makers = {"ba20k": gg.config_ba20k, "er5k": gg.config_er5k}
@@ -291,14 +308,11 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, device="cuda")
     for kg in kgs:
         kg.check()
     stats = [kg.stats() for kg in kgs]
-    value = world * work_per_step / (ms * 1e-3) / 1e9
+    value = job_value(work_per_step, world, ms)
 
     # roofline of the dominant kernel (the MS-BFS launches)
     alg = sum(msbfs_alg_bytes(g, st["block_bits"], st["bfs_level_sum"], st["bfs_launches"])

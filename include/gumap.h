@@ -337,6 +337,16 @@ int gumap_server_get_stats(gumap_server *s, gumap_server_stats *out);
 /* gumap_server_destroy - stop the scheduler (finishing launched work), free everything. NULL allowed. */
 int gumap_server_destroy(gumap_server *s);
 
+/*
+ * gumap_selftest_wait_timeout - check that a device-side wait of this library
+ * gives up instead of hanging: launches the grid barrier of the multi-source
+ * BFS with one CTA that never arrives and a limit of limit_s seconds
+ * (1 ms .. 5 s), waits, and returns the status the waiting CTAs recorded:
+ * GUMAP_ERR_TIMEOUT when the mechanism works. The context stays usable.
+ * Synchronous. (Failure handling of the library, not a step of the paper.)
+ */
+int gumap_selftest_wait_timeout(int device, double limit_s);
+
 /* Static string for a status code (never NULL). */
 const char *gumap_status_string(int status);
 

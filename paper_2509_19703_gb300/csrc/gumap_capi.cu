@@ -666,6 +666,26 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
     return GUMAP_OK;
 }
 
+int gumap_selftest_wait_timeout(int device, double limit_s) {
+    if (!(limit_s >= 1e-3 && limit_s <= 5.0)) return fail(GUMAP_ERR_INVALID_ARG, "limit must be in [1 ms, 5 s]");
+    CK(cudaSetDevice(device), "cudaSetDevice");
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
+    void* buf = nullptr;
+    CK(cudaMalloc(&buf, 64), "cudaMalloc");
+    GridBarrier* bar = static_cast<GridBarrier*>(buf);
+    int32_t* status = reinterpret_cast<int32_t*>(static_cast<char*>(buf) + 32);
+    cudaError_t e = cudaMemset(buf, 0, 64);
+    if (e == cudaSuccess)
+        e = launch_barrier_selftest(bar, status, (unsigned long long)(limit_s * 1e9), sms, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int32_t st = -1;
+    if (e == cudaSuccess) e = cudaMemcpy(&st, status, sizeof(st), cudaMemcpyDeviceToHost);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    return st == 0 ? fail(GUMAP_ERR_CUDA, "the bounded wait completed although it could not") : st;
+}
+
 int gumap_knn_rho_sigma(gumap_knn* h, float* rho, float* sigma, void* stream) {
     if (!h || h->last_n_src < 0) return fail(GUMAP_ERR_INVALID_ARG, "no run yet");
     if (h->last_n_src == 0) return GUMAP_OK;

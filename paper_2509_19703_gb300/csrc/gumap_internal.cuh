@@ -131,6 +131,8 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem_bytes, cudaSt
 int msbfs_max_blocks_per_sm(int block_threads);
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);
 cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s);
+cudaError_t launch_barrier_selftest(GridBarrier* bar, int32_t* status, unsigned long long limit_ns, int grid,
+                                    cudaStream_t s);
 
 // ---- frontier.cu
 cudaError_t launch_frontier(const FrontierArgs& a, cudaStream_t s);

@@ -66,9 +66,9 @@ __device__ __forceinline__ unsigned ld_volatile_u32(const uint32_t* p) {
 
 // Grid-wide barrier for a cooperative launch. Thread 0 of each CTA arrives
 // on a counter; the last arrival bumps the generation. Waiters poll the
-// generation for at most kWaitLimitNs, then record a timeout and return
-// false (every later barrier of that CTA is skipped by the caller).
-__device__ bool grid_barrier(GridBarrier* bar, int32_t* status) {
+// generation for at most limit_ns, then record a timeout and return false
+// (every later barrier of that CTA is skipped by the caller).
+__device__ bool grid_barrier(GridBarrier* bar, int32_t* status, unsigned long long limit_ns = kWaitLimitNs) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -84,7 +84,7 @@ __device__ bool grid_barrier(GridBarrier* bar, int32_t* status) {
         } else {
             unsigned long long t0 = globaltimer_ns();
             while (ld_acquire_u32(&bar->gen) == gen0) {
-                if (globaltimer_ns() - t0 > kWaitLimitNs) {
+                if (globaltimer_ns() - t0 > limit_ns) {
                     atomicExch(status, kStatusTimeout);
                     ok = 0;
                     break;
@@ -395,6 +395,15 @@ __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
     }
 }
 
+// Self-test of the bounded wait: every CTA but `absent` enters the grid
+// barrier, which therefore can never complete; the waiters must give up
+// after limit_ns and record kStatusTimeout. No fault, no trap, no hang.
+__global__ void barrier_selftest_kernel(GridBarrier* bar, int32_t* status, unsigned long long limit_ns,
+                                        int absent) {
+    if ((int)blockIdx.x == absent) return;
+    grid_barrier(bar, status, limit_ns);
+}
+
 __global__ void identity_kernel(int32_t* dst, int32_t n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -414,6 +423,13 @@ cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s
     MsbfsArgs copy = a;
     void* params[] = {&copy};
     return cudaLaunchCooperativeKernel((const void*)msbfs_kernel, dim3(grid), dim3(block), params, 0, s);
+}
+
+cudaError_t launch_barrier_selftest(GridBarrier* bar, int32_t* status, unsigned long long limit_ns, int grid,
+                                    cudaStream_t s) {
+    int absent = 0;
+    void* params[] = {&bar, &status, &limit_ns, &absent};
+    return cudaLaunchCooperativeKernel((const void*)barrier_selftest_kernel, dim3(grid), dim3(256), params, 0, s);
 }
 
 cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s) {

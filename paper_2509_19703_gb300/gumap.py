@@ -114,6 +114,8 @@ def load():
             lib.gumap_last_error.restype = ctypes.c_char_p
             lib.gumap_server_clock.argtypes = [vp]
             lib.gumap_server_clock.restype = ctypes.c_double
+            lib.gumap_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_double]
+            lib.gumap_selftest_wait_timeout.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -239,6 +241,11 @@ def gumap_knn_run_noalloc(row_ptr, col_idx, n: int, nnz: int, k: int, mode: int,
                                         int(n), int(nnz), int(k), int(mode), _dptr(out_idx, torch.int32, "out_idx"),
                                         _dptr(out_dist, torch.int16, "out_dist"), _dptr(status, torch.int32, "status"),
                                         _stream(stream)), "gumap_knn_run_noalloc")
+
+
+def gumap_selftest_wait_timeout(device: int = 0, limit_s: float = 0.05) -> int:
+    """Status of a grid barrier that can never complete (GUMAP_ERR_TIMEOUT expected)."""
+    return int(load().gumap_selftest_wait_timeout(int(device), float(limit_s)))
 
 
 # ---------------------------------------------------------------- serving
