@@ -85,6 +85,9 @@ extern "C" {
 #define GUMAP_OPT_STATE_BYTES 4 /* value: device bytes allowed for MS-BFS bitsets, 0 = auto */
 #define GUMAP_OPT_HEAVY_DEGREE 5 /* value: MS-BFS vertices of larger degree are processed by a whole warp
                                     (default 64); setting it synchronises the device */
+#define GUMAP_OPT_DIRECTION   6 /* value: MS-BFS level direction: 0 = choose per level (default),
+                                   1 = pull only, 2 = push from level 2 on                      */
+#define GUMAP_OPT_PUSH_DIV    7 /* value: push when frontier edges * value < unvisited edges (default 8) */
 
 typedef struct gumap_knn gumap_knn;
 
@@ -213,6 +216,8 @@ typedef struct {
     double  bfs_init_ms;     /* MS-BFS device time in clearing + level-1 push (device timer) */
     double  bfs_pull_ms;     /* MS-BFS device time in the pull steps of levels >= 2 */
     double  bfs_extract_ms;  /* MS-BFS device time in the kNN extraction steps */
+    double  bfs_push_ms;     /* MS-BFS device time in push levels (queue preparation + push) */
+    int64_t bfs_push_levels; /* MS-BFS levels run as a push since the last reset */
 } gumap_knn_stats;
 
 /*

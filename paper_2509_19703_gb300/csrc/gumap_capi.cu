@@ -165,6 +165,11 @@ struct gumap_knn {
     int64_t opt_block_bits = 0;
     int opt_profile = 0;
     int64_t opt_state_bytes = 0;
+    // GUMAP_OPT_DIRECTION: pull only by default. Push levels are correct but
+    // were slower on every measured workload: with many sources per block the
+    // frontier holds most vertices even when each row holds few bits.
+    int opt_direction = 1;
+    int opt_push_div = 8;    // GUMAP_OPT_PUSH_DIV
 
     // MS-BFS scratch
     DevBuf bits;        // F, N, V
@@ -293,7 +298,9 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
     const int W = S / 32;
     const size_t words = (size_t)h->n * W;
     int rc;
-    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t), "bitsets"))) return rc;
+    // bitsets F, N, V, then 4 frontier queues and the queue-entry levels (n ints each)
+    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t) + 5 * (size_t)h->n * sizeof(int32_t), "bitsets")))
+        return rc;
     if ((rc = ensure(h->act, (size_t)W * 4, "act"))) return rc;
     if ((rc = ensure(h->need, (size_t)W * 4, "need"))) return rc;
     if ((rc = ensure(h->cnt, (size_t)S * 4, "cnt"))) return rc;
@@ -322,13 +329,17 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.k = h->k;
         a.partial = h->mode == GUMAP_PARTIAL ? 1 : 0;
         a.ctr = h->d_ctr;
+        a.direction = h->opt_direction;
+        a.push_div = h->opt_push_div;
+        a.queue = reinterpret_cast<int32_t*>(base + 3 * words);
+        a.inq = a.queue + 4 * (size_t)h->n;
         CK(cudaMemsetAsync(&h->d_ctr->bar, 0, sizeof(GridBarrier), st), "reset barrier");
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->opt_profile) {
             if ((rc = next_event_pair(h, &e0, &e1))) return rc;
             CK(cudaEventRecord(e0, st), "cudaEventRecord");
         }
-        CK(launch_msbfs(a, h->coop_grid, 256, st), "msbfs launch");
+        CK(launch_msbfs(a, msbfs_grid_for(a, h->coop_grid), 256, st), "msbfs launch");
         if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
         h->bfs_launches++;
         h->kernel_launches++;
@@ -743,6 +754,14 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             if (value < 0) return fail(GUMAP_ERR_INVALID_ARG, "negative budget");
             h->opt_state_bytes = value;
             return GUMAP_OK;
+        case GUMAP_OPT_DIRECTION:
+            if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "direction must be 0, 1 or 2");
+            h->opt_direction = (int)value;
+            return GUMAP_OK;
+        case GUMAP_OPT_PUSH_DIV:
+            if (value < 1 || value > (1 << 20)) return fail(GUMAP_ERR_INVALID_ARG, "push divisor out of range");
+            h->opt_push_div = (int)value;
+            return GUMAP_OK;
         case GUMAP_OPT_HEAVY_DEGREE:
             if (value < 0 || value > 0x7FFFFFFF) return fail(GUMAP_ERR_INVALID_ARG, "bad degree threshold");
             CK(cudaSetDevice(h->device), "cudaSetDevice");
@@ -778,6 +797,8 @@ int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
     out->bfs_init_ms = (double)c.t_init_ns * 1e-6;
     out->bfs_pull_ms = (double)c.t_pull_ns * 1e-6;
     out->bfs_extract_ms = (double)c.t_extract_ns * 1e-6;
+    out->bfs_push_ms = (double)c.t_push_ns * 1e-6;
+    out->bfs_push_levels = c.push_levels;
     return GUMAP_OK;
 }
 
@@ -793,7 +814,8 @@ int gumap_knn_reset_stats(gumap_knn* h) {
     CK(cudaMemcpy(&c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
     c.levels_max = 0;
     c.level_sum = 0;
-    c.t_init_ns = c.t_pull_ns = c.t_extract_ns = 0;
+    c.t_init_ns = c.t_pull_ns = c.t_extract_ns = c.t_push_ns = 0;
+    c.push_levels = 0;
     CK(cudaMemcpy(h->d_ctr, &c, sizeof(c), cudaMemcpyHostToDevice), "write counters");
     return GUMAP_OK;
 }

@@ -41,6 +41,13 @@ struct DeviceCounters {
     unsigned long long t_init_ns;
     unsigned long long t_pull_ns;
     unsigned long long t_extract_ns;
+    // direction choice of the MS-BFS levels (slot d % 4 belongs to level d)
+    int32_t qcnt[4];                 // vertices in the frontier queue of level d
+    int32_t qvalid[4];               // 1 if that queue was built
+    unsigned long long f_edges[4];   // sum of deg(v) over nonzero (v, group) items of level d
+    unsigned long long u_edges[4];   // sum of deg(v) over (v, group) items left unvisited after a pull
+    long long push_levels;           // push levels run since the last host reset
+    unsigned long long t_push_ns;    // device time of push levels (prep + push)
 };
 
 // Arguments of one multi-source BFS launch over a block of sources.
@@ -69,6 +76,12 @@ struct MsbfsArgs {
     int32_t k;
     int32_t partial;         // 1: stop each source once its list is complete
     DeviceCounters* ctr;
+    // direction-optimising levels: 0 = choose per level, 1 = pull only,
+    // 2 = push from level 2 on; queue/inq may be NULL only with 1
+    int32_t direction;
+    int32_t push_div;        // push when frontier edges * push_div < unvisited edges
+    int32_t* queue;          // [4][n] frontier queues, slot d % 4
+    int32_t* inq;            // [n] level at which the vertex last entered a queue
 };
 
 // Arguments of one partial-BFS launch with one warp per source.
@@ -130,6 +143,7 @@ cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem_bytes, cudaSt
 // ---- msbfs.cu
 int msbfs_max_blocks_per_sm(int block_threads);
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);
+int msbfs_grid_for(const MsbfsArgs& a, int max_grid);
 cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s);
 cudaError_t launch_barrier_selftest(GridBarrier* bar, int32_t* status, unsigned long long limit_ns, int grid,
                                     cudaStream_t s);

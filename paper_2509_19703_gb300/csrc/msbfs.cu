@@ -135,11 +135,16 @@ __device__ void phase_init(const MsbfsArgs& a) {
     const long long words4 = (long long)a.n * (a.W >> 2);
     uint4* V4 = reinterpret_cast<uint4*>(a.V);
     uint4* N4 = reinterpret_cast<uint4*>(a.N);
+    uint4* F4 = reinterpret_cast<uint4*>(a.F);
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    const bool clear_f = a.direction != 1;  // a push into F (level 2) needs it zero
     for (long long i = tid; i < words4; i += nthr) {
         V4[i] = z;
         N4[i] = z;
+        if (clear_f) F4[i] = z;
     }
+    if (a.inq)
+        for (long long i = tid; i < a.n; i += nthr) a.inq[i] = 0;
     for (long long i = tid; i < a.W; i += nthr) {
         long long lo = i * 32;
         uint32_t m;
@@ -160,7 +165,41 @@ __device__ void phase_init(const MsbfsArgs& a) {
         a.ctr->lvl_any[0] = 0u;
         a.ctr->lvl_any[1] = 0u;
         a.ctr->lvl_any[2] = 0u;
+        for (int q = 0; q < 4; ++q) {
+            a.ctr->qcnt[q] = 0;
+            a.ctr->qvalid[q] = 0;
+            a.ctr->f_edges[q] = 0ull;
+            a.ctr->u_edges[q] = 0ull;
+        }
+        a.ctr->qvalid[0] = 1;  // F was cleared: the buffer level 2 writes holds no row
+        a.ctr->u_edges[0] = (unsigned long long)__ldg(a.row_ptr + a.n) * (unsigned long long)(a.W >> 2);
     }
+}
+
+// Appends each lane's v (where want) to q with one atomic per warp. All 32
+// lanes must call it together.
+__device__ __forceinline__ void warp_append(bool want, int v, int32_t* q, int32_t* cnt) {
+    const unsigned m = __ballot_sync(kFull, want);
+    if (!m) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(cnt, __popc(m));
+    base = __shfl_sync(kFull, base, leader);
+    if (want) q[base + __popc(m & ((1u << lane) - 1u))] = v;
+}
+
+// Block-wide sum of a per-thread counter into a global one (one atomic per
+// CTA). All threads of the CTA must call it.
+__device__ __forceinline__ void block_add(unsigned long long x, unsigned long long* dst) {
+    __shared__ unsigned long long s_acc;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+    if (threadIdx.x == 0) s_acc = 0ull;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_acc, x);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
 }
 
 // Phase 1: seed V with the sources (level 0), push level 1 into N, and take
@@ -176,6 +215,7 @@ __device__ void phase_seed(const MsbfsArgs& a) {
     const long long warp = tid >> 5;
     const long long nwarps = nthr >> 5;
     int any = 0;
+    unsigned long long fe = 0ull;  // edges leaving the level-1 frontier (for the direction choice)
     for (long long j = warp; j < a.nb; j += nwarps) {
         const int s = a.src[j];
         const bool ok = s >= 0 && s < a.n;  // an invalid source is an empty row
@@ -187,6 +227,7 @@ __device__ void phase_seed(const MsbfsArgs& a) {
         for (int e = e0 + lane; e < e1; e += 32) {
             const int u = __ldg(a.col + e);
             atomicOr(Ncol + (size_t)u * a.W, bit);
+            fe += (unsigned long long)(__ldg(a.row_ptr + u + 1) - __ldg(a.row_ptr + u));
         }
         const int take = deg < a.k ? deg : a.k;
         int32_t* oi = a.out_idx + (size_t)j * a.k;
@@ -206,11 +247,17 @@ __device__ void phase_seed(const MsbfsArgs& a) {
         }
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[1], 1u);
+    block_add(fe, &a.ctr->f_edges[1]);
 }
 
-// Pull step of level d (see file comment).
+// Pull step of level d (see file comment). Also measures, for the choice of
+// the next level's direction, the edges of the new frontier (sum of deg(v)
+// over nonzero (v, group) items: what a push would touch) and of the items
+// still unvisited (what the next pull would touch at most).
 __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
-                           int slot) {
+                           int slot, int d) {
+    unsigned long long fe = 0ull, ue = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr->qvalid[d % 4] = 0;  // a pull builds no queue
     const int G = a.W >> 2;
     const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -243,6 +290,11 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
                 if (covers4(acc, todo)) break;
             }
             acc = and4(acc, todo);
+            if (lane == 0) {
+                const unsigned long long dv = (unsigned long long)(e1 - e0);
+                if (nz4(acc)) fe += dv;
+                if (nz4(andnot4(todo, acc))) ue += dv;
+            }
         }
         if (lane == 0) {
             N4[off] = acc;
@@ -277,12 +329,118 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
                 if (covers4(acc, todo)) break;
             }
             acc = and4(acc, todo);
+            const unsigned long long dv = (unsigned long long)(e1 - e0);
+            if (nz4(acc)) fe += dv;
+            if (nz4(andnot4(todo, acc))) ue += dv;
         }
         N4[off] = acc;
         V4[off] = vis;
         any |= nz4(acc) ? 1 : 0;
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
+    if (a.direction == 0) {  // the statistics only feed the automatic choice
+        block_add(fe, &a.ctr->f_edges[d % 4]);
+        block_add(ue, &a.ctr->u_edges[d % 4]);
+    }
+}
+
+// Preparation of a push level d: (a) if level d-1 was a pull, list the
+// vertices of its frontier (rows of F with a nonzero group) into queue
+// d-1; (b) clear the buffer level d writes (it holds level d-2): only the
+// rows of queue d-2 when that queue exists, else all of it.
+__device__ void phase_push_prep(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
+                                int d) {
+    const int G = a.W >> 2;
+    const int lane = threadIdx.x & 31;
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
+    uint4* N4 = reinterpret_cast<uint4*>(Nc);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    if (!ld_volatile_i32(&a.ctr->qvalid[(d - 1) % 4])) {
+        int32_t* q = a.queue + (size_t)((d - 1) % 4) * a.n;
+        for (long long t0 = gtid & ~31ll; t0 < a.n; t0 += nthr) {
+            const int v = (int)(t0 + lane);
+            bool nzrow = false;
+            if (v < a.n) {
+                const uint4* row = F4 + (size_t)v * G;
+                for (int g = 0; g < G && !nzrow; ++g) nzrow = nz4(ldcg4(row + g));
+                if (nzrow) a.inq[v] = d - 1;
+            }
+            warp_append(nzrow, v, q, &a.ctr->qcnt[(d - 1) % 4]);
+        }
+    }
+    if (ld_volatile_i32(&a.ctr->qvalid[(d - 2) % 4])) {
+        const int32_t* q = a.queue + (size_t)((d - 2) % 4) * a.n;
+        const long long items = (long long)ld_volatile_i32(&a.ctr->qcnt[(d - 2) % 4]) * G;
+        for (long long t = gtid; t < items; t += nthr) {
+            const long long i = t / G;
+            N4[(size_t)__ldcg(q + i) * G + (t - i * G)] = z;
+        }
+    } else {
+        const long long words4 = (long long)a.n * G;
+        for (long long t = gtid; t < words4; t += nthr) N4[t] = z;
+    }
+    // the queue-valid flags change only in phase_push, after the barrier that
+    // ends this phase: every CTA must read the same values here
+}
+
+// Push step of level d: one warp per (frontier vertex u, group g), lanes over
+// u's neighbours v, each ORing F[u][g] & act & ~(V[v] | F[v]) into N[v][g];
+// v joins queue d the first time it gains a bit. F[u][g] is folded into
+// V[u][g] here (a pull does that for every item).
+__device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc, int d) {
+    const int G = a.W >> 2;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
+    uint4* V4 = reinterpret_cast<uint4*>(a.V);
+    const uint4* act4 = reinterpret_cast<const uint4*>(a.act);
+    const int32_t* qin = a.queue + (size_t)((d - 1) % 4) * a.n;
+    int32_t* qout = a.queue + (size_t)(d % 4) * a.n;
+    const long long items = (long long)ld_volatile_i32(&a.ctr->qcnt[(d - 1) % 4]) * G;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctr->qvalid[(d - 1) % 4] = 1;  // compacted by the prep phase if it was missing
+        a.ctr->qvalid[d % 4] = 1;        // built by this phase
+    }
+    int any = 0;
+    unsigned long long fe = 0ull;
+    for (long long it = gwarp; it < items; it += nwarps) {
+        const long long i = it / G;
+        const int g = (int)(it - i * G);
+        const int u = __ldcg(qin + i);
+        const size_t uo = (size_t)u * G + g;
+        const uint4 f = ldcg4(F4 + uo);
+        if (!nz4(f)) continue;
+        if (lane == 0) V4[uo] = or4(ldcg4(V4 + uo), f);
+        const uint4 fa = and4(f, ldcg4(act4 + g));
+        if (!nz4(fa)) continue;
+        const int e0 = __ldg(a.row_ptr + u), e1 = __ldg(a.row_ptr + u + 1);
+        for (int base = e0; base < e1; base += 32) {
+            const int e = base + lane;
+            const int v = e < e1 ? __ldg(a.col + e) : 0;
+            bool want = false;
+            if (e < e1) {
+                const size_t vo = (size_t)v * G + g;
+                const uint4 m = andnot4(fa, or4(ldcg4(V4 + vo), ldcg4(F4 + vo)));
+                if (nz4(m)) {
+                    uint32_t* nw = Nc + vo * 4;
+                    bool fresh = true;
+                    if (m.x) fresh &= atomicOr(nw + 0, m.x) == 0u;
+                    if (m.y) fresh &= atomicOr(nw + 1, m.y) == 0u;
+                    if (m.z) fresh &= atomicOr(nw + 2, m.z) == 0u;
+                    if (m.w) fresh &= atomicOr(nw + 3, m.w) == 0u;
+                    if (fresh) fe += (unsigned long long)(__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
+                    any = 1;
+                    want = ld_volatile_i32(a.inq + v) != d && atomicExch(a.inq + v, d) != d;
+                }
+            }
+            warp_append(want, v, qout, &a.ctr->qcnt[d % 4]);
+        }
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[d % 3], 1u);
+    block_add(fe, &a.ctr->f_edges[d % 4]);
 }
 
 // Extraction of level d: one warp per 32-source word column with incomplete
@@ -348,7 +506,8 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
 __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long t_prev = timer ? globaltimer_ns() : 0ull;
-    unsigned long long t_init = 0, t_pull = 0, t_extract = 0;
+    unsigned long long t_init = 0, t_pull = 0, t_extract = 0, t_push = 0;
+    long long pushes = 0;
     auto lap = [&](unsigned long long& acc) {
         if (timer) {
             const unsigned long long t = globaltimer_ns();
@@ -367,12 +526,42 @@ __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
     int last = 1;
     bool go = ld_volatile_u32(&a.ctr->lvl_any[1]) != 0u;
     if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) go = false;
+    int last_pull = 0;  // u_edges[0] holds the "everything unvisited" estimate
     for (int d = 2; go && d <= a.n; ++d) {
         const int need_now = ld_volatile_i32(&a.ctr->n_need);
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr->lvl_any[(d + 1) % 3] = 0u;
-        phase_pull(a, Fc, Nc, d % 3);
-        if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
-        lap(t_pull);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            // slots of level d + 1 (last used by level d - 3)
+            a.ctr->lvl_any[(d + 1) % 3] = 0u;
+            a.ctr->qcnt[(d + 1) % 4] = 0;
+            a.ctr->f_edges[(d + 1) % 4] = 0ull;
+            a.ctr->u_edges[(d + 1) % 4] = 0ull;
+        }
+        // Direction of level d, decided identically by every thread from
+        // values settled before the last barrier: push when the edges out of
+        // the frontier are few against the edges still to be explored
+        // (Beamer's rule in bit-parallel form). The estimate of unexplored
+        // edges comes from a pull at most two levels back; older, pull again.
+        bool push = false;
+        if (a.direction == 2) {
+            push = true;
+        } else if (a.direction == 0 && d - last_pull <= 2) {
+            const unsigned long long fe = *reinterpret_cast<volatile unsigned long long*>(&a.ctr->f_edges[(d - 1) % 4]);
+            const unsigned long long ue = *reinterpret_cast<volatile unsigned long long*>(&a.ctr->u_edges[last_pull % 4]);
+            push = fe * (unsigned long long)a.push_div < ue;
+        }
+        if (push) {
+            phase_push_prep(a, Fc, Nc, d);
+            if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+            phase_push(a, Fc, Nc, d);
+            if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+            lap(t_push);
+            ++pushes;
+        } else {
+            phase_pull(a, Fc, Nc, d % 3, d);
+            if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+            lap(t_pull);
+            last_pull = d;
+        }
         if (ld_volatile_u32(&a.ctr->lvl_any[d % 3]) == 0u) break;
         last = d;
         if (need_now > 0) {
@@ -392,6 +581,8 @@ __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
         a.ctr->t_init_ns += t_init;
         a.ctr->t_pull_ns += t_pull;
         a.ctr->t_extract_ns += t_extract;
+        a.ctr->t_push_ns += t_push;
+        a.ctr->push_levels += pushes;
     }
 }
 
@@ -417,6 +608,19 @@ int msbfs_max_blocks_per_sm(int block_threads) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, msbfs_kernel, block_threads, 0) != cudaSuccess)
         return 0;
     return nb;
+}
+
+// CTAs for one launch: one thread per (vertex, group) item and one warp
+// per extraction column, at most the resident maximum. Fewer CTAs make
+// every grid barrier cheaper on small graphs.
+int msbfs_grid_for(const MsbfsArgs& a, int max_grid) {
+    const long long items = (long long)a.n * (a.W >> 2);
+    long long g = (items + 255) / 256;
+    const long long for_extract = ((a.nb + 31) / 32 + 7) / 8;
+    if (g < for_extract) g = for_extract;
+    if (g < 1) g = 1;
+    if (g > max_grid) g = max_grid;
+    return (int)g;
 }
 
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s) {

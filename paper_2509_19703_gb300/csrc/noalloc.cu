@@ -135,6 +135,7 @@ extern "C" int gumap_knn_run_noalloc(const int32_t* row_ptr, const int32_t* col_
         a.k = k;
         a.partial = mode == GUMAP_PARTIAL ? 1 : 0;
         a.ctr = ctr;
+        a.direction = 1;  // pull only: the push levels' queues would need more scratch
         if (cudaMemsetAsync(&ctr->bar, 0, sizeof(GridBarrier), st) != cudaSuccess) return GUMAP_ERR_CUDA;
         if (launch_msbfs(a, setup.coop_grid, 256, st) != cudaSuccess) return GUMAP_ERR_CUDA;
     }

@@ -270,7 +270,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
     const size_t o_a = c.take<float>((size_t)N * k);
     const size_t o_rho = c.take<float>((size_t)N);
     const size_t o_sigma = c.take<float>((size_t)N);
-    size_t o_slab = 0, o_bits = 0, o_act = 0, o_need = 0, o_cnt = 0, o_order = 0;
+    size_t o_slab = 0, o_bits = 0, o_act = 0, o_need = 0, o_cnt = 0, o_order = 0, o_queue = 0;
     if (small && slab > 0) o_slab = c.take<uint32_t>((size_t)slab * s->batch_grid);
     if (!small && group[0]->mode == GUMAP_FULL) {
         o_bits = c.take<uint32_t>((size_t)N * W * 3);
@@ -278,6 +278,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
         o_need = c.take<uint32_t>((size_t)W);
         o_cnt = c.take<int32_t>((size_t)W * 32);
         o_order = c.take<int32_t>((size_t)N);
+        o_queue = c.take<int32_t>((size_t)N * 5);  // 4 frontier queues + queue-entry levels
     }
     const size_t dev_bytes = c.off;
     // pinned staging: status word, rp, col, offs, units
@@ -400,8 +401,12 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
             a.k = k;
             a.partial = 0;
             a.ctr = ctr;
+            a.direction = 1;  // pull only (see GUMAP_OPT_DIRECTION)
+            a.push_div = 8;
+            a.queue = reinterpret_cast<int32_t*>(dptr(o_queue));
+            a.inq = a.queue + 4 * (size_t)N;
             ck(cudaMemsetAsync(&ctr->bar, 0, sizeof(GridBarrier), st));
-            ck(launch_msbfs(a, s->coop_grid, 256, st));
+            ck(launch_msbfs(a, msbfs_grid_for(a, s->coop_grid), 256, st));
         }
         L->engine = GUMAP_ENGINE_MSBFS;
     }

@@ -23,6 +23,8 @@ FULL, PARTIAL = 0, 1
 WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE = 0x0, 0x1, 0x2
 ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER, ENGINE_BATCH = 0, 1, 2, 3, 4
 OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
+OPT_DIRECTION, OPT_PUSH_DIV = 6, 7
+DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
 MAX_K = 256
 DIST_INF = 0xFFFF
 
@@ -45,7 +47,8 @@ class _Stats(ctypes.Structure):
                 ("levels_max", ctypes.c_int32), ("bfs_launches", ctypes.c_int64), ("bfs_ms", ctypes.c_double),
                 ("bfs_level_sum", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("bfs_init_ms", ctypes.c_double),
-                ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double)]
+                ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double),
+                ("bfs_push_ms", ctypes.c_double), ("bfs_push_levels", ctypes.c_int64)]
 
 
 class _ServerOpts(ctypes.Structure):

@@ -12,7 +12,8 @@ W_TOL = 1e-5       # absolute tolerance on FP32 weights vs the FP64 oracle
 SIGMA_RTOL = 1e-5  # relative tolerance on sigma
 
 
-def run_gpu(g, k, mode="full", engine=None, block_bits=None, sources=None, directed=False, coo=True):
+def run_gpu(g, k, mode="full", engine=None, block_bits=None, sources=None, directed=False, coo=True,
+            direction=None):
     flags = gumap.WEIGHTS_DIRECTED if directed else gumap.WEIGHTS_UNION
     m = gumap.FULL if mode == "full" else gumap.PARTIAL
     with gumap.KnnGraph.from_graph(g, k, mode=m, flags=flags) as kg:
@@ -20,6 +21,8 @@ def run_gpu(g, k, mode="full", engine=None, block_bits=None, sources=None, direc
             kg.set_option(gumap.OPT_ENGINE, engine)
         if block_bits is not None:
             kg.set_option(gumap.OPT_BLOCK_BITS, block_bits)
+        if direction is not None:
+            kg.set_option(gumap.OPT_DIRECTION, direction)
         src_t = None
         if sources is not None:
             src_t = torch.as_tensor(np.asarray(sources, dtype=np.int32), device="cuda")

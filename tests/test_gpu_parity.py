@@ -55,6 +55,27 @@ def test_zoo_partial_both_engines(g, k):
     assert_parity(run_gpu(g, k, "partial", engine=MSBFS), ref, f"{g.name} partial/msbfs k={k}")
 
 
+@pytest.mark.parametrize("direction", [gumap.DIRECTION_PULL, gumap.DIRECTION_PUSH])
+@pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
+def test_zoo_forced_direction(g, k, direction):
+    """Every level a pull, or every level from 2 on a push: same rows."""
+    for mode in ("full", "partial"):
+        ref = oracle_ref(g, k, mode)
+        assert_parity(run_gpu(g, k, mode, engine=MSBFS, direction=direction, block_bits=256), ref,
+                      f"{g.name} {mode} k={k} direction={direction}")
+
+
+def test_direction_switches_on_a_long_grid():
+    """Narrow source blocks on a long grid: the automatic rule runs push
+    levels (sparse frontiers) and pull levels, with identical rows."""
+    g = gg.grid(120, 80)
+    ref = oracle_ref(g, 15, "full")
+    res = run_gpu(g, 15, "full", engine=MSBFS, block_bits=256, direction=gumap.DIRECTION_AUTO)
+    assert_parity(res, ref, "grid 120x80 auto")
+    assert res["stats"]["bfs_push_levels"] > 0
+    assert res["stats"]["bfs_level_sum"] > res["stats"]["bfs_push_levels"]
+
+
 def test_config1_grid32_full():
     """32 x 32 grid, all 1024 sources, k = 15 (the small full-form case)."""
     g = gg.config_grid32()
