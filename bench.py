@@ -278,6 +278,7 @@ def run_ours(args):
     works = [component_work(g) for g in graphs]
     work_per_step = int(sum(int(w.sum()) for w in works))
     kgs = [gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=gumap.FULL) for g in graphs]
+    tuned = [kg.autotune() for kg in kgs]  # engine settings timed on each graph, before any timed step
     for kg in kgs:
         kg.set_option(gumap.OPT_PROFILE, 1)
     outs = [kg.alloc_outputs(g.n) for kg, g in zip(kgs, graphs)]
@@ -381,7 +382,10 @@ def run_ours(args):
                            "work_edges_per_step": work_per_step, "parallelism": f"replicas x{world}",
                            "l2": "flushed (512 MB write) before each timed step",
                            "block_bits": [st["block_bits"] for st in stats],
-                           "levels_max": [st["levels_max"] for st in stats]},
+                           "levels_max": [st["levels_max"] for st in stats],
+                           "autotuned": [{key: t[key] for key in ("engine", "state_bytes", "pull_width", "heavy_mult",
+                                                                   "direction", "best_ms", "default_ms")}
+                                         for t in tuned]},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)

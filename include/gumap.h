@@ -88,6 +88,7 @@ extern "C" {
 #define GUMAP_OPT_DIRECTION   6 /* value: MS-BFS level direction: 0 = choose per level (default),
                                    1 = pull only, 2 = push from level 2 on                      */
 #define GUMAP_OPT_PUSH_DIV    7 /* value: push when frontier edges * value < unvisited edges (default 8) */
+#define GUMAP_OPT_PULL_WIDTH  8 /* value: 32-bit words per MS-BFS pull item, 4 (default) or 2     */
 
 typedef struct gumap_knn gumap_knn;
 
@@ -219,6 +220,44 @@ typedef struct {
     double  bfs_push_ms;     /* MS-BFS device time in push levels (queue preparation + push) */
     int64_t bfs_push_levels; /* MS-BFS levels run as a push since the last reset */
 } gumap_knn_stats;
+
+typedef struct {
+    int32_t n;
+    int64_t nnz;
+    int32_t k;
+    int32_t mode;
+    uint32_t flags;
+    int32_t max_degree;
+    int32_t batch;           /* 1 for handles made by gumap_batch_create */
+} gumap_knn_info;
+
+/* gumap_knn_get_info - the shape of the handle's graph and request. */
+int gumap_knn_get_info(gumap_knn *h, gumap_knn_info *out);
+
+typedef struct {
+    int32_t from_cache;      /* 1: settings read from the cache, nothing timed */
+    int32_t candidates;      /* settings timed */
+    double best_ms;          /* device time of one gumap_knn_run with the chosen settings */
+    double default_ms;       /* ... with the settings the handle had before */
+    int32_t engine, pull_width, heavy_mult, direction;
+    int64_t state_bytes;
+} gumap_tune_result;
+
+/*
+ * gumap_knn_autotune - pick the engine settings for this handle's graph by
+ * timing gumap_knn_run (all vertices) on it: MS-BFS state budget (which
+ * sets the source-block width), pull item width, heavy-vertex degree
+ * multiplier and level direction for the full form; engine for the partial
+ * form. The best settings are applied to the handle and, if cache_path is
+ * not NULL, appended to that JSON-lines file under a key of the graph's
+ * shape class (form, k, log2 n, log2 mean degree, hub ratio); a later
+ * handle of the same class created while the environment variable
+ * GUMAP_TUNE_CACHE names that file starts with them. If the cache already
+ * holds the key, its settings are applied without timing. Synchronous;
+ * allocates scratch outputs for the timing runs. (Library tuning, not a
+ * step of the paper.) Errors: INVALID_ARG, OOM, CUDA.
+ */
+int gumap_knn_autotune(gumap_knn *h, const char *cache_path, gumap_tune_result *out);
 
 /*
  * gumap_knn_get_stats - counters since the last reset. Synchronises the

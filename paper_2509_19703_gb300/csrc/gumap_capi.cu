@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -149,7 +150,9 @@ struct gumap_knn {
     int mode = GUMAP_FULL;
     uint32_t flags = 0;
     int num_sms = 0;
-    int coop_grid = 0;
+    int coop_grid = 0;     // resident CTAs of the MS-BFS kernel with 128-bit pull items
+    int coop_grid2 = 0;    // ... with 64-bit pull items
+    int opt_pull_width = 4;
 
     int32_t* d_rp = nullptr;
     int32_t* d_col = nullptr;
@@ -237,11 +240,13 @@ size_t held_bytes(const gumap_knn* h) {
 }
 
 // Sources per MS-BFS block: the largest multiple of 128 whose three bitsets
-// fit the state budget (default 96 MB, so a block's state stays resident in
-// the 126 MB L2), balanced over the blocks the sources need.
+// fit the state budget, balanced over the blocks the sources need. The
+// default budget (256 MB) is the autotuner's choice on the 20,000-vertex
+// scale-free graph: one wide block beats two L2-sized ones, because every
+// block repeats the levels, the grid barriers and the extraction scans.
 int choose_block_bits(const gumap_knn* h, int32_t n_src) {
     if (h->opt_block_bits > 0) return (int)h->opt_block_bits;
-    const double budget = h->opt_state_bytes > 0 ? (double)h->opt_state_bytes : 96.0 * 1024 * 1024;
+    const double budget = h->opt_state_bytes > 0 ? (double)h->opt_state_bytes : 256.0 * 1024 * 1024;
     long long smax = (long long)(budget * 8.0 / (3.0 * (double)std::max<int32_t>(h->n, 1)));
     smax = (smax / 128) * 128;
     if (smax < 128) smax = 128;
@@ -331,6 +336,7 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.ctr = h->d_ctr;
         a.direction = h->opt_direction;
         a.push_div = h->opt_push_div;
+        a.pull_width = h->opt_pull_width;
         a.queue = reinterpret_cast<int32_t*>(base + 3 * words);
         a.inq = a.queue + 4 * (size_t)h->n;
         CK(cudaMemsetAsync(&h->d_ctr->bar, 0, sizeof(GridBarrier), st), "reset barrier");
@@ -339,7 +345,8 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
             if ((rc = next_event_pair(h, &e0, &e1))) return rc;
             CK(cudaEventRecord(e0, st), "cudaEventRecord");
         }
-        CK(launch_msbfs(a, msbfs_grid_for(a, h->coop_grid), 256, st), "msbfs launch");
+        CK(launch_msbfs(a, msbfs_grid_for(a, a.pull_width == 2 ? h->coop_grid2 : h->coop_grid), 256, st),
+           "msbfs launch");
         if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
         h->bfs_launches++;
         h->kernel_launches++;
@@ -480,6 +487,9 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     const int per_sm = msbfs_max_blocks_per_sm(256);
     if (per_sm <= 0) { gumap_knn_destroy(h); return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident"); }
     h->coop_grid = h->num_sms * per_sm;
+    const int per_sm2 = msbfs_max_blocks_per_sm(256, 2);
+    if (per_sm2 <= 0) { gumap_knn_destroy(h); return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident"); }
+    h->coop_grid2 = h->num_sms * per_sm2;
 
     const cudaMemcpyKind kind = (flags & GUMAP_CSR_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if ((e = cudaMalloc(&h->d_rp, sizeof(int32_t) * (n + 1))) != cudaSuccess ||
@@ -536,6 +546,7 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
         gumap_knn_destroy(h);
         return cuda_fail(e, "create");
     }
+    tune_apply_cached(h, std::getenv("GUMAP_TUNE_CACHE"));  // settings of a tuned graph of this shape
     *out = h;
     return GUMAP_OK;
 }
@@ -758,6 +769,10 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "direction must be 0, 1 or 2");
             h->opt_direction = (int)value;
             return GUMAP_OK;
+        case GUMAP_OPT_PULL_WIDTH:
+            if (value != 2 && value != 4) return fail(GUMAP_ERR_INVALID_ARG, "pull width must be 2 or 4 words");
+            h->opt_pull_width = (int)value;
+            return GUMAP_OK;
         case GUMAP_OPT_PUSH_DIV:
             if (value < 1 || value > (1 << 20)) return fail(GUMAP_ERR_INVALID_ARG, "push divisor out of range");
             h->opt_push_div = (int)value;
@@ -771,6 +786,21 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
         default:
             return fail(GUMAP_ERR_INVALID_ARG, "unknown option %d", option);
     }
+}
+
+int gumap_knn_get_info(gumap_knn* h, gumap_knn_info* out) {
+    if (!h || !out) return fail(GUMAP_ERR_INVALID_ARG, "NULL argument");
+    memset(out, 0, sizeof(*out));
+    out->n = h->n;
+    out->nnz = h->nnz;
+    out->k = h->k;
+    out->mode = h->mode;
+    out->flags = h->flags;
+    int32_t maxd = 0;
+    for (int32_t d : h->deg) maxd = std::max(maxd, d);
+    out->max_degree = maxd;
+    out->batch = h->batch ? 1 : 0;
+    return GUMAP_OK;
 }
 
 int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {

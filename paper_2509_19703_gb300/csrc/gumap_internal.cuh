@@ -82,6 +82,7 @@ struct MsbfsArgs {
     int32_t push_div;        // push when frontier edges * push_div < unvisited edges
     int32_t* queue;          // [4][n] frontier queues, slot d % 4
     int32_t* inq;            // [n] level at which the vertex last entered a queue
+    int32_t pull_width;      // words per pull item: 4 (128 bits; also when 0) or 2 (64 bits)
 };
 
 // Arguments of one partial-BFS launch with one warp per source.
@@ -134,6 +135,9 @@ bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, 
 int32_t plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr, const int32_t* modes,
                    std::vector<BatchUnit>& units, size_t& smem, long long& slab);
 
+// ---- tune.cu
+void tune_apply_cached(struct gumap_knn* h, const char* cache_path);
+
 // ---- batch.cu
 cudaError_t batch_prepare(size_t smem_bytes);
 int batch_threads();
@@ -141,7 +145,7 @@ const void* batch_kernel_ptr();
 cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem_bytes, cudaStream_t s);
 
 // ---- msbfs.cu
-int msbfs_max_blocks_per_sm(int block_threads);
+int msbfs_max_blocks_per_sm(int block_threads, int pull_width = 4);
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);
 int msbfs_grid_for(const MsbfsArgs& a, int max_grid);
 cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s);

@@ -250,22 +250,57 @@ __device__ void phase_seed(const MsbfsArgs& a) {
     block_add(fe, &a.ctr->f_edges[1]);
 }
 
-// Pull step of level d (see file comment). Also measures, for the choice of
-// the next level's direction, the edges of the new frontier (sum of deg(v)
-// over nonzero (v, group) items: what a push would touch) and of the items
-// still unvisited (what the next pull would touch at most).
+// Vector helpers of the pull for its two item widths: a thread owns either a
+// 128-bit group (uint4, four words) or a 64-bit group (uint2, two words) of
+// a vertex row.
+template <int GW> struct PullVec;
+template <> struct PullVec<4> { using T = uint4; };
+template <> struct PullVec<2> { using T = uint2; };
+
+__device__ __forceinline__ uint4 vzero(uint4) { return make_uint4(0u, 0u, 0u, 0u); }
+__device__ __forceinline__ uint2 vzero(uint2) { return make_uint2(0u, 0u); }
+__device__ __forceinline__ uint4 vor(uint4 a, uint4 b) { return or4(a, b); }
+__device__ __forceinline__ uint2 vor(uint2 a, uint2 b) { return make_uint2(a.x | b.x, a.y | b.y); }
+__device__ __forceinline__ uint4 vand(uint4 a, uint4 b) { return and4(a, b); }
+__device__ __forceinline__ uint2 vand(uint2 a, uint2 b) { return make_uint2(a.x & b.x, a.y & b.y); }
+__device__ __forceinline__ uint4 vandnot(uint4 a, uint4 b) { return andnot4(a, b); }
+__device__ __forceinline__ uint2 vandnot(uint2 a, uint2 b) { return make_uint2(a.x & ~b.x, a.y & ~b.y); }
+__device__ __forceinline__ bool vnz(uint4 a) { return nz4(a); }
+__device__ __forceinline__ bool vnz(uint2 a) { return (a.x | a.y) != 0u; }
+__device__ __forceinline__ uint4 vld(const uint4* p) { return __ldcg(p); }
+__device__ __forceinline__ uint2 vld(const uint2* p) { return __ldcg(p); }
+__device__ __forceinline__ uint4 vwarp_or(uint4 a) { return warp_or4(a); }
+__device__ __forceinline__ uint2 vwarp_or(uint2 a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.x |= __shfl_xor_sync(kFull, a.x, o);
+        a.y |= __shfl_xor_sync(kFull, a.y, o);
+    }
+    return a;
+}
+template <typename T>
+__device__ __forceinline__ bool vcovers(T acc, T todo) { return !vnz(vandnot(todo, acc)); }
+
+// Pull step of level d (see file comment), with items of GW words. Also
+// measures, for the choice of the next level's direction, the edges of the
+// new frontier (sum of deg(v) over nonzero (v, group) items: what a push
+// would touch) and of the items still unvisited (what the next pull would
+// touch at most).
+template <int GW>
 __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
                            int slot, int d) {
+    using VT = typename PullVec<GW>::T;
     unsigned long long fe = 0ull, ue = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr->qvalid[d % 4] = 0;  // a pull builds no queue
-    const int G = a.W >> 2;
+    const int G = a.W / GW;
     const int lane = threadIdx.x & 31;
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
-    const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
-    uint4* N4 = reinterpret_cast<uint4*>(Nc);
-    uint4* V4 = reinterpret_cast<uint4*>(a.V);
-    const uint4* act4 = reinterpret_cast<const uint4*>(a.act);
+    const VT* FV = reinterpret_cast<const VT*>(Fc);
+    VT* NV = reinterpret_cast<VT*>(Nc);
+    VT* VV = reinterpret_cast<VT*>(a.V);
+    const VT* actV = reinterpret_cast<const VT*>(a.act);
+    const VT zero = vzero(VT{});
     int any = 0;
 
     // heavy vertices: one warp per (v, g), lanes split the neighbour list
@@ -275,31 +310,31 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const int g = (int)(it - (long long)h * G);
         const int v = __ldg(a.heavy + h);
         const size_t off = (size_t)v * G + g;
-        const uint4 vis = or4(ldcg4(V4 + off), ldcg4(F4 + off));
-        const uint4 todo = andnot4(ldcg4(act4 + g), vis);
-        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
-        if (nz4(todo)) {
+        const VT vis = vor(vld(VV + off), vld(FV + off));
+        const VT todo = vandnot(vld(actV + g), vis);
+        VT acc = zero;
+        if (vnz(todo)) {
             const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
             for (int base = e0; base < e1; base += 64) {
                 const int ea = base + lane, eb = base + 32 + lane;
                 const int ua = ea < e1 ? __ldg(a.col + ea) : -1;
                 const int ub = eb < e1 ? __ldg(a.col + eb) : -1;
-                if (ua >= 0) acc = or4(acc, ldcg4(F4 + (size_t)ua * G + g));
-                if (ub >= 0) acc = or4(acc, ldcg4(F4 + (size_t)ub * G + g));
-                acc = warp_or4(acc);
-                if (covers4(acc, todo)) break;
+                if (ua >= 0) acc = vor(acc, vld(FV + (size_t)ua * G + g));
+                if (ub >= 0) acc = vor(acc, vld(FV + (size_t)ub * G + g));
+                acc = vwarp_or(acc);
+                if (vcovers(acc, todo)) break;
             }
-            acc = and4(acc, todo);
+            acc = vand(acc, todo);
             if (lane == 0) {
                 const unsigned long long dv = (unsigned long long)(e1 - e0);
-                if (nz4(acc)) fe += dv;
-                if (nz4(andnot4(todo, acc))) ue += dv;
+                if (vnz(acc)) fe += dv;
+                if (vnz(vandnot(todo, acc))) ue += dv;
             }
         }
         if (lane == 0) {
-            N4[off] = acc;
-            V4[off] = vis;
-            any |= nz4(acc) ? 1 : 0;
+            NV[off] = acc;
+            VV[off] = vis;
+            any |= vnz(acc) ? 1 : 0;
         }
     }
 
@@ -311,31 +346,30 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const int v = __ldg(a.light + li);
         const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
         const size_t off = (size_t)v * G + g;
-        const uint4 vis = or4(ldcg4(V4 + off), ldcg4(F4 + off));
-        const uint4 todo = andnot4(ldcg4(act4 + g), vis);
-        uint4 acc = make_uint4(0u, 0u, 0u, 0u);
-        if (nz4(todo)) {
-            const uint4* fg = F4 + g;
+        const VT vis = vor(vld(VV + off), vld(FV + off));
+        const VT todo = vandnot(vld(actV + g), vis);
+        VT acc = zero;
+        if (vnz(todo)) {
+            const VT* fg = FV + g;
             for (int e = e0; e < e1; e += 8) {
                 int u[8];
 #pragma unroll
                 for (int q = 0; q < 8; ++q) u[q] = (e + q < e1) ? __ldg(a.col + e + q) : -1;
-                uint4 f[8];
+                VT f[8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    f[q] = u[q] >= 0 ? ldcg4(fg + (size_t)u[q] * G) : make_uint4(0u, 0u, 0u, 0u);
+                for (int q = 0; q < 8; ++q) f[q] = u[q] >= 0 ? vld(fg + (size_t)u[q] * G) : zero;
 #pragma unroll
-                for (int q = 0; q < 8; ++q) acc = or4(acc, f[q]);
-                if (covers4(acc, todo)) break;
+                for (int q = 0; q < 8; ++q) acc = vor(acc, f[q]);
+                if (vcovers(acc, todo)) break;
             }
-            acc = and4(acc, todo);
+            acc = vand(acc, todo);
             const unsigned long long dv = (unsigned long long)(e1 - e0);
-            if (nz4(acc)) fe += dv;
-            if (nz4(andnot4(todo, acc))) ue += dv;
+            if (vnz(acc)) fe += dv;
+            if (vnz(vandnot(todo, acc))) ue += dv;
         }
-        N4[off] = acc;
-        V4[off] = vis;
-        any |= nz4(acc) ? 1 : 0;
+        NV[off] = acc;
+        VV[off] = vis;
+        any |= vnz(acc) ? 1 : 0;
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
     if (a.direction == 0) {  // the statistics only feed the automatic choice
@@ -503,6 +537,7 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
     }
 }
 
+template <int GW>
 __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long t_prev = timer ? globaltimer_ns() : 0ull;
@@ -557,7 +592,7 @@ __global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
             lap(t_push);
             ++pushes;
         } else {
-            phase_pull(a, Fc, Nc, d % 3, d);
+            phase_pull<GW>(a, Fc, Nc, d % 3, d);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             lap(t_pull);
             last_pull = d;
@@ -603,10 +638,10 @@ __global__ void identity_kernel(int32_t* dst, int32_t n) {
 
 }  // namespace
 
-int msbfs_max_blocks_per_sm(int block_threads) {
+int msbfs_max_blocks_per_sm(int block_threads, int pull_width) {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, msbfs_kernel, block_threads, 0) != cudaSuccess)
-        return 0;
+    const void* k = pull_width == 2 ? (const void*)msbfs_kernel<2> : (const void*)msbfs_kernel<4>;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block_threads, 0) != cudaSuccess) return 0;
     return nb;
 }
 
@@ -626,7 +661,8 @@ int msbfs_grid_for(const MsbfsArgs& a, int max_grid) {
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s) {
     MsbfsArgs copy = a;
     void* params[] = {&copy};
-    return cudaLaunchCooperativeKernel((const void*)msbfs_kernel, dim3(grid), dim3(block), params, 0, s);
+    const void* k = a.pull_width == 2 ? (const void*)msbfs_kernel<2> : (const void*)msbfs_kernel<4>;
+    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block), params, 0, s);
 }
 
 cudaError_t launch_barrier_selftest(GridBarrier* bar, int32_t* status, unsigned long long limit_ns, int grid,

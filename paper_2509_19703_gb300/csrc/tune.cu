@@ -1,0 +1,236 @@
+// Autotuner of the engine settings (gumap_knn_autotune) and its cache.
+//
+// Settings are timed on the handle's own graph through the public calls
+// (gumap_knn_set_option, gumap_knn_run): for the full form the MS-BFS state
+// budget (it sets the source-block width), the pull item width, the degree
+// multiplier above which a vertex's items are warp-wide and the level
+// direction; for the partial form the engine. Each candidate runs once to
+// warm up, then three times with the L2 flushed before each run; the median
+// device time decides. The winner is kept in a JSON-lines cache under a key
+// of the graph's shape class, so graphs of the same class start tuned.
+#include "gumap.h"
+#include "gumap_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <string>
+#include <vector>
+
+namespace {
+
+struct Setting {
+    int engine = GUMAP_ENGINE_AUTO;
+    int pull_width = 4;
+    int heavy_mult = 4;
+    int direction = 1;
+    long long state_bytes = 0;
+};
+
+std::string shape_key(const gumap_knn_info& in) {
+    const double mean = in.n > 0 ? (double)in.nnz / in.n : 0.0;
+    const double hub = in.max_degree / std::max(mean, 1.0);
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%s/k%d/w%d/logn%.2f/logdeg%.1f/loghub%d", in.mode == GUMAP_FULL ? "full" : "partial",
+             in.k, (in.flags & GUMAP_WEIGHTS_DIRECTED) ? 0 : 1, std::round(std::log2((double)in.n) * 4.0) / 4.0,
+             std::round(std::log2(mean + 1.0) * 2.0) / 2.0, (int)std::lround(std::log2(hub + 1.0)));
+    return buf;
+}
+
+bool read_cache(const char* path, const std::string& key, Setting* s) {
+    std::ifstream f(path);
+    if (!f) return false;
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        char k[200];
+        Setting t;
+        double ms = 0;
+        if (sscanf(line.c_str(),
+                   "{\"key\": \"%199[^\"]\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, "
+                   "\"direction\": %d, \"state_bytes\": %lld, \"ms\": %lf}",
+                   k, &t.engine, &t.pull_width, &t.heavy_mult, &t.direction, &t.state_bytes, &ms) == 7 &&
+            key == k) {
+            *s = t;  // the last entry of a key wins
+            found = true;
+        }
+    }
+    return found;
+}
+
+void append_cache(const char* path, const std::string& key, const Setting& s, double ms) {
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f,
+            "{\"key\": \"%s\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, \"direction\": %d, "
+            "\"state_bytes\": %lld, \"ms\": %.6f}\n",
+            key.c_str(), s.engine, s.pull_width, s.heavy_mult, s.direction, s.state_bytes, ms);
+    fclose(f);
+}
+
+int apply(gumap_knn* h, const gumap_knn_info& in, const Setting& s) {
+    int rc;
+    if ((rc = gumap_knn_set_option(h, GUMAP_OPT_ENGINE, s.engine))) return rc;
+    if (s.engine == GUMAP_ENGINE_MSBFS || s.engine == GUMAP_ENGINE_AUTO) {
+        const long long mean = in.n > 0 ? in.nnz / in.n : 0;
+        if ((rc = gumap_knn_set_option(h, GUMAP_OPT_STATE_BYTES, s.state_bytes))) return rc;
+        if ((rc = gumap_knn_set_option(h, GUMAP_OPT_PULL_WIDTH, s.pull_width))) return rc;
+        if ((rc = gumap_knn_set_option(h, GUMAP_OPT_DIRECTION, s.direction))) return rc;
+        if ((rc = gumap_knn_set_option(h, GUMAP_OPT_HEAVY_DEGREE, std::max<long long>(64, s.heavy_mult * mean))))
+            return rc;
+    }
+    return GUMAP_OK;
+}
+
+}  // namespace
+
+namespace gumap {
+
+// Applies cached settings at handle creation (GUMAP_TUNE_CACHE); silent on
+// any failure: the handle keeps its defaults.
+void tune_apply_cached(gumap_knn* h, const char* path) {
+    gumap_knn_info in;
+    if (!path || !*path || gumap_knn_get_info(h, &in) != GUMAP_OK || in.batch) return;
+    Setting s;
+    if (read_cache(path, shape_key(in), &s)) apply(h, in, s);
+}
+
+}  // namespace gumap
+
+extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tune_result* out) {
+    gumap_knn_info in;
+    int rc = gumap_knn_get_info(h, &in);
+    if (rc) return rc;
+    if (in.batch) return GUMAP_ERR_INVALID_ARG;
+    gumap_tune_result res;
+    std::memset(&res, 0, sizeof(res));
+    const std::string key = shape_key(in);
+    Setting best;
+    if (cache_path && read_cache(cache_path, key, &best)) {
+        if ((rc = apply(h, in, best))) return rc;
+        res.from_cache = 1;
+        res.engine = best.engine;
+        res.pull_width = best.pull_width;
+        res.heavy_mult = best.heavy_mult;
+        res.direction = best.direction;
+        res.state_bytes = best.state_bytes;
+        if (out) *out = res;
+        return GUMAP_OK;
+    }
+
+    const size_t cells = (size_t)in.n * in.k;
+    void *idx = nullptr, *dist = nullptr, *w = nullptr, *flush = nullptr;
+    const size_t flush_bytes = 256ull << 20;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (st) cudaStreamSynchronize(st);
+        cudaFree(idx);
+        cudaFree(dist);
+        cudaFree(w);
+        cudaFree(flush);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+    };
+    if (cudaMalloc(&idx, cells * 4) != cudaSuccess || cudaMalloc(&dist, cells * 2) != cudaSuccess ||
+        cudaMalloc(&w, cells * 4) != cudaSuccess || cudaMalloc(&flush, flush_bytes) != cudaSuccess) {
+        cleanup();
+        return GUMAP_ERR_OOM;
+    }
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cleanup();
+        return GUMAP_ERR_CUDA;
+    }
+    // median device time of three runs (L2 flushed before each), after one warm-up run
+    auto time_run = [&](double* ms) -> int {
+        int r = gumap_knn_run(h, nullptr, in.n, (int32_t*)idx, (uint16_t*)dist, (float*)w, st);
+        if (r) return r;
+        double t[3];
+        for (int i = 0; i < 3; ++i) {
+            if (cudaMemsetAsync(flush, i, flush_bytes, st) != cudaSuccess || cudaEventRecord(e0, st) != cudaSuccess)
+                return GUMAP_ERR_CUDA;
+            if ((r = gumap_knn_run(h, nullptr, in.n, (int32_t*)idx, (uint16_t*)dist, (float*)w, st))) return r;
+            float f = 0.0f;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&f, e0, e1) != cudaSuccess)
+                return GUMAP_ERR_CUDA;
+            t[i] = f;
+        }
+        std::sort(t, t + 3);
+        *ms = t[1];
+        return gumap_knn_check(h, st);
+    };
+
+    std::vector<Setting> cands;
+    if (in.mode == GUMAP_FULL) {
+        for (long long budget : {96ll << 20, 256ll << 20, 1024ll << 20})
+            for (int width : {4, 2})
+                for (int hm : {2, 4, 8}) {
+                    Setting s;
+                    s.engine = GUMAP_ENGINE_MSBFS;
+                    s.state_bytes = budget;
+                    s.pull_width = width;
+                    s.heavy_mult = hm;
+                    s.direction = 1;
+                    cands.push_back(s);
+                }
+    } else {
+        Setting f;
+        f.engine = GUMAP_ENGINE_FRONTIER;
+        cands.push_back(f);
+        for (long long budget : {96ll << 20, 256ll << 20}) {
+            Setting s;
+            s.engine = GUMAP_ENGINE_MSBFS;
+            s.state_bytes = budget;
+            cands.push_back(s);
+        }
+    }
+    double default_ms = 0.0;
+    if ((rc = time_run(&default_ms))) {
+        cleanup();
+        return rc;
+    }
+    double best_ms = 1e300;
+    for (const Setting& s : cands) {
+        double ms = 0.0;
+        if ((rc = apply(h, in, s)) || (rc = time_run(&ms))) {
+            cleanup();
+            return rc;
+        }
+        res.candidates++;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = s;
+        }
+    }
+    if (in.mode == GUMAP_FULL) {  // then the automatic direction on the best settings
+        Setting s = best;
+        s.direction = 0;
+        double ms = 0.0;
+        if ((rc = apply(h, in, s)) || (rc = time_run(&ms))) {
+            cleanup();
+            return rc;
+        }
+        res.candidates++;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = s;
+        }
+    }
+    cleanup();
+    if ((rc = apply(h, in, best))) return rc;
+    if (cache_path) append_cache(cache_path, key, best, best_ms);
+    res.best_ms = best_ms;
+    res.default_ms = default_ms;
+    res.engine = best.engine;
+    res.pull_width = best.pull_width;
+    res.heavy_mult = best.heavy_mult;
+    res.direction = best.direction;
+    res.state_bytes = best.state_bytes;
+    if (out) *out = res;
+    return GUMAP_OK;
+}

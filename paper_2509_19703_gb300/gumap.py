@@ -23,7 +23,7 @@ FULL, PARTIAL = 0, 1
 WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE = 0x0, 0x1, 0x2
 ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER, ENGINE_BATCH = 0, 1, 2, 3, 4
 OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
-OPT_DIRECTION, OPT_PUSH_DIV = 6, 7
+OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH = 6, 7, 8
 DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
 MAX_K = 256
 DIST_INF = 0xFFFF
@@ -49,6 +49,17 @@ class _Stats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("bfs_init_ms", ctypes.c_double),
                 ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double),
                 ("bfs_push_ms", ctypes.c_double), ("bfs_push_levels", ctypes.c_int64)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("k", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("flags", ctypes.c_uint32), ("max_degree", ctypes.c_int32), ("batch", ctypes.c_int32)]
+
+
+class _Tune(ctypes.Structure):
+    _fields_ = [("from_cache", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double),
+                ("default_ms", ctypes.c_double), ("engine", ctypes.c_int32), ("pull_width", ctypes.c_int32),
+                ("heavy_mult", ctypes.c_int32), ("direction", ctypes.c_int32), ("state_bytes", ctypes.c_int64)]
 
 
 class _ServerOpts(ctypes.Structure):
@@ -106,6 +117,8 @@ def load():
                 "gumap_serve_release": [vp, ctypes.c_uint64],
                 "gumap_server_get_stats": [vp, ctypes.POINTER(_ServerStats)],
                 "gumap_server_destroy": [vp],
+                "gumap_knn_get_info": [vp, ctypes.POINTER(_Info)],
+                "gumap_knn_autotune": [vp, ctypes.c_char_p, ctypes.POINTER(_Tune)],
             }
             for name, args in sig.items():
                 f = getattr(lib, name)
@@ -223,6 +236,20 @@ def gumap_knn_get_stats(h) -> dict:
     s = _Stats()
     _check(load().gumap_knn_get_stats(h, ctypes.byref(s)), "gumap_knn_get_stats")
     return {f: getattr(s, f) for f, _ in _Stats._fields_}
+
+
+def gumap_knn_get_info(h) -> dict:
+    i = _Info()
+    _check(load().gumap_knn_get_info(h, ctypes.byref(i)), "gumap_knn_get_info")
+    return {f: getattr(i, f) for f, _ in _Info._fields_}
+
+
+def gumap_knn_autotune(h, cache_path: str | None = None) -> dict:
+    """Time engine settings on the handle's graph, apply the best (see gumap.h)."""
+    r = _Tune()
+    _check(load().gumap_knn_autotune(h, cache_path.encode() if cache_path else None, ctypes.byref(r)),
+           "gumap_knn_autotune")
+    return {f: getattr(r, f) for f, _ in _Tune._fields_}
 
 
 def gumap_knn_reset_stats(h):
@@ -400,6 +427,12 @@ class KnnGraph:
 
     def stats(self) -> dict:
         return gumap_knn_get_stats(self.h)
+
+    def info(self) -> dict:
+        return gumap_knn_get_info(self.h)
+
+    def autotune(self, cache_path: str | None = None) -> dict:
+        return gumap_knn_autotune(self.h, cache_path)
 
     def reset_stats(self):
         gumap_knn_reset_stats(self.h)

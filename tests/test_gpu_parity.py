@@ -65,6 +65,24 @@ def test_zoo_forced_direction(g, k, direction):
                       f"{g.name} {mode} k={k} direction={direction}")
 
 
+@pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
+def test_zoo_64bit_pull_items(g, k):
+    """Pull items of 64 bits instead of 128: same rows."""
+    ref = oracle_ref(g, k, "full")
+    with gumap.KnnGraph.from_graph(g, k) as kg:
+        kg.set_option(gumap.OPT_PULL_WIDTH, 2)
+        kg.set_option(gumap.OPT_BLOCK_BITS, 384)
+        out = kg.run()
+        r, c, w = kg.coo()
+        kg.check()
+        res = dict(idx=out["idx"].cpu().numpy(), dist=gumap.dist_u16(out["dist"]),
+                   w=out["w"].cpu().numpy().astype(np.float64), coo=(r.cpu().numpy(), c.cpu().numpy(),
+                                                                      w.cpu().numpy().astype(np.float64)))
+        rho, sigma = kg.rho_sigma()
+        res.update(rho=rho.cpu().numpy().astype(np.float64), sigma=sigma.cpu().numpy().astype(np.float64))
+    assert_parity(res, ref, f"{g.name} width 2 k={k}")
+
+
 def test_direction_switches_on_a_long_grid():
     """Narrow source blocks on a long grid: the automatic rule runs push
     levels (sparse frontiers) and pull levels, with identical rows."""
