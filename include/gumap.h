@@ -266,8 +266,18 @@ int gumap_knn_autotune(gumap_knn *h, const char *cache_path, gumap_tune_result *
 int gumap_knn_get_stats(gumap_knn *h, gumap_knn_stats *out);
 int gumap_knn_reset_stats(gumap_knn *h);
 
-/* gumap_knn_destroy - free everything the handle owns (synchronises the device). NULL is allowed. */
+/* gumap_knn_destroy - free everything the handle owns (synchronises the device). NULL is allowed.
+ * Device buffers go back to the library's pool (see gumap_pool_trim), so creating a handle of the
+ * same shape again allocates nothing. */
 int gumap_knn_destroy(gumap_knn *h);
+
+/* gumap_pool_trim - return the pool's cached device buffers of `device` (-1: all devices) to CUDA.
+ * The pool keeps at most GUMAP_POOL_BYTES (environment, default 8 GiB); beyond that, freed buffers
+ * go straight back to CUDA. */
+int gumap_pool_trim(int device);
+
+/* Bytes the pool currently caches over all devices. */
+int64_t gumap_pool_cached_bytes(void);
 
 /*
  * gumap_knn_run_noalloc - kNN lists of every vertex (the same rows as

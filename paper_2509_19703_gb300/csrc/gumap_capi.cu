@@ -212,21 +212,25 @@ struct gumap_knn {
 
 namespace {
 
+// Buffers come from the library's pool (pool.cu). Growing one waits for the
+// device first: queued work may still use the old block.
 int ensure(DevBuf& b, size_t bytes, const char* what) {
     if (b.bytes >= bytes && b.p) return GUMAP_OK;
     if (b.p) {
-        cudaFree(b.p);
+        CK(cudaDeviceSynchronize(), "sync before growing a buffer");
+        pool_free(b.p, b.bytes);
         b.p = nullptr;
         b.bytes = 0;
     }
     if (bytes == 0) bytes = 16;
-    CK(cudaMalloc(&b.p, bytes), what);
+    CK(pool_alloc(&b.p, bytes), what);
     b.bytes = bytes;
     return GUMAP_OK;
 }
 
+// The caller guarantees the device is done with the buffer.
 void release(DevBuf& b) {
-    if (b.p) cudaFree(b.p);
+    if (b.p) pool_free(b.p, b.bytes);
     b.p = nullptr;
     b.bytes = 0;
 }
@@ -436,14 +440,14 @@ const char* gumap_last_error(void) { return g_last_error.c_str(); }
 int gumap_knn_destroy(gumap_knn* h) {
     if (!h) return GUMAP_OK;
     cudaSetDevice(h->device);
-    cudaDeviceSynchronize();
-    cudaFree(h->d_rp);
-    cudaFree(h->d_col);
-    cudaFree(h->d_identity);
-    cudaFree(h->d_order);
-    cudaFree(h->d_units);
+    cudaDeviceSynchronize();  // nothing queued may still use the buffers handed back below
+    pool_free(h->d_rp, sizeof(int32_t) * ((size_t)h->n + 1));
+    pool_free(h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz, 1));
+    pool_free(h->d_identity, sizeof(int32_t) * (size_t)h->n);
+    pool_free(h->d_order, sizeof(int32_t) * (size_t)h->n);
+    pool_free(h->d_units, sizeof(BatchUnit) * (size_t)std::max<int32_t>(h->n_units, 1));
     release(h->vslab);
-    cudaFree(h->d_ctr);
+    pool_free(h->d_ctr, sizeof(DeviceCounters));
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
     for (DevBuf* b : bs) release(*b);
@@ -492,10 +496,10 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     h->coop_grid2 = h->num_sms * per_sm2;
 
     const cudaMemcpyKind kind = (flags & GUMAP_CSR_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if ((e = cudaMalloc(&h->d_rp, sizeof(int32_t) * (n + 1))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_col, sizeof(int32_t) * std::max<int64_t>(nnz, 1))) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_identity, sizeof(int32_t) * n)) != cudaSuccess ||
-        (e = cudaMalloc(&h->d_ctr, sizeof(DeviceCounters))) != cudaSuccess) {
+    if ((e = pool_alloc((void**)&h->d_rp, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess ||
+        (e = pool_alloc((void**)&h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
+        (e = pool_alloc((void**)&h->d_identity, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
+        (e = pool_alloc((void**)&h->d_ctr, sizeof(DeviceCounters))) != cudaSuccess) {
         gumap_knn_destroy(h);
         return cuda_fail(e, "cudaMalloc");
     }
@@ -519,7 +523,7 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
             return fail(GUMAP_ERR_INVALID_GRAPH, "invalid CSR (device validation)");
         }
     }
-    if ((e = cudaMalloc(&h->d_order, sizeof(int32_t) * n)) != cudaSuccess) {
+    if ((e = pool_alloc((void**)&h->d_order, sizeof(int32_t) * (size_t)n)) != cudaSuccess) {
         gumap_knn_destroy(h);
         return cuda_fail(e, "cudaMalloc");
     }
@@ -605,7 +609,8 @@ int gumap_batch_create(gumap_knn** out, int32_t n_graphs, const int32_t* vertex_
         gumap_knn_destroy(h);
         return rc;
     }
-    if ((e = cudaMalloc(&h->d_units, sizeof(BatchUnit) * sorted.size())) != cudaSuccess ||
+    h->n_units = (int32_t)sorted.size();  // sizes the block handed back by destroy
+    if ((e = pool_alloc((void**)&h->d_units, sizeof(BatchUnit) * sorted.size())) != cudaSuccess ||
         (e = cudaMemcpy(h->d_units, sorted.data(), sizeof(BatchUnit) * sorted.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess) {
         gumap_knn_destroy(h);

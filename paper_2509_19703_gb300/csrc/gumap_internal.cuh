@@ -135,6 +135,12 @@ bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, 
 int32_t plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr, const int32_t* modes,
                    std::vector<BatchUnit>& units, size_t& smem, long long& slab);
 
+// ---- pool.cu: the handles' device-memory pool
+cudaError_t pool_alloc(void** p, size_t bytes);
+void pool_free(void* p, size_t bytes);  // the device must be done with p
+void pool_trim(int device);             // device < 0: every device
+size_t pool_cached_bytes();
+
 // ---- tune.cu
 void tune_apply_cached(struct gumap_knn* h, const char* cache_path);
 

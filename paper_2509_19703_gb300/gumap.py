@@ -132,6 +132,10 @@ def load():
             lib.gumap_server_clock.restype = ctypes.c_double
             lib.gumap_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_double]
             lib.gumap_selftest_wait_timeout.restype = ctypes.c_int
+            lib.gumap_pool_trim.argtypes = [ctypes.c_int]
+            lib.gumap_pool_trim.restype = ctypes.c_int
+            lib.gumap_pool_cached_bytes.argtypes = []
+            lib.gumap_pool_cached_bytes.restype = ctypes.c_int64
             _lib = lib
     return _lib
 
@@ -271,6 +275,14 @@ def gumap_knn_run_noalloc(row_ptr, col_idx, n: int, nnz: int, k: int, mode: int,
                                         int(n), int(nnz), int(k), int(mode), _dptr(out_idx, torch.int32, "out_idx"),
                                         _dptr(out_dist, torch.int16, "out_dist"), _dptr(status, torch.int32, "status"),
                                         _stream(stream)), "gumap_knn_run_noalloc")
+
+
+def gumap_pool_trim(device: int = -1):
+    _check(load().gumap_pool_trim(int(device)), "gumap_pool_trim")
+
+
+def gumap_pool_cached_bytes() -> int:
+    return int(load().gumap_pool_cached_bytes())
 
 
 def gumap_selftest_wait_timeout(device: int = 0, limit_s: float = 0.05) -> int:

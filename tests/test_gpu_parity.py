@@ -245,6 +245,19 @@ def test_device_csr_valid_path():
         gumap.gumap_knn_destroy(h)
 
 
+def test_pooled_buffers_across_handles():
+    """Handles destroyed and created again reuse pooled device buffers
+    (holding the previous graph's data) and still give the oracle's rows."""
+    gumap.gumap_pool_trim(-1)
+    assert gumap.gumap_pool_cached_bytes() == 0
+    graphs = [gg.barabasi_albert(2500, 3, 161), gg.grid(40, 60), gg.barabasi_albert(2500, 3, 162)]
+    for g in graphs * 2:
+        assert_parity(run_gpu(g, 15, "full"), oracle_ref(g, 15, "full"), g.name)
+        assert gumap.gumap_pool_cached_bytes() > 0
+    gumap.gumap_pool_trim(-1)
+    assert gumap.gumap_pool_cached_bytes() == 0
+
+
 def test_repeated_runs_are_identical():
     """The handle's scratch is reused across runs without leaking state."""
     g = gg.barabasi_albert(3000, 4, 72)
