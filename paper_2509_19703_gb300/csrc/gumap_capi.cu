@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -175,7 +176,7 @@ struct gumap_knn {
     int opt_push_div = 8;    // GUMAP_OPT_PUSH_DIV
 
     // MS-BFS scratch
-    DevBuf bits;        // F, N, V
+    DevBuf bits;        // F, N, S
     DevBuf act, need, cnt;
 
     // per-run scratch
@@ -285,6 +286,34 @@ int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b) {
 // Processing order of the MS-BFS pull: vertices of degree > heavy_deg
 // (warp-wide items) then the rest, each by decreasing degree (a counting
 // sort on the host degrees, stable in vertex id). Synchronous upload.
+// Per-device launch limits of the MS-BFS kernel, queried once per device
+// (the attribute and occupancy queries cost more than the rest of creating
+// a small handle). The caller has made `device` current.
+struct LaunchLimits {
+    int sms = 0;
+    int per_sm4 = 0;  // resident CTAs per SM with 128-bit pull items
+    int per_sm2 = 0;  // ... with 64-bit pull items
+};
+
+int launch_limits(int device, LaunchLimits& out) {
+    static std::mutex mu;
+    static std::vector<LaunchLimits> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    if ((size_t)device < cache.size() && cache[(size_t)device].sms > 0) {
+        out = cache[(size_t)device];
+        return GUMAP_OK;
+    }
+    LaunchLimits l;
+    CK(cudaDeviceGetAttribute(&l.sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
+    l.per_sm4 = msbfs_max_blocks_per_sm(256);
+    l.per_sm2 = msbfs_max_blocks_per_sm(256, 2);
+    if (l.sms <= 0 || l.per_sm4 <= 0 || l.per_sm2 <= 0) return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident");
+    if (cache.size() <= (size_t)device) cache.resize((size_t)device + 1);
+    cache[(size_t)device] = l;
+    out = l;
+    return GUMAP_OK;
+}
+
 int build_order(gumap_knn* h) {
     const int32_t n = h->n;
     int32_t maxd = 0;
@@ -307,7 +336,7 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
     const int W = S / 32;
     const size_t words = (size_t)h->n * W;
     int rc;
-    // bitsets F, N, V, then 4 frontier queues and the queue-entry levels (n ints each)
+    // bitsets F, N, S, then 4 frontier queues and the queue-entry levels (n ints each)
     if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t) + 5 * (size_t)h->n * sizeof(int32_t), "bitsets")))
         return rc;
     if ((rc = ensure(h->act, (size_t)W * 4, "act"))) return rc;
@@ -325,7 +354,7 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.W = W;
         a.F = base;
         a.N = base + words;
-        a.V = base + 2 * words;
+        a.S = base + 2 * words;
         a.heavy = h->d_order;
         a.n_heavy = h->n_heavy;
         a.light = h->d_order + h->n_heavy;
@@ -484,16 +513,15 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     h->k = k;
     h->mode = mode;
     h->flags = flags;
-    cudaDeviceProp prop;
-    cudaError_t e = cudaGetDeviceProperties(&prop, device);
-    if (e != cudaSuccess) { gumap_knn_destroy(h); return cuda_fail(e, "cudaGetDeviceProperties"); }
-    h->num_sms = prop.multiProcessorCount;
-    const int per_sm = msbfs_max_blocks_per_sm(256);
-    if (per_sm <= 0) { gumap_knn_destroy(h); return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident"); }
-    h->coop_grid = h->num_sms * per_sm;
-    const int per_sm2 = msbfs_max_blocks_per_sm(256, 2);
-    if (per_sm2 <= 0) { gumap_knn_destroy(h); return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident"); }
-    h->coop_grid2 = h->num_sms * per_sm2;
+    LaunchLimits lim;
+    if (int lrc = launch_limits(device, lim)) {
+        gumap_knn_destroy(h);
+        return lrc;
+    }
+    h->num_sms = lim.sms;
+    h->coop_grid = lim.sms * lim.per_sm4;
+    h->coop_grid2 = lim.sms * lim.per_sm2;
+    cudaError_t e;
 
     const cudaMemcpyKind kind = (flags & GUMAP_CSR_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if ((e = pool_alloc((void**)&h->d_rp, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess ||
@@ -528,14 +556,19 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
         return cuda_fail(e, "cudaMalloc");
     }
     {
-        std::vector<int32_t> rp_host((size_t)n + 1);
-        if ((e = cudaMemcpy(rp_host.data(), h->d_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost)) !=
-            cudaSuccess) {
-            gumap_knn_destroy(h);
-            return cuda_fail(e, "row_ptr readback");
+        std::vector<int32_t> rp_dev;  // row_ptr read back when the CSR came on the device
+        const int32_t* rp = row_ptr;
+        if (flags & GUMAP_CSR_ON_DEVICE) {
+            rp_dev.resize((size_t)n + 1);
+            if ((e = cudaMemcpy(rp_dev.data(), h->d_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost)) !=
+                cudaSuccess) {
+                gumap_knn_destroy(h);
+                return cuda_fail(e, "row_ptr readback");
+            }
+            rp = rp_dev.data();
         }
         h->deg.resize((size_t)n);
-        for (int32_t v = 0; v < n; ++v) h->deg[(size_t)v] = rp_host[(size_t)v + 1] - rp_host[(size_t)v];
+        for (int32_t v = 0; v < n; ++v) h->deg[(size_t)v] = rp[(size_t)v + 1] - rp[(size_t)v];
     }
     // A vertex is "heavy" (one warp per item) only when its degree is well
     // above the graph's mean: on a uniform dense graph every vertex is long

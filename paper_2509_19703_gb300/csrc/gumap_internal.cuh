@@ -60,7 +60,7 @@ struct MsbfsArgs {
     int32_t W;               // 32-bit words per vertex row, multiple of 4
     uint32_t* F;             // frontier  [n][W]
     uint32_t* N;             // next      [n][W]
-    uint32_t* V;             // visited   [n][W]
+    uint32_t* S;             // seen      [n][W] (every level so far, the frontier included)
     // Processing order of the pull: vertices of degree above the heavy
     // threshold (one warp per item), then the rest (one thread per item),
     // each list by decreasing degree so the longest items start first.

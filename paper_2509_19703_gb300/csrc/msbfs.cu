@@ -5,9 +5,10 @@
 // W a multiple of 4 so a thread moves 128 bits with one uint4 access):
 //   F[v]  frontier: sources that reached v at the previous level
 //   N[v]  next:     sources that reach v at the current level
-//   V[v]  visited:  sources that reached v before the previous level
-// A level is the pull step  N[v] = (OR_{u in adj(v)} F[u]) & act & ~(V[v] | F[v]),
-// which is the frontier expansion of Algorithm 4 (tovisit -> newvisit) and of
+//   S[v]  seen:     sources that reached v at any level so far (F included)
+// A level is the pull step  N[v] = (OR_{u in adj(v)} F[u]) & act & ~S[v],
+// then S[v] |= N[v], which is the frontier expansion of Algorithm 4
+// (tovisit -> newvisit) and of
 // the BFS inside AllPairsShortestPath (Algorithm 1) run for 32*W sources at
 // once. The OR over neighbours stops as soon as every still-missing source
 // bit is covered (the bottom-up early exit), and a vertex already reached by
@@ -22,8 +23,10 @@
 // longest items start first and the short ones fill the tail before the
 // grid barrier.
 //
-// Level 1 is a push from the sources (their adjacency rows), and its kNN
-// entries are the first k entries of each source's sorted CSR row.
+// Level 1 is a push from the sources (their adjacency rows) into N only,
+// and its kNN entries are the first k entries of each source's sorted CSR
+// row; level 2 folds the level-1 frontier into S (one stream instead of an
+// atomic per edge).
 // For later levels the extraction phase scans each word column of N in
 // vertex order, transposes 32x32 bit tiles with warp ballots, and appends
 // to every incomplete source the vertices it reached at this level in
@@ -127,19 +130,19 @@ __device__ __forceinline__ uint4 warp_or4(uint4 a) {
 
 // ---------------------------------------------------------------- phases
 
-// Phase 0: clear V and N, prefill the block's output rows with padding,
+// Phase 0: clear S and N, prefill the block's output rows with padding,
 // mark valid source bits in act/need.
 __device__ void phase_init(const MsbfsArgs& a) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const long long words4 = (long long)a.n * (a.W >> 2);
-    uint4* V4 = reinterpret_cast<uint4*>(a.V);
+    uint4* S4 = reinterpret_cast<uint4*>(a.S);
     uint4* N4 = reinterpret_cast<uint4*>(a.N);
     uint4* F4 = reinterpret_cast<uint4*>(a.F);
     const uint4 z = make_uint4(0u, 0u, 0u, 0u);
     const bool clear_f = a.direction != 1;  // a push into F (level 2) needs it zero
     for (long long i = tid; i < words4; i += nthr) {
-        V4[i] = z;
+        S4[i] = z;
         N4[i] = z;
         if (clear_f) F4[i] = z;
     }
@@ -202,14 +205,14 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
     if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
 }
 
-// Phase 1: seed V with the sources (level 0), push level 1 into N, and take
+// Phase 1: seed S with the sources (level 0), push level 1 into N, and take
 // the level-1 kNN entries straight from each source's sorted CSR row.
 __device__ void phase_seed(const MsbfsArgs& a) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long nthr = (long long)gridDim.x * blockDim.x;
     for (long long j = tid; j < a.nb; j += nthr) {
         const int s = a.src[j];
-        if (s >= 0 && s < a.n) atomicOr(&a.V[(size_t)s * a.W + (j >> 5)], 1u << (j & 31));
+        if (s >= 0 && s < a.n) atomicOr(&a.S[(size_t)s * a.W + (j >> 5)], 1u << (j & 31));
     }
     const int lane = threadIdx.x & 31;
     const long long warp = tid >> 5;
@@ -281,7 +284,8 @@ __device__ __forceinline__ uint2 vwarp_or(uint2 a) {
 template <typename T>
 __device__ __forceinline__ bool vcovers(T acc, T todo) { return !vnz(vandnot(todo, acc)); }
 
-// Pull step of level d (see file comment), with items of GW words. Also
+// Pull step of level d (see file comment), with items of GW words. At level
+// 2 the frontier F (level 1) is not yet in S: it is ORed in here. Also
 // measures, for the choice of the next level's direction, the edges of the
 // new frontier (sum of deg(v) over nonzero (v, group) items: what a push
 // would touch) and of the items still unvisited (what the next pull would
@@ -298,7 +302,8 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     const long long nthr = (long long)gridDim.x * blockDim.x;
     const VT* FV = reinterpret_cast<const VT*>(Fc);
     VT* NV = reinterpret_cast<VT*>(Nc);
-    VT* VV = reinterpret_cast<VT*>(a.V);
+    VT* SV = reinterpret_cast<VT*>(a.S);
+    const bool fold = d == 2;
     const VT* actV = reinterpret_cast<const VT*>(a.act);
     const VT zero = vzero(VT{});
     int any = 0;
@@ -310,8 +315,9 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const int g = (int)(it - (long long)h * G);
         const int v = __ldg(a.heavy + h);
         const size_t off = (size_t)v * G + g;
-        const VT vis = vor(vld(VV + off), vld(FV + off));
-        const VT todo = vandnot(vld(actV + g), vis);
+        const VT s0 = vld(SV + off);
+        const VT seen = fold ? vor(s0, vld(FV + off)) : s0;
+        const VT todo = vandnot(vld(actV + g), seen);
         VT acc = zero;
         if (vnz(todo)) {
             const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
@@ -333,7 +339,8 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         }
         if (lane == 0) {
             NV[off] = acc;
-            VV[off] = vis;
+            const VT s1 = vor(seen, acc);
+            if (vnz(vandnot(s1, s0))) SV[off] = s1;
             any |= vnz(acc) ? 1 : 0;
         }
     }
@@ -346,8 +353,9 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const int v = __ldg(a.light + li);
         const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
         const size_t off = (size_t)v * G + g;
-        const VT vis = vor(vld(VV + off), vld(FV + off));
-        const VT todo = vandnot(vld(actV + g), vis);
+        const VT s0 = vld(SV + off);
+        const VT seen = fold ? vor(s0, vld(FV + off)) : s0;
+        const VT todo = vandnot(vld(actV + g), seen);
         VT acc = zero;
         if (vnz(todo)) {
             const VT* fg = FV + g;
@@ -368,7 +376,8 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
             if (vnz(vandnot(todo, acc))) ue += dv;
         }
         NV[off] = acc;
-        VV[off] = vis;
+        const VT s1 = vor(seen, acc);
+        if (vnz(vandnot(s1, s0))) SV[off] = s1;
         any |= vnz(acc) ? 1 : 0;
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
@@ -420,17 +429,21 @@ __device__ void phase_push_prep(const MsbfsArgs& a, const uint32_t* __restrict__
 }
 
 // Push step of level d: one warp per (frontier vertex u, group g), lanes over
-// u's neighbours v, each ORing F[u][g] & act & ~(V[v] | F[v]) into N[v][g];
-// v joins queue d the first time it gains a bit. F[u][g] is folded into
-// V[u][g] here (a pull does that for every item).
+// u's neighbours v, each ORing F[u][g] & act & ~S[v] into N[v][g] and S[v][g];
+// v joins queue d the first time it gains a bit. Bits that another warp
+// adds to S[v] during the level are already in N[v], so reading S[v] while
+// it grows loses nothing. At level 2 the level-1 frontier is not yet in S:
+// each queue item folds F[u][g] into S[u][g] (atomically, as other warps
+// may be adding to the same row) and the mask also excludes F[v].
 __device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc, int d) {
     const int G = a.W >> 2;
     const int lane = threadIdx.x & 31;
     const long long gwarp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
-    uint4* V4 = reinterpret_cast<uint4*>(a.V);
+    const uint4* S4 = reinterpret_cast<const uint4*>(a.S);
     const uint4* act4 = reinterpret_cast<const uint4*>(a.act);
+    const bool fold = d == 2;
     const int32_t* qin = a.queue + (size_t)((d - 1) % 4) * a.n;
     int32_t* qout = a.queue + (size_t)(d % 4) * a.n;
     const long long items = (long long)ld_volatile_i32(&a.ctr->qcnt[(d - 1) % 4]) * G;
@@ -447,7 +460,13 @@ __device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const size_t uo = (size_t)u * G + g;
         const uint4 f = ldcg4(F4 + uo);
         if (!nz4(f)) continue;
-        if (lane == 0) V4[uo] = or4(ldcg4(V4 + uo), f);
+        if (fold && lane == 0) {
+            uint32_t* su = a.S + uo * 4;
+            if (f.x) atomicOr(su + 0, f.x);
+            if (f.y) atomicOr(su + 1, f.y);
+            if (f.z) atomicOr(su + 2, f.z);
+            if (f.w) atomicOr(su + 3, f.w);
+        }
         const uint4 fa = and4(f, ldcg4(act4 + g));
         if (!nz4(fa)) continue;
         const int e0 = __ldg(a.row_ptr + u), e1 = __ldg(a.row_ptr + u + 1);
@@ -457,14 +476,20 @@ __device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
             bool want = false;
             if (e < e1) {
                 const size_t vo = (size_t)v * G + g;
-                const uint4 m = andnot4(fa, or4(ldcg4(V4 + vo), ldcg4(F4 + vo)));
+                const uint4 sv = ldcg4(S4 + vo);
+                const uint4 m = andnot4(fa, fold ? or4(sv, ldcg4(F4 + vo)) : sv);
                 if (nz4(m)) {
                     uint32_t* nw = Nc + vo * 4;
+                    uint32_t* sw = a.S + vo * 4;
                     bool fresh = true;
                     if (m.x) fresh &= atomicOr(nw + 0, m.x) == 0u;
                     if (m.y) fresh &= atomicOr(nw + 1, m.y) == 0u;
                     if (m.z) fresh &= atomicOr(nw + 2, m.z) == 0u;
                     if (m.w) fresh &= atomicOr(nw + 3, m.w) == 0u;
+                    if (m.x) atomicOr(sw + 0, m.x);
+                    if (m.y) atomicOr(sw + 1, m.y);
+                    if (m.z) atomicOr(sw + 2, m.z);
+                    if (m.w) atomicOr(sw + 3, m.w);
                     if (fresh) fe += (unsigned long long)(__ldg(a.row_ptr + v + 1) - __ldg(a.row_ptr + v));
                     any = 1;
                     want = ld_volatile_i32(a.inq + v) != d && atomicExch(a.inq + v, d) != d;
@@ -538,7 +563,7 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
 }
 
 template <int GW>
-__global__ void __launch_bounds__(256) msbfs_kernel(MsbfsArgs a) {
+__global__ void __launch_bounds__(256, 3) msbfs_kernel(MsbfsArgs a) {
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
     unsigned long long t_prev = timer ? globaltimer_ns() : 0ull;
     unsigned long long t_init = 0, t_pull = 0, t_extract = 0, t_push = 0;

@@ -122,7 +122,7 @@ extern "C" int gumap_knn_run_noalloc(const int32_t* row_ptr, const int32_t* col_
         a.W = W;
         a.F = bits;
         a.N = bits + words;
-        a.V = bits + 2 * words;
+        a.S = bits + 2 * words;
         a.heavy = order;
         a.n_heavy = 0;
         a.light = order;

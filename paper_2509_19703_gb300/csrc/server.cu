@@ -388,7 +388,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
             a.W = W;
             a.F = bits;
             a.N = bits + words;
-            a.V = bits + 2 * words;
+            a.S = bits + 2 * words;
             a.heavy = order;
             a.n_heavy = 0;
             a.light = order;
