@@ -84,11 +84,18 @@ extern "C" {
 #define GUMAP_OPT_PROFILE     3 /* value: 1 = time each BFS launch with CUDA events       */
 #define GUMAP_OPT_STATE_BYTES 4 /* value: device bytes allowed for MS-BFS bitsets, 0 = auto */
 #define GUMAP_OPT_HEAVY_DEGREE 5 /* value: MS-BFS vertices of larger degree are processed by a whole warp
-                                    (default 64); setting it synchronises the device */
-#define GUMAP_OPT_DIRECTION   6 /* value: MS-BFS level direction: 0 = choose per level (default),
-                                   1 = pull only, 2 = push from level 2 on                      */
+                                    (default max(64, 4 x mean degree)); setting it synchronises the device */
+#define GUMAP_OPT_DIRECTION   6 /* value: MS-BFS level direction: 0 = choose per level,
+                                   1 = pull only (default), 2 = push from level 2 on            */
 #define GUMAP_OPT_PUSH_DIV    7 /* value: push when frontier edges * value < unvisited edges (default 8) */
 #define GUMAP_OPT_PULL_WIDTH  8 /* value: 32-bit words per MS-BFS pull item, 4 (default) or 2     */
+#define GUMAP_OPT_CTAS_PER_SM 9 /* value: resident 256-thread MS-BFS CTAs per SM the kernel is built
+                                   for: 3 (default, up to 80 registers a thread) or 4 (64)        */
+#define GUMAP_OPT_STAGE      10 /* value: 1 (default) = each MS-BFS CTA bulk-copies its slice of the
+                                   ordinary-degree rows into shared memory once per launch when
+                                   every slice fits; 0 = neighbour ids always read from the CSR;
+                                   2 = (tests) the staged kernel reads its slice from global memory,
+                                   the path it takes when a bulk copy does not complete           */
 
 typedef struct gumap_knn gumap_knn;
 
@@ -219,6 +226,7 @@ typedef struct {
     double  bfs_extract_ms;  /* MS-BFS device time in the kNN extraction steps */
     double  bfs_push_ms;     /* MS-BFS device time in push levels (queue preparation + push) */
     int64_t bfs_push_levels; /* MS-BFS levels run as a push since the last reset */
+    int64_t bfs_staged_launches; /* MS-BFS launches whose rows were staged in shared memory */
 } gumap_knn_stats;
 
 typedef struct {
@@ -241,14 +249,17 @@ typedef struct {
     double default_ms;       /* ... with the settings the handle had before */
     int32_t engine, pull_width, heavy_mult, direction;
     int64_t state_bytes;
+    int32_t ctas_per_sm;
+    int32_t stage;
 } gumap_tune_result;
 
 /*
  * gumap_knn_autotune - pick the engine settings for this handle's graph by
  * timing gumap_knn_run (all vertices) on it: MS-BFS state budget (which
  * sets the source-block width), pull item width, heavy-vertex degree
- * multiplier and level direction for the full form; engine for the partial
- * form. The best settings are applied to the handle and, if cache_path is
+ * multiplier, CTAs per SM (the CTA shape: registers per thread against
+ * resident warps), staging of rows in shared memory and level direction for
+ * the full form; engine for the partial form. The best settings are applied to the handle and, if cache_path is
  * not NULL, appended to that JSON-lines file under a key of the graph's
  * shape class (form, k, log2 n, log2 mean degree, hub ratio); a later
  * handle of the same class created while the environment variable

@@ -151,9 +151,11 @@ struct gumap_knn {
     int mode = GUMAP_FULL;
     uint32_t flags = 0;
     int num_sms = 0;
-    int coop_grid = 0;     // resident CTAs of the MS-BFS kernel with 128-bit pull items
-    int coop_grid2 = 0;    // ... with 64-bit pull items
+    int coop_grid[2][2] = {};  // resident MS-BFS CTAs: [64-bit pull items][4 CTAs per SM build]
     int opt_pull_width = 4;
+    int opt_ctas_per_sm = 3;   // GUMAP_OPT_CTAS_PER_SM
+    int opt_stage = 1;         // GUMAP_OPT_STAGE
+    int stage_cap[2] = {};     // dynamic shared memory a staged launch may use: [4 CTAs per SM build]
 
     int32_t* d_rp = nullptr;
     int32_t* d_col = nullptr;
@@ -161,6 +163,21 @@ struct gumap_knn {
     int32_t* d_order = nullptr;  // MS-BFS processing order (heavy vertices first)
     int32_t n_heavy = 0;
     int32_t heavy_deg = 64;
+    // staged pull (see MsbfsArgs): the light vertices in processing order
+    // (host copy) and, per grid size used so far, the CTA-major layout of
+    // their rows: CTA b owns positions b, b + grid, b + 2 grid, ... (every
+    // CTA gets the same mix of degrees), stored contiguously per CTA
+    std::vector<int32_t> light_order;
+    struct SliceCut {
+        int grid;
+        int32_t* d_cut;    // [grid + 1] first pair of each CTA
+        int2* d_meta;      // (vertex, ocol offset) per position, CTA-major, + 3 of padding
+        int32_t* d_ocol;   // the rows in that order, + 4 of padding
+        size_t meta_bytes, ocol_bytes;
+        int bytes;         // shared memory of the largest CTA share, rounded up to 1 KB
+    };
+    std::vector<SliceCut> cuts;
+    int64_t staged_launches = 0;
     std::vector<int32_t> deg;    // host copy of the vertex degrees
     DeviceCounters* d_ctr = nullptr;
 
@@ -238,6 +255,7 @@ void release(DevBuf& b) {
 
 size_t held_bytes(const gumap_knn* h) {
     size_t t = (size_t)(h->n + 1) * 4 + (size_t)h->nnz * 4 + (size_t)h->n * 4 + sizeof(DeviceCounters);
+    for (const auto& c : h->cuts) t += (size_t)(c.grid + 1) * 4 + c.meta_bytes + c.ocol_bytes;
     const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
                           &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
     for (const DevBuf* b : bs) t += b->bytes;
@@ -283,16 +301,13 @@ int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b) {
     return GUMAP_OK;
 }
 
-// Processing order of the MS-BFS pull: vertices of degree > heavy_deg
-// (warp-wide items) then the rest, each by decreasing degree (a counting
-// sort on the host degrees, stable in vertex id). Synchronous upload.
 // Per-device launch limits of the MS-BFS kernel, queried once per device
 // (the attribute and occupancy queries cost more than the rest of creating
 // a small handle). The caller has made `device` current.
 struct LaunchLimits {
     int sms = 0;
-    int per_sm4 = 0;  // resident CTAs per SM with 128-bit pull items
-    int per_sm2 = 0;  // ... with 64-bit pull items
+    int per_sm[2][2] = {};  // resident CTAs per SM: [64-bit pull items][4 CTAs per SM build]
+    int stage_cap[2] = {};  // dynamic shared memory per CTA that keeps that residency: [4 CTAs per SM build]
 };
 
 int launch_limits(int device, LaunchLimits& out) {
@@ -305,15 +320,49 @@ int launch_limits(int device, LaunchLimits& out) {
     }
     LaunchLimits l;
     CK(cudaDeviceGetAttribute(&l.sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
-    l.per_sm4 = msbfs_max_blocks_per_sm(256);
-    l.per_sm2 = msbfs_max_blocks_per_sm(256, 2);
-    if (l.sms <= 0 || l.per_sm4 <= 0 || l.per_sm2 <= 0) return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident");
+    for (int w = 0; w < 2; ++w)
+        for (int c = 0; c < 2; ++c) {
+            l.per_sm[w][c] = msbfs_max_blocks_per_sm(256, w ? 2 : 4, c ? 4 : 3);
+            if (l.per_sm[w][c] <= 0) return fail(GUMAP_ERR_CUDA, "msbfs kernel cannot be resident");
+        }
+    if (l.sms <= 0) return fail(GUMAP_ERR_CUDA, "no SMs");
+    // the shared memory of an SM split over the resident CTAs, less the
+    // per-CTA reservation and the kernel's static arrays, in whole KB; then
+    // checked (and lowered if needed) against the occupancy calculator
+    int smem_sm = 0, reserved = 0, smem_block_optin = 0;
+    CK(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device), "device attribute");
+    CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device), "device attribute");
+    CK(cudaDeviceGetAttribute(&smem_block_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device), "device attribute");
+    const int want3 = std::min(smem_block_optin, ((smem_sm / 3 - reserved - 512) / 1024) * 1024);
+    CK(msbfs_allow_smem(want3), "kernel shared memory attribute");
+    for (int c = 0; c < 2; ++c) {
+        const int ctas = c ? 4 : 3;
+        int cap = std::min(want3, ((smem_sm / ctas - reserved - 512) / 1024) * 1024);
+        while (cap >= 16384 && (msbfs_max_blocks_per_sm(256, 4, ctas, (size_t)cap, true) < l.per_sm[0][c] ||
+                                msbfs_max_blocks_per_sm(256, 2, ctas, (size_t)cap, true) < l.per_sm[1][c]))
+            cap -= 4096;
+        l.stage_cap[c] = cap >= 16384 ? cap : 0;
+    }
     if (cache.size() <= (size_t)device) cache.resize((size_t)device + 1);
     cache[(size_t)device] = l;
     out = l;
     return GUMAP_OK;
 }
 
+void free_cuts(gumap_knn* h) {
+    for (auto& c : h->cuts) {
+        pool_free(c.d_cut, (size_t)(c.grid + 1) * 4);
+        pool_free(c.d_meta, c.meta_bytes);
+        pool_free(c.d_ocol, c.ocol_bytes);
+    }
+    h->cuts.clear();
+}
+
+// Processing order of the MS-BFS pull: vertices of degree > heavy_deg
+// (warp-wide items) then the rest, each by decreasing degree (a counting
+// sort on the host degrees, stable in vertex id). Synchronous upload. The
+// staged layouts of the previous order are dropped: the caller guarantees
+// no launch still uses them.
 int build_order(gumap_knn* h) {
     const int32_t n = h->n;
     int32_t maxd = 0;
@@ -326,10 +375,64 @@ int build_order(gumap_knn* h) {
     while (nh < n && h->deg[order[(size_t)nh]] > h->heavy_deg) ++nh;
     h->n_heavy = nh;
     CK(cudaMemcpy(h->d_order, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice), "order upload");
+
+    h->light_order.assign(order.begin() + nh, order.end());
+    free_cuts(h);
     return GUMAP_OK;
 }
 
-int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
+// The staged layout for a launch of `grid` CTAs (see the handle's
+// SliceCut): CTA b's positions b, b + grid, ... stored contiguously, their
+// (vertex, offset) pairs uploaded and their rows gathered on stream st.
+// Built at the first launch with that grid size, then kept.
+int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut** out) {
+    for (const auto& c : h->cuts)
+        if (c.grid == grid) {
+            *out = &c;
+            return GUMAP_OK;
+        }
+    const int64_t nl = (int64_t)h->light_order.size();
+    std::vector<int2> meta((size_t)nl + 3);
+    std::vector<int32_t> cut((size_t)grid + 1);
+    int64_t off = 0, i = 0;
+    long long worst = 0;
+    for (int b = 0; b < grid; ++b) {
+        cut[(size_t)b] = (int32_t)i;
+        const int64_t i0 = i, off0 = off;
+        for (int64_t p = b; p < nl; p += grid) {
+            const int32_t v = h->light_order[(size_t)p];
+            meta[(size_t)i++] = make_int2(v, (int)off);
+            off += h->deg[(size_t)v];
+        }
+        worst = std::max(worst, stage_slice_bytes(i0, i, off0, off));
+    }
+    cut[(size_t)grid] = (int32_t)i;
+    for (int64_t j = nl; j < nl + 3; ++j) meta[(size_t)j] = make_int2(0, (int)off);
+    gumap_knn::SliceCut c{grid, nullptr, nullptr, nullptr, sizeof(int2) * meta.size(),
+                          sizeof(int32_t) * ((size_t)off + 4),
+                          (int)std::min<long long>(((worst + 1023) / 1024) * 1024, 1 << 30)};
+    cudaError_t e;
+    if ((e = pool_alloc((void**)&c.d_cut, (size_t)(grid + 1) * 4)) != cudaSuccess ||
+        (e = pool_alloc((void**)&c.d_meta, c.meta_bytes)) != cudaSuccess ||
+        (e = pool_alloc((void**)&c.d_ocol, c.ocol_bytes)) != cudaSuccess) {
+        pool_free(c.d_cut, (size_t)(grid + 1) * 4);
+        pool_free(c.d_meta, c.meta_bytes);
+        pool_free(c.d_ocol, c.ocol_bytes);
+        return cuda_fail(e, "cudaMalloc");
+    }
+    h->cuts.push_back(c);  // owned by the handle from here on (freed with it)
+    CK(cudaMemcpyAsync(c.d_cut, cut.data(), (size_t)(grid + 1) * 4, cudaMemcpyHostToDevice, st), "cut upload");
+    CK(cudaMemcpyAsync(c.d_meta, meta.data(), c.meta_bytes, cudaMemcpyHostToDevice, st), "pairs upload");
+    CK(cudaMemsetAsync(c.d_ocol + off, 0, 4 * sizeof(int32_t), st), "row padding");
+    CK(launch_gather_rows(h->d_rp, h->d_col, c.d_meta, (int32_t)nl, c.d_ocol, st), "gather rows");
+    // the host vectors go out of scope: make sure the copies have read them
+    CK(cudaStreamSynchronize(st), "layout upload");
+    *out = &h->cuts.back();
+    return GUMAP_OK;
+}
+
+// identity: src is the handle's 0 .. n-1 (all vertices as sources)
+int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
               cudaStream_t st) {
     const int S = choose_block_bits(h, n_src);
     if (S % 128 != 0 || S <= 0) return fail(GUMAP_ERR_INVALID_ARG, "block bits must be a positive multiple of 128");
@@ -350,6 +453,8 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.col = h->d_col;
         a.n = h->n;
         a.src = src + (size_t)b * S;
+        a.identity = identity ? 1 : 0;
+        a.src_lo = b * S;
         a.nb = std::min<int32_t>(S, n_src - b * S);
         a.W = W;
         a.F = base;
@@ -370,15 +475,30 @@ int run_msbfs(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_idx,
         a.direction = h->opt_direction;
         a.push_div = h->opt_push_div;
         a.pull_width = h->opt_pull_width;
+        a.ctas_per_sm = h->opt_ctas_per_sm;
         a.queue = reinterpret_cast<int32_t*>(base + 3 * words);
         a.inq = a.queue + 4 * (size_t)h->n;
-        CK(cudaMemsetAsync(&h->d_ctr->bar, 0, sizeof(GridBarrier), st), "reset barrier");
+        const int grid = msbfs_grid_for(a, h->coop_grid[a.pull_width == 2][a.ctas_per_sm == 4]);
+        const int cap = h->stage_cap[a.ctas_per_sm == 4];
+        if (h->opt_stage && h->n > h->n_heavy && cap > 0) {
+            const gumap_knn::SliceCut* c = nullptr;
+            if ((rc = get_cut(h, grid, st, &c))) return rc;
+            if (c->bytes <= cap) {
+                a.staged = h->opt_stage;
+                a.stage_bytes = c->bytes;
+                a.meta = c->d_meta;
+                a.ocol = c->d_ocol;
+                a.slice = c->d_cut;
+                h->staged_launches++;
+            }
+        }
+        CK(cudaMemsetAsync(h->d_ctr, 0, kLaunchCounterBytes, st), "reset barrier");
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         if (h->opt_profile) {
             if ((rc = next_event_pair(h, &e0, &e1))) return rc;
             CK(cudaEventRecord(e0, st), "cudaEventRecord");
         }
-        CK(launch_msbfs(a, msbfs_grid_for(a, a.pull_width == 2 ? h->coop_grid2 : h->coop_grid), 256, st),
+        CK(launch_msbfs(a, grid, 256, st),
            "msbfs launch");
         if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
         h->bfs_launches++;
@@ -474,6 +594,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     pool_free(h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz, 1));
     pool_free(h->d_identity, sizeof(int32_t) * (size_t)h->n);
     pool_free(h->d_order, sizeof(int32_t) * (size_t)h->n);
+    free_cuts(h);
     pool_free(h->d_units, sizeof(BatchUnit) * (size_t)std::max<int32_t>(h->n_units, 1));
     release(h->vslab);
     pool_free(h->d_ctr, sizeof(DeviceCounters));
@@ -519,8 +640,10 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
         return lrc;
     }
     h->num_sms = lim.sms;
-    h->coop_grid = lim.sms * lim.per_sm4;
-    h->coop_grid2 = lim.sms * lim.per_sm2;
+    for (int w = 0; w < 2; ++w)
+        for (int c = 0; c < 2; ++c) h->coop_grid[w][c] = lim.sms * lim.per_sm[w][c];
+    h->stage_cap[0] = lim.stage_cap[0];
+    h->stage_cap[1] = lim.stage_cap[1];
     cudaError_t e;
 
     const cudaMemcpyKind kind = (flags & GUMAP_CSR_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -685,7 +808,7 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
     const int engine = pick_engine(h);
     h->last_engine = engine;
     if (engine == GUMAP_ENGINE_MSBFS) {
-        rc = run_msbfs(h, src, n_src, out_idx, out_dist, st);
+        rc = run_msbfs(h, src, sources == nullptr, n_src, out_idx, out_dist, st);
     } else if (engine == GUMAP_ENGINE_FRONTIER) {
         if (h->mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
         rc = run_frontier(h, src, n_src, out_idx, out_dist, st);
@@ -704,11 +827,11 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
     h->kernel_launches++;
     if (want_union) {
         const long long cnt = 2ll * n_src * k;
+        const int B = key_bits_for(h->n);
         if ((rc = ensure(h->keys, cnt * 8, "coo keys")) || (rc = ensure(h->vals, cnt * 4, "coo vals")) ||
             (rc = ensure(h->keys_tmp, cnt * 8, "coo keys tmp")) || (rc = ensure(h->vals_tmp, cnt * 4, "coo vals tmp")) ||
             (rc = ensure(h->sort_temp, radix_sort_temp_bytes(cnt), "sort temp")))
             return rc;
-        const int B = key_bits_for(h->n);
         CK(cudaMemsetAsync(&h->d_ctr->coo_nnz, 0, sizeof(unsigned long long), st), "memset nnz");
         CK(launch_union(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, B,
                         static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), h->d_ctr, st),
@@ -811,6 +934,14 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             if (value != 2 && value != 4) return fail(GUMAP_ERR_INVALID_ARG, "pull width must be 2 or 4 words");
             h->opt_pull_width = (int)value;
             return GUMAP_OK;
+        case GUMAP_OPT_STAGE:
+            if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "stage must be 0, 1 or 2");
+            h->opt_stage = (int)value;
+            return GUMAP_OK;
+        case GUMAP_OPT_CTAS_PER_SM:
+            if (value != 0 && value != 3 && value != 4) return fail(GUMAP_ERR_INVALID_ARG, "CTAs per SM must be 3 or 4");
+            h->opt_ctas_per_sm = value == 4 ? 4 : 3;
+            return GUMAP_OK;
         case GUMAP_OPT_PUSH_DIV:
             if (value < 1 || value > (1 << 20)) return fail(GUMAP_ERR_INVALID_ARG, "push divisor out of range");
             h->opt_push_div = (int)value;
@@ -820,7 +951,9 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             CK(cudaSetDevice(h->device), "cudaSetDevice");
             CK(cudaDeviceSynchronize(), "sync");
             h->heavy_deg = (int32_t)value;
-            return build_order(h);
+            if (int rc = build_order(h)) return rc;
+            CK(cudaDeviceSynchronize(), "sync");  // the rows gathered on the legacy stream are ready for any stream
+            return GUMAP_OK;
         default:
             return fail(GUMAP_ERR_INVALID_ARG, "unknown option %d", option);
     }
@@ -867,6 +1000,7 @@ int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
     out->bfs_extract_ms = (double)c.t_extract_ns * 1e-6;
     out->bfs_push_ms = (double)c.t_push_ns * 1e-6;
     out->bfs_push_levels = c.push_levels;
+    out->bfs_staged_launches = h->staged_launches;
     return GUMAP_OK;
 }
 
@@ -876,6 +1010,7 @@ int gumap_knn_reset_stats(gumap_knn* h) {
     CK(cudaDeviceSynchronize(), "sync");
     h->bfs_launches = 0;
     h->kernel_launches = 0;
+    h->staged_launches = 0;
     h->bfs_ms_done = 0.0;
     h->ev_used = 0;
     DeviceCounters c;

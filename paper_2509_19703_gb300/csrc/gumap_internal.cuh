@@ -2,6 +2,7 @@
 // Nothing here is part of the public ABI (include/gumap.h).
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -19,18 +20,27 @@ constexpr unsigned long long kWaitLimitNs = 10ull * 1000ull * 1000ull * 1000ull;
 // Status values written by kernels into DeviceCounters::status.
 constexpr int kStatusTimeout = 7;     // == GUMAP_ERR_TIMEOUT
 constexpr int kStatusBadSource = 1;   // == GUMAP_ERR_INVALID_ARG (a source id outside [0, n))
+constexpr int kStatusInternal = 4;    // == GUMAP_ERR_CUDA (device data disagrees with a host-side check)
 
 struct GridBarrier {
     unsigned int count;
     unsigned int gen;
 };
 
-// Small per-handle block of device counters; zeroed at handle creation.
+// Small per-handle block of device counters; zeroed at handle creation. The
+// fields before `status` belong to one MS-BFS launch: the host zeroes them
+// (kLaunchCounterBytes) on the launch's stream before every launch.
 struct DeviceCounters {
     GridBarrier bar;
-    int32_t status;
     int32_t n_need;            // sources of the running block whose list is incomplete
     uint32_t lvl_any[3];       // "some vertex was reached at level d" in slot d % 3
+    // direction choice of the MS-BFS levels (slot d % 4 belongs to level d)
+    int32_t qcnt[4];                 // vertices in the frontier queue of level d
+    int32_t qvalid[4];               // 1 if that queue was built
+    unsigned long long f_edges[4];   // sum of deg(v) over nonzero (v, group) items of level d
+    unsigned long long u_edges[4];   // sum of deg(v) over (v, group) items left unvisited after a pull
+    // ---- kept across launches
+    int32_t status;
     int32_t levels;            // deepest level reached by the last MS-BFS launch
     int32_t levels_max;        // max over launches since the last host reset
     int32_t aux_count;         // scratch counter of the set-up kernels
@@ -41,14 +51,10 @@ struct DeviceCounters {
     unsigned long long t_init_ns;
     unsigned long long t_pull_ns;
     unsigned long long t_extract_ns;
-    // direction choice of the MS-BFS levels (slot d % 4 belongs to level d)
-    int32_t qcnt[4];                 // vertices in the frontier queue of level d
-    int32_t qvalid[4];               // 1 if that queue was built
-    unsigned long long f_edges[4];   // sum of deg(v) over nonzero (v, group) items of level d
-    unsigned long long u_edges[4];   // sum of deg(v) over (v, group) items left unvisited after a pull
     long long push_levels;           // push levels run since the last host reset
     unsigned long long t_push_ns;    // device time of push levels (prep + push)
 };
+constexpr size_t kLaunchCounterBytes = offsetof(DeviceCounters, status);
 
 // Arguments of one multi-source BFS launch over a block of sources.
 struct MsbfsArgs {
@@ -56,6 +62,8 @@ struct MsbfsArgs {
     const int32_t* col;
     int32_t n;
     const int32_t* src;      // block's sources: vertex of bit j is src[j]
+    int32_t identity;        // 1: src[j] == src_lo + j for every j (a range of consecutive vertices)
+    int32_t src_lo;
     int32_t nb;              // sources in the block (<= 32 * W)
     int32_t W;               // 32-bit words per vertex row, multiple of 4
     uint32_t* F;             // frontier  [n][W]
@@ -83,7 +91,32 @@ struct MsbfsArgs {
     int32_t* queue;          // [4][n] frontier queues, slot d % 4
     int32_t* inq;            // [n] level at which the vertex last entered a queue
     int32_t pull_width;      // words per pull item: 4 (128 bits; also when 0) or 2 (64 bits)
+    int32_t ctas_per_sm;     // kernel build: 3 (also when 0) or 4 resident CTAs per SM
+    // Staged pull (staged = 1): the rows of the light vertices in processing
+    // order (ocol) with per-position (vertex, offset into ocol) pairs (meta:
+    // n_light + 1 entries used, 2 more of padding; ocol has 4 ints of
+    // padding), cut into one slice of positions per CTA, [slice[b],
+    // slice[b + 1]). Each CTA bulk-copies its slice into shared memory once
+    // per launch and reads every level's neighbour ids from there; the host
+    // has checked that each slice fits stage_bytes. staged = 0: rows are
+    // read from the global CSR.
+    const int2* meta;
+    const int32_t* ocol;
+    const int32_t* slice;
+    int32_t staged;          // 2: staged build reading the slice from global memory (the path
+                             // taken when a copy does not complete; for tests)
+    int32_t stage_bytes;     // dynamic shared memory of the launch (0 when not staged)
 };
+
+// Shared-memory bytes one CTA's staged slice takes (the kernel rounds the
+// same way): the (vertex, offset) pairs of positions [p0, p1] from an even
+// index, and the neighbour ids [c0, c1) from a multiple of 4, so both
+// copies start and end on 16-byte boundaries.
+inline long long stage_slice_bytes(long long p0, long long p1, long long c0, long long c1) {
+    const long long m = (((p1 + 2) & ~1ll) - (p0 & ~1ll)) * 8;
+    const long long c = (((c1 + 3) & ~3ll) - (c0 & ~3ll)) * 4;
+    return m + c;
+}
 
 // Arguments of one partial-BFS launch with one warp per source.
 struct FrontierArgs {
@@ -151,7 +184,12 @@ const void* batch_kernel_ptr();
 cudaError_t launch_batch(const BatchArgs& a, int grid, size_t smem_bytes, cudaStream_t s);
 
 // ---- msbfs.cu
-int msbfs_max_blocks_per_sm(int block_threads, int pull_width = 4);
+int msbfs_max_blocks_per_sm(int block_threads, int pull_width = 4, int ctas_per_sm = 3, size_t dyn_smem = 0,
+                            bool staged = false);
+// Allows the kernel builds up to `bytes` of dynamic shared memory.
+cudaError_t msbfs_allow_smem(int bytes);
+cudaError_t launch_gather_rows(const int32_t* row_ptr, const int32_t* col, const int2* meta, int32_t n_pos,
+                               int32_t* ocol, cudaStream_t s);
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);
 int msbfs_grid_for(const MsbfsArgs& a, int max_grid);
 cudaError_t launch_identity(int32_t* dst, int32_t n, cudaStream_t s);

@@ -67,6 +67,53 @@ __device__ __forceinline__ unsigned ld_volatile_u32(const uint32_t* p) {
     return *reinterpret_cast<const volatile uint32_t*>(p);
 }
 
+// ---- bulk copy global -> shared (TMA engine), completion on an mbarrier
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the async (bulk-copy) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// dst, src 16-byte aligned, bytes a nonzero multiple of 16
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Waits for phase `parity` of the barrier for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  unsigned long long limit_ns) {
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
 // Grid-wide barrier for a cooperative launch. Thread 0 of each CTA arrives
 // on a counter; the last arrival bumps the generation. Waiters poll the
 // generation for at most limit_ns, then record a timeout and return false
@@ -163,17 +210,8 @@ __device__ void phase_init(const MsbfsArgs& a) {
         a.out_dist[i] = kDistInf;
     }
     for (long long i = tid; i < a.nb; i += nthr) a.cnt[i] = 0;
-    if (tid == 0) {
+    if (tid == 0) {  // the other per-launch counters were zeroed by the host
         a.ctr->n_need = a.nb;
-        a.ctr->lvl_any[0] = 0u;
-        a.ctr->lvl_any[1] = 0u;
-        a.ctr->lvl_any[2] = 0u;
-        for (int q = 0; q < 4; ++q) {
-            a.ctr->qcnt[q] = 0;
-            a.ctr->qvalid[q] = 0;
-            a.ctr->f_edges[q] = 0ull;
-            a.ctr->u_edges[q] = 0ull;
-        }
         a.ctr->qvalid[0] = 1;  // F was cleared: the buffer level 2 writes holds no row
         a.ctr->u_edges[0] = (unsigned long long)__ldg(a.row_ptr + a.n) * (unsigned long long)(a.W >> 2);
     }
@@ -203,6 +241,118 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
     if ((threadIdx.x & 31) == 0 && x) atomicAdd(&s_acc, x);
     __syncthreads();
     if (threadIdx.x == 0 && s_acc) atomicAdd(dst, s_acc);
+}
+
+// Phases 0 and 1 in one pass for a block whose sources are the consecutive
+// vertices src_lo .. src_lo + nb - 1 (every run over all vertices). Level 1
+// is computed as a pull instead of pushed: N[v] = the block's sources
+// adjacent to v, read off v's sorted row (one warp per vertex, 4096 source
+// bits per round, each neighbour read once), and S[v] = v's own bit; both
+// rows are written in full, so nothing is cleared first and no atomics touch
+// the bitsets. Each source's level-1 kNN entries (the first k of its row)
+// and padding are written by one warp, the act/need masks one 32-source word
+// per warp. The per-launch counters were zeroed by the host.
+__device__ void phase_init_identity(const MsbfsArgs& a) {
+    __shared__ __align__(16) uint32_t s_chunk[8][128];  // per warp: 128 words = 4096 source bits
+    const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nthr = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const long long gwarp = gtid >> 5, nwarps = nthr >> 5;
+    uint32_t* sc = s_chunk[(threadIdx.x >> 5) & 7];
+    const int G4 = a.W >> 2;
+    const int chunks = (a.W + 127) >> 7;
+    uint4* N4 = reinterpret_cast<uint4*>(a.N);
+    uint4* S4 = reinterpret_cast<uint4*>(a.S);
+    uint4* F4 = reinterpret_cast<uint4*>(a.F);
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    const bool clear_f = a.direction != 1;  // a push into F (level 2) needs it zero
+    const long long src_hi = (long long)a.src_lo + a.nb;
+    int any = 0;
+    unsigned long long fe = 0ull;
+    for (long long v = gwarp; v < a.n; v += nwarps) {
+        const int r0 = __ldg(a.row_ptr + v), r1 = __ldg(a.row_ptr + v + 1);
+        int lo = r0, hi = r1;  // first neighbour >= src_lo
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (__ldg(a.col + mid) < a.src_lo) lo = mid + 1;
+            else hi = mid;
+        }
+        int e = lo;
+        const long long j = v - a.src_lo;  // v's bit in the block, if v is one of its sources
+        for (int c = 0; c < chunks; ++c) {
+            reinterpret_cast<uint4*>(sc)[lane] = z;
+            __syncwarp();
+            const long long base = (long long)a.src_lo + 4096ll * c;
+            const long long top = base + 4096 < src_hi ? base + 4096 : src_hi;
+            while (true) {  // the neighbours in [base, top) are the next entries of the sorted row
+                const int idx = e + lane;
+                const long long u = idx < r1 ? (long long)__ldg(a.col + idx) : src_hi;
+                const bool in = u < top;
+                if (in) atomicOr(&sc[(u - base) >> 5], 1u << ((u - base) & 31));
+                const unsigned m = __ballot_sync(kFull, in);
+                e += __popc(m);
+                if (m != kFull) break;
+            }
+            __syncwarp();
+            const int g = c * 32 + lane;
+            if (g < G4) {
+                const uint4 nbits = reinterpret_cast<const uint4*>(sc)[lane];
+                const size_t off = (size_t)v * G4 + g;
+                N4[off] = nbits;
+                uint4 sbits = z;
+                if (j >= 0 && j < a.nb && (j >> 7) == g) {
+                    const uint32_t bit = 1u << (j & 31);
+                    const int wi = (int)((j >> 5) & 3);
+                    sbits.x = wi == 0 ? bit : 0u;
+                    sbits.y = wi == 1 ? bit : 0u;
+                    sbits.z = wi == 2 ? bit : 0u;
+                    sbits.w = wi == 3 ? bit : 0u;
+                }
+                S4[off] = sbits;
+                if (clear_f) F4[off] = z;
+                if (nz4(nbits)) {
+                    any = 1;
+                    fe += (unsigned long long)(r1 - r0);
+                }
+            }
+            __syncwarp();
+        }
+        if (a.inq && lane == 0) a.inq[v] = 0;
+    }
+    // level-1 kNN entries of each source and the padding after them
+    for (long long jj = gwarp; jj < a.nb; jj += nwarps) {
+        const int s = a.src_lo + (int)jj;
+        const int e0 = __ldg(a.row_ptr + s), e1 = __ldg(a.row_ptr + s + 1);
+        const int take = e1 - e0 < a.k ? e1 - e0 : a.k;
+        int32_t* oi = a.out_idx + (size_t)jj * a.k;
+        uint16_t* od = a.out_dist + (size_t)jj * a.k;
+        for (int t = lane; t < a.k; t += 32) {
+            oi[t] = t < take ? __ldg(a.col + e0 + t) : -1;
+            od[t] = t < take ? (uint16_t)1 : kDistInf;
+        }
+        if (lane == 0) a.cnt[jj] = take;
+    }
+    // act / need, one word of 32 sources per warp: a source whose row holds
+    // k entries has its list; one with an empty row is finished and silent
+    for (long long w = gwarp; w < a.W; w += nwarps) {
+        const long long jj = w * 32 + lane;
+        const bool valid = jj < a.nb;
+        const int d = valid ? __ldg(a.row_ptr + a.src_lo + jj + 1) - __ldg(a.row_ptr + a.src_lo + jj) : 0;
+        const unsigned vm = __ballot_sync(kFull, valid);
+        const unsigned dm = __ballot_sync(kFull, valid && (d >= a.k || d == 0));
+        const unsigned zm = __ballot_sync(kFull, valid && d == 0);
+        if (lane == 0) {
+            a.need[w] = vm & ~dm;
+            a.act[w] = vm & ~(a.partial ? dm : zm);
+            if (vm & ~dm) atomicAdd(&a.ctr->n_need, __popc(vm & ~dm));
+        }
+    }
+    if (gtid == 0) {
+        a.ctr->qvalid[0] = 1;
+        a.ctr->u_edges[0] = (unsigned long long)__ldg(a.row_ptr + a.n) * (unsigned long long)(a.W >> 2);
+    }
+    if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[1], 1u);
+    if (a.direction == 0) block_add(fe, &a.ctr->f_edges[1]);
 }
 
 // Phase 1: seed S with the sources (level 0), push level 1 into N, and take
@@ -284,15 +434,70 @@ __device__ __forceinline__ uint2 vwarp_or(uint2 a) {
 template <typename T>
 __device__ __forceinline__ bool vcovers(T acc, T todo) { return !vnz(vandnot(todo, acc)); }
 
+// A CTA's view of its staged slice (see MsbfsArgs): mode 0 = not staged
+// (light items spread over the grid, rows from the global CSR); 1 = the
+// slice's (vertex, offset) pairs and neighbour ids in shared memory; 2 = the
+// same slice read from global memory (the bulk copy did not complete).
+struct StageView {
+    const int2* meta;     // pairs of positions p0 .. p0 + P
+    const int32_t* col;   // neighbour ids; an offset o of meta is col[o - cbase]
+    int32_t P;
+    int32_t cbase;
+    int32_t mode;
+};
+
+// One light (vertex v, group g) item of the pull: the OR of the neighbours'
+// frontier groups over the ids col[e0, e1), stopping once every missing
+// source is covered. SLICE: col is a staged slice (plain loads; shared
+// memory, or global memory when the copy failed), else the global CSR (read
+// through the read-only path). NB neighbour loads are in flight at once.
+template <int GW, int NB, bool SLICE>
+__device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* __restrict__ FV,
+                                                typename PullVec<GW>::T* __restrict__ NV,
+                                                typename PullVec<GW>::T* __restrict__ SV,
+                                                const typename PullVec<GW>::T* __restrict__ actV, int G, int g, int v,
+                                                const int32_t* __restrict__ col, int e0, int e1, bool fold,
+                                                unsigned long long& fe, unsigned long long& ue, int& any) {
+    using VT = typename PullVec<GW>::T;
+    const VT zero = vzero(VT{});
+    const size_t off = (size_t)v * G + g;
+    const VT s0 = vld(SV + off);
+    const VT seen = fold ? vor(s0, vld(FV + off)) : s0;
+    const VT todo = vandnot(vld(actV + g), seen);
+    VT acc = zero;
+    if (vnz(todo)) {
+        const VT* fg = FV + g;
+        for (int e = e0; e < e1; e += NB) {
+            int u[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) u[q] = (e + q < e1) ? (SLICE ? col[e + q] : __ldg(col + e + q)) : -1;
+            VT f[NB];
+#pragma unroll
+            for (int q = 0; q < NB; ++q) f[q] = u[q] >= 0 ? vld(fg + (size_t)u[q] * G) : zero;
+#pragma unroll
+            for (int q = 0; q < NB; ++q) acc = vor(acc, f[q]);
+            if (vcovers(acc, todo)) break;
+        }
+        acc = vand(acc, todo);
+        const unsigned long long dv = (unsigned long long)(e1 - e0);
+        if (vnz(acc)) fe += dv;
+        if (vnz(vandnot(todo, acc))) ue += dv;
+    }
+    NV[off] = acc;
+    const VT s1 = vor(seen, acc);
+    if (vnz(vandnot(s1, s0))) SV[off] = s1;
+    any |= vnz(acc) ? 1 : 0;
+}
+
 // Pull step of level d (see file comment), with items of GW words. At level
 // 2 the frontier F (level 1) is not yet in S: it is ORed in here. Also
 // measures, for the choice of the next level's direction, the edges of the
 // new frontier (sum of deg(v) over nonzero (v, group) items: what a push
 // would touch) and of the items still unvisited (what the next pull would
 // touch at most).
-template <int GW>
+template <int GW, int NB, bool STAGED>
 __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
-                           int slot, int d) {
+                           int slot, int d, const StageView& sv) {
     using VT = typename PullVec<GW>::T;
     unsigned long long fe = 0ull, ue = 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) a.ctr->qvalid[d % 4] = 0;  // a pull builds no queue
@@ -346,39 +551,24 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     }
 
     // light vertices: one thread per (v, g), eight neighbour loads in flight
-    const long long total = (long long)a.n_light * G;
-    for (long long t = gtid; t < total; t += nthr) {
-        const int li = (int)(t / G);
-        const int g = (int)(t - (long long)li * G);
-        const int v = __ldg(a.light + li);
-        const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
-        const size_t off = (size_t)v * G + g;
-        const VT s0 = vld(SV + off);
-        const VT seen = fold ? vor(s0, vld(FV + off)) : s0;
-        const VT todo = vandnot(vld(actV + g), seen);
-        VT acc = zero;
-        if (vnz(todo)) {
-            const VT* fg = FV + g;
-            for (int e = e0; e < e1; e += 8) {
-                int u[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) u[q] = (e + q < e1) ? __ldg(a.col + e + q) : -1;
-                VT f[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) f[q] = u[q] >= 0 ? vld(fg + (size_t)u[q] * G) : zero;
-#pragma unroll
-                for (int q = 0; q < 8; ++q) acc = vor(acc, f[q]);
-                if (vcovers(acc, todo)) break;
-            }
-            acc = vand(acc, todo);
-            const unsigned long long dv = (unsigned long long)(e1 - e0);
-            if (vnz(acc)) fe += dv;
-            if (vnz(vandnot(todo, acc))) ue += dv;
+    if (!STAGED) {  // rows from the global CSR, items over the whole grid
+        const long long total = (long long)a.n_light * G;
+        for (long long t = gtid; t < total; t += nthr) {
+            const int li = (int)(t / G);
+            const int g = (int)(t - (long long)li * G);
+            const int v = __ldg(a.light + li);
+            pull_light_item<GW, NB, false>(FV, NV, SV, actV, G, g, v, a.col, __ldg(a.row_ptr + v),
+                                       __ldg(a.row_ptr + v + 1), fold, fe, ue, any);
         }
-        NV[off] = acc;
-        const VT s1 = vor(seen, acc);
-        if (vnz(vandnot(s1, s0))) SV[off] = s1;
-        any |= vnz(acc) ? 1 : 0;
+    } else {  // this CTA's slice of positions, rows from shared memory (mode 1) or global (mode 2)
+        const long long total = (long long)sv.P * G;
+        for (long long t = threadIdx.x; t < total; t += blockDim.x) {
+            const int pi = (int)(t / G);
+            const int g = (int)(t - (long long)pi * G);
+            const int2 m0 = sv.meta[pi], m1 = sv.meta[pi + 1];
+            pull_light_item<GW, NB, true>(FV, NV, SV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase, fold,
+                                      fe, ue, any);
+        }
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
     if (a.direction == 0) {  // the statistics only feed the automatic choice
@@ -562,24 +752,83 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
     }
 }
 
-template <int GW>
-__global__ void __launch_bounds__(256, 3) msbfs_kernel(MsbfsArgs a) {
+// Thread 0: start the bulk copies of this CTA's staged slice (see
+// MsbfsArgs) into dyn, completing on bar. st: [0] positions P, [1] index of
+// position p0 among the copied pairs, [2] ocol index of the first copied
+// id, [3] 1 if the copies were issued, [4] bytes of the pairs.
+__device__ void stage_issue(const MsbfsArgs& a, unsigned long long* bar, int* st, unsigned char* dyn) {
+    const int p0 = __ldg(a.slice + blockIdx.x), p1 = __ldg(a.slice + blockIdx.x + 1);
+    const int m_lo = p0 & ~1, m_hi = (p1 + 2) & ~1;
+    const int c0 = __ldg(&a.meta[p0].y), c1 = __ldg(&a.meta[p1].y);
+    const int c_lo = c0 & ~3, c_hi = (c1 + 3) & ~3;
+    const long long mb = (long long)(m_hi - m_lo) * 8, cb = (long long)(c_hi - c_lo) * 4;
+    st[0] = p1 - p0;
+    st[1] = p0 - m_lo;
+    st[2] = c_lo;
+    st[3] = 0;
+    st[4] = (int)mb;
+    mbar_init(bar, 1);
+    if (a.staged == 2) return;  // test mode: no copies, the slice is read from global memory
+    if (p1 >= p0 && cb >= 0 && mb + cb <= a.stage_bytes) {
+        mbar_expect_tx(bar, (unsigned)(mb + cb));
+        bulk_copy_g2s(dyn, a.meta + m_lo, (unsigned)mb, bar);
+        if (cb > 0) bulk_copy_g2s(dyn + mb, a.ocol + c_lo, (unsigned)cb, bar);
+        st[3] = 1;
+    } else {
+        atomicExch(&a.ctr->status, kStatusInternal);  // the host's slice check disagrees with the data
+    }
+}
+
+// All levels of one launch. copies_done: the staged slice's copies (if any
+// were issued) have landed, so the CTA may exit.
+template <int GW, int NB, bool STAGED>
+__device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long long* bar, const int* st,
+                                             unsigned char* dyn, bool& copies_done) {
+    // phase times of block 0's thread 0, kept in shared memory (not in
+    // registers every thread would carry through every phase)
+    __shared__ unsigned long long s_time[6];  // last stamp, init, pull, extract, push, push levels
+    enum { kLast, kInit, kPull, kExtract, kPush, kPushes };
     const bool timer = blockIdx.x == 0 && threadIdx.x == 0;
-    unsigned long long t_prev = timer ? globaltimer_ns() : 0ull;
-    unsigned long long t_init = 0, t_pull = 0, t_extract = 0, t_push = 0;
-    long long pushes = 0;
-    auto lap = [&](unsigned long long& acc) {
+    if (timer) {
+        s_time[kLast] = globaltimer_ns();
+        for (int i = 1; i < 6; ++i) s_time[i] = 0ull;
+    }
+    auto lap = [&](int slot) {
         if (timer) {
             const unsigned long long t = globaltimer_ns();
-            acc += t - t_prev;
-            t_prev = t;
+            s_time[slot] += t - s_time[kLast];
+            s_time[kLast] = t;
         }
     };
-    phase_init(a);
-    if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
-    phase_seed(a);
-    if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
-    lap(t_init);
+    if (a.identity) {
+        phase_init_identity(a);
+        if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+    } else {
+        phase_init(a);
+        if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+        phase_seed(a);
+        if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+    }
+    StageView sv{nullptr, nullptr, 0, 0, 0};
+    if (STAGED) {
+        const bool issued = st[3] != 0;
+        const bool ok = __syncthreads_and(issued && mbar_wait_bounded(bar, 0, kWaitLimitNs));
+        copies_done = ok || !issued;
+        if (ok) {
+            sv.meta = reinterpret_cast<const int2*>(dyn) + st[1];
+            sv.col = reinterpret_cast<const int32_t*>(dyn + st[4]);
+            sv.cbase = st[2];
+            sv.mode = 1;
+        } else {
+            if (threadIdx.x == 0 && issued) atomicExch(&a.ctr->status, kStatusTimeout);
+            sv.meta = a.meta + __ldg(a.slice + blockIdx.x);
+            sv.col = a.ocol;
+            sv.cbase = 0;
+            sv.mode = 2;
+        }
+        sv.P = st[0];
+    }
+    lap(kInit);
 
     uint32_t* Fc = a.N;  // level-1 frontier was pushed into N
     uint32_t* Nc = a.F;
@@ -614,12 +863,12 @@ __global__ void __launch_bounds__(256, 3) msbfs_kernel(MsbfsArgs a) {
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             phase_push(a, Fc, Nc, d);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
-            lap(t_push);
-            ++pushes;
+            lap(kPush);
+            if (timer) ++s_time[kPushes];
         } else {
-            phase_pull<GW>(a, Fc, Nc, d % 3, d);
+            phase_pull<GW, NB, STAGED>(a, Fc, Nc, d % 3, d, sv);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
-            lap(t_pull);
+            lap(kPull);
             last_pull = d;
         }
         if (ld_volatile_u32(&a.ctr->lvl_any[d % 3]) == 0u) break;
@@ -627,7 +876,7 @@ __global__ void __launch_bounds__(256, 3) msbfs_kernel(MsbfsArgs a) {
         if (need_now > 0) {
             phase_extract(a, Nc, d);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
-            lap(t_extract);
+            lap(kExtract);
             if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) break;
         }
         uint32_t* t = Fc;
@@ -638,12 +887,30 @@ __global__ void __launch_bounds__(256, 3) msbfs_kernel(MsbfsArgs a) {
         a.ctr->levels = last;
         a.ctr->level_sum += last;
         if (last > a.ctr->levels_max) a.ctr->levels_max = last;
-        a.ctr->t_init_ns += t_init;
-        a.ctr->t_pull_ns += t_pull;
-        a.ctr->t_extract_ns += t_extract;
-        a.ctr->t_push_ns += t_push;
-        a.ctr->push_levels += pushes;
+        a.ctr->t_init_ns += s_time[kInit];
+        a.ctr->t_pull_ns += s_time[kPull];
+        a.ctr->t_extract_ns += s_time[kExtract];
+        a.ctr->t_push_ns += s_time[kPush];
+        a.ctr->push_levels += (long long)s_time[kPushes];
     }
+}
+
+// OCC: resident CTAs per SM the kernel is built for (3: up to 80 registers a
+// thread; 4: 64 registers, more warps to hide latency). STAGED: the light
+// rows come from the CTA's slice staged in shared memory (a separate build,
+// so the other one carries none of its code or registers).
+template <int GW, int OCC, bool STAGED>
+__global__ void __launch_bounds__(256, OCC) msbfs_kernel(MsbfsArgs a) {
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ int s_stage[5];
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    if (STAGED && threadIdx.x == 0) stage_issue(a, &s_bar, s_stage, s_dyn);
+    bool copies_done = !STAGED;
+    // eight neighbour loads in flight per light item (fewer measured slower even where the
+    // 64-register build spills)
+    msbfs_levels<GW, 8, STAGED>(a, &s_bar, s_stage, s_dyn, copies_done);
+    // a CTA that left early must not exit while a bulk copy still writes its shared memory
+    if (STAGED && !copies_done && s_stage[3]) mbar_wait_bounded(&s_bar, 0, kWaitLimitNs);
 }
 
 // Self-test of the bounded wait: every CTA but `absent` enters the grid
@@ -655,6 +922,18 @@ __global__ void barrier_selftest_kernel(GridBarrier* bar, int32_t* status, unsig
     grid_barrier(bar, status, limit_ns);
 }
 
+// ocol[meta[p].y ...] = the CSR row of vertex meta[p].x, one warp per position.
+__global__ void gather_rows_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                                   const int2* __restrict__ meta, int32_t n_pos, int32_t* __restrict__ ocol) {
+    const int lane = threadIdx.x & 31;
+    for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_pos;
+         p += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const int2 m = meta[p];
+        const int e0 = row_ptr[m.x], e1 = row_ptr[m.x + 1];
+        for (int e = e0 + lane; e < e1; e += 32) ocol[m.y + (e - e0)] = col[e];
+    }
+}
+
 __global__ void identity_kernel(int32_t* dst, int32_t n) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -663,11 +942,46 @@ __global__ void identity_kernel(int32_t* dst, int32_t n) {
 
 }  // namespace
 
-int msbfs_max_blocks_per_sm(int block_threads, int pull_width) {
+namespace {
+
+template <bool STAGED>
+const void* msbfs_kernel_for_t(int pull_width, int ctas_per_sm) {
+    if (pull_width == 2)
+        return ctas_per_sm == 4 ? (const void*)msbfs_kernel<2, 4, STAGED> : (const void*)msbfs_kernel<2, 3, STAGED>;
+    return ctas_per_sm == 4 ? (const void*)msbfs_kernel<4, 4, STAGED> : (const void*)msbfs_kernel<4, 3, STAGED>;
+}
+
+const void* msbfs_kernel_for(int pull_width, int ctas_per_sm, bool staged) {
+    return staged ? msbfs_kernel_for_t<true>(pull_width, ctas_per_sm) : msbfs_kernel_for_t<false>(pull_width, ctas_per_sm);
+}
+
+}  // namespace
+
+int msbfs_max_blocks_per_sm(int block_threads, int pull_width, int ctas_per_sm, size_t dyn_smem, bool staged) {
     int nb = 0;
-    const void* k = pull_width == 2 ? (const void*)msbfs_kernel<2> : (const void*)msbfs_kernel<4>;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block_threads, 0) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, msbfs_kernel_for(pull_width, ctas_per_sm, staged),
+                                                      block_threads, dyn_smem) != cudaSuccess)
+        return 0;
     return nb;
+}
+
+cudaError_t msbfs_allow_smem(int bytes) {
+    for (int w : {2, 4})
+        for (int c : {3, 4}) {
+            cudaError_t e = cudaFuncSetAttribute(msbfs_kernel_for(w, c, true),
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+            if (e != cudaSuccess) return e;
+        }
+    return cudaSuccess;
+}
+
+cudaError_t launch_gather_rows(const int32_t* row_ptr, const int32_t* col, const int2* meta, int32_t n_pos,
+                               int32_t* ocol, cudaStream_t s) {
+    if (n_pos <= 0) return cudaSuccess;
+    long long g = ((long long)n_pos * 32 + 255) / 256;
+    if (g > 152 * 16) g = 152 * 16;
+    gather_rows_kernel<<<(unsigned)g, 256, 0, s>>>(row_ptr, col, meta, n_pos, ocol);
+    return cudaGetLastError();
 }
 
 // CTAs for one launch: one thread per (vertex, group) item and one warp
@@ -686,8 +1000,8 @@ int msbfs_grid_for(const MsbfsArgs& a, int max_grid) {
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s) {
     MsbfsArgs copy = a;
     void* params[] = {&copy};
-    const void* k = a.pull_width == 2 ? (const void*)msbfs_kernel<2> : (const void*)msbfs_kernel<4>;
-    return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(block), params, 0, s);
+    return cudaLaunchCooperativeKernel(msbfs_kernel_for(a.pull_width, a.ctas_per_sm, a.staged != 0), dim3(grid),
+                                       dim3(block), params, a.staged ? (size_t)a.stage_bytes : 0, s);
 }
 
 cudaError_t launch_barrier_selftest(GridBarrier* bar, int32_t* status, unsigned long long limit_ns, int grid,

@@ -118,6 +118,8 @@ extern "C" int gumap_knn_run_noalloc(const int32_t* row_ptr, const int32_t* col_
         a.col = col_idx;
         a.n = n;
         a.src = order + (size_t)b * S;
+        a.identity = 1;  // order holds 0 .. n-1
+        a.src_lo = b * S;
         a.nb = std::min<int32_t>(S, n - b * S);
         a.W = W;
         a.F = bits;
@@ -136,7 +138,7 @@ extern "C" int gumap_knn_run_noalloc(const int32_t* row_ptr, const int32_t* col_
         a.partial = mode == GUMAP_PARTIAL ? 1 : 0;
         a.ctr = ctr;
         a.direction = 1;  // pull only: the push levels' queues would need more scratch
-        if (cudaMemsetAsync(&ctr->bar, 0, sizeof(GridBarrier), st) != cudaSuccess) return GUMAP_ERR_CUDA;
+        if (cudaMemsetAsync(ctr, 0, kLaunchCounterBytes, st) != cudaSuccess) return GUMAP_ERR_CUDA;
         if (launch_msbfs(a, setup.coop_grid, 256, st) != cudaSuccess) return GUMAP_ERR_CUDA;
     }
     if (status_out &&

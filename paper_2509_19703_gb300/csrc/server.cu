@@ -384,6 +384,8 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
             a.col = d_col;
             a.n = (int32_t)N;
             a.src = order + (size_t)b * S;
+            a.identity = 1;  // order holds 0 .. N-1
+            a.src_lo = b * S;
             a.nb = (int32_t)std::min<long long>(S, N - (long long)b * S);
             a.W = W;
             a.F = bits;
@@ -405,7 +407,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
             a.push_div = 8;
             a.queue = reinterpret_cast<int32_t*>(dptr(o_queue));
             a.inq = a.queue + 4 * (size_t)N;
-            ck(cudaMemsetAsync(&ctr->bar, 0, sizeof(GridBarrier), st));
+            ck(cudaMemsetAsync(ctr, 0, kLaunchCounterBytes, st));
             ck(launch_msbfs(a, msbfs_grid_for(a, s->coop_grid), 256, st));
         }
         L->engine = GUMAP_ENGINE_MSBFS;

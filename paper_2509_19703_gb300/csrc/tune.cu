@@ -3,8 +3,9 @@
 // Settings are timed on the handle's own graph through the public calls
 // (gumap_knn_set_option, gumap_knn_run): for the full form the MS-BFS state
 // budget (it sets the source-block width), the pull item width, the degree
-// multiplier above which a vertex's items are warp-wide and the level
-// direction; for the partial form the engine. Each candidate runs once to
+// multiplier above which a vertex's items are warp-wide, then on the best of
+// those the CTAs per SM (the CTA shape), the staging of rows in shared
+// memory and the level direction; for the partial form the engine. Each candidate runs once to
 // warm up, then three times with the L2 flushed before each run; the median
 // device time decides. The winner is kept in a JSON-lines cache under a key
 // of the graph's shape class, so graphs of the same class start tuned.
@@ -27,6 +28,8 @@ struct Setting {
     int heavy_mult = 4;
     int direction = 1;
     long long state_bytes = 0;
+    int ctas_per_sm = 3;
+    int stage = 1;
 };
 
 std::string shape_key(const gumap_knn_info& in) {
@@ -50,8 +53,9 @@ bool read_cache(const char* path, const std::string& key, Setting* s) {
         double ms = 0;
         if (sscanf(line.c_str(),
                    "{\"key\": \"%199[^\"]\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, "
-                   "\"direction\": %d, \"state_bytes\": %lld, \"ms\": %lf}",
-                   k, &t.engine, &t.pull_width, &t.heavy_mult, &t.direction, &t.state_bytes, &ms) == 7 &&
+                   "\"direction\": %d, \"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"ms\": %lf}",
+                   k, &t.engine, &t.pull_width, &t.heavy_mult, &t.direction, &t.state_bytes, &t.ctas_per_sm,
+                   &t.stage, &ms) == 9 &&
             key == k) {
             *s = t;  // the last entry of a key wins
             found = true;
@@ -65,8 +69,9 @@ void append_cache(const char* path, const std::string& key, const Setting& s, do
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, \"direction\": %d, "
-            "\"state_bytes\": %lld, \"ms\": %.6f}\n",
-            key.c_str(), s.engine, s.pull_width, s.heavy_mult, s.direction, s.state_bytes, ms);
+            "\"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"ms\": %.6f}\n",
+            key.c_str(), s.engine, s.pull_width, s.heavy_mult, s.direction, s.state_bytes, s.ctas_per_sm, s.stage,
+            ms);
     fclose(f);
 }
 
@@ -78,6 +83,8 @@ int apply(gumap_knn* h, const gumap_knn_info& in, const Setting& s) {
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_STATE_BYTES, s.state_bytes))) return rc;
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_PULL_WIDTH, s.pull_width))) return rc;
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_DIRECTION, s.direction))) return rc;
+        if ((rc = gumap_knn_set_option(h, GUMAP_OPT_CTAS_PER_SM, s.ctas_per_sm))) return rc;
+        if ((rc = gumap_knn_set_option(h, GUMAP_OPT_STAGE, s.stage))) return rc;
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_HEAVY_DEGREE, std::max<long long>(64, s.heavy_mult * mean))))
             return rc;
     }
@@ -116,6 +123,8 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
         res.heavy_mult = best.heavy_mult;
         res.direction = best.direction;
         res.state_bytes = best.state_bytes;
+        res.ctas_per_sm = best.ctas_per_sm;
+        res.stage = best.stage;
         if (out) *out = res;
         return GUMAP_OK;
     }
@@ -207,18 +216,22 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
             best = s;
         }
     }
-    if (in.mode == GUMAP_FULL) {  // then the automatic direction on the best settings
-        Setting s = best;
-        s.direction = 0;
-        double ms = 0.0;
-        if ((rc = apply(h, in, s)) || (rc = time_run(&ms))) {
-            cleanup();
-            return rc;
-        }
-        res.candidates++;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = s;
+    if (in.mode == GUMAP_FULL) {  // then, one at a time on the best so far: CTA shape, staging, direction
+        for (int step = 0; step < 3; ++step) {
+            Setting s = best;
+            if (step == 0) s.ctas_per_sm = best.ctas_per_sm == 4 ? 3 : 4;
+            else if (step == 1) s.stage = best.stage ? 0 : 1;
+            else s.direction = 0;
+            double ms = 0.0;
+            if ((rc = apply(h, in, s)) || (rc = time_run(&ms))) {
+                cleanup();
+                return rc;
+            }
+            res.candidates++;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = s;
+            }
         }
     }
     cleanup();
@@ -231,6 +244,8 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
     res.heavy_mult = best.heavy_mult;
     res.direction = best.direction;
     res.state_bytes = best.state_bytes;
+    res.ctas_per_sm = best.ctas_per_sm;
+    res.stage = best.stage;
     if (out) *out = res;
     return GUMAP_OK;
 }

@@ -23,7 +23,7 @@ FULL, PARTIAL = 0, 1
 WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE = 0x0, 0x1, 0x2
 ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER, ENGINE_BATCH = 0, 1, 2, 3, 4
 OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
-OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH = 6, 7, 8
+OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH, OPT_CTAS_PER_SM, OPT_STAGE = 6, 7, 8, 9, 10
 DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
 MAX_K = 256
 DIST_INF = 0xFFFF
@@ -48,7 +48,8 @@ class _Stats(ctypes.Structure):
                 ("bfs_level_sum", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("bfs_init_ms", ctypes.c_double),
                 ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double),
-                ("bfs_push_ms", ctypes.c_double), ("bfs_push_levels", ctypes.c_int64)]
+                ("bfs_push_ms", ctypes.c_double), ("bfs_push_levels", ctypes.c_int64),
+                ("bfs_staged_launches", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
@@ -59,7 +60,8 @@ class _Info(ctypes.Structure):
 class _Tune(ctypes.Structure):
     _fields_ = [("from_cache", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double),
                 ("default_ms", ctypes.c_double), ("engine", ctypes.c_int32), ("pull_width", ctypes.c_int32),
-                ("heavy_mult", ctypes.c_int32), ("direction", ctypes.c_int32), ("state_bytes", ctypes.c_int64)]
+                ("heavy_mult", ctypes.c_int32), ("direction", ctypes.c_int32), ("state_bytes", ctypes.c_int64),
+                ("ctas_per_sm", ctypes.c_int32), ("stage", ctypes.c_int32)]
 
 
 class _ServerOpts(ctypes.Structure):

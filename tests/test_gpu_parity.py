@@ -65,22 +65,31 @@ def test_zoo_forced_direction(g, k, direction):
                       f"{g.name} {mode} k={k} direction={direction}")
 
 
+@pytest.mark.parametrize("width,ctas,stage", [(2, 3, 1), (4, 4, 1), (2, 4, 0), (4, 3, 0), (4, 3, 2)])
 @pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
-def test_zoo_64bit_pull_items(g, k):
-    """Pull items of 64 bits instead of 128: same rows."""
+def test_zoo_kernel_builds(g, k, width, ctas, stage):
+    """Every build of the kernel gives the same rows: pull items of 64 or 128
+    bits, 3 or 4 CTAs per SM, rows staged in shared memory (1), read from the
+    CSR (0), or the staged kernel's fallback reading its slice from global
+    memory (2)."""
     ref = oracle_ref(g, k, "full")
     with gumap.KnnGraph.from_graph(g, k) as kg:
-        kg.set_option(gumap.OPT_PULL_WIDTH, 2)
+        kg.set_option(gumap.OPT_PULL_WIDTH, width)
+        kg.set_option(gumap.OPT_CTAS_PER_SM, ctas)
+        kg.set_option(gumap.OPT_STAGE, stage)
         kg.set_option(gumap.OPT_BLOCK_BITS, 384)
         out = kg.run()
         r, c, w = kg.coo()
         kg.check()
+        staged = kg.stats()["bfs_staged_launches"]
         res = dict(idx=out["idx"].cpu().numpy(), dist=gumap.dist_u16(out["dist"]),
                    w=out["w"].cpu().numpy().astype(np.float64), coo=(r.cpu().numpy(), c.cpu().numpy(),
                                                                       w.cpu().numpy().astype(np.float64)))
         rho, sigma = kg.rho_sigma()
         res.update(rho=rho.cpu().numpy().astype(np.float64), sigma=sigma.cpu().numpy().astype(np.float64))
-    assert_parity(res, ref, f"{g.name} width 2 k={k}")
+    assert_parity(res, ref, f"{g.name} width {width} ctas {ctas} stage {stage} k={k}")
+    if stage == 0:
+        assert staged == 0
 
 
 def test_direction_switches_on_a_long_grid():
@@ -200,7 +209,27 @@ def test_union_with_explicit_sources_is_rejected():
         assert e.value.status == gumap.ERR_INVALID_ARG
 
 
-@pytest.mark.parametrize("bad", ["asym", "unsorted", "self", "dup", "range"])
+def test_rows_are_staged_on_a_scale_free_graph():
+    """The default run stages the light rows in shared memory (and the
+    statistics say so); the rows match the oracle."""
+    g = gg.barabasi_albert(4000, 4, 151)
+    ref = oracle_ref(g, 15, "full")
+    res = run_gpu(g, 15, "full")
+    assert_parity(res, ref, "BA-4000 staged")
+    assert res["stats"]["bfs_staged_launches"] > 0
+
+
+def test_bad_option_values_are_rejected():
+    g = gg.grid(5, 5)
+    with gumap.KnnGraph.from_graph(g, 3) as kg:
+        for opt, val in ((gumap.OPT_CTAS_PER_SM, 5), (gumap.OPT_PULL_WIDTH, 3), (gumap.OPT_DIRECTION, 7),
+                         (gumap.OPT_STAGE, 3)):
+            with pytest.raises(gumap.GumapError) as e:
+                kg.set_option(opt, val)
+            assert e.value.status == gumap.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("bad", ["asym", "unsorted", "self", "dup", "range", "rowptr"])
 @pytest.mark.parametrize("where", ["host", "device"])
 def test_invalid_csr_rejected(bad, where):
     g = gg.grid(4, 4)
@@ -216,6 +245,8 @@ def test_invalid_csr_rejected(bad, where):
         col[1] = col[0]
     elif bad == "range":
         col[-1] = 99
+    elif bad == "rowptr":
+        rp[2] = rp[1] - 1  # a decreasing row pointer
     if where == "host":
         args = (rp, col)
         flags = 0
