@@ -830,7 +830,7 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
         const int B = key_bits_for(h->n);
         if ((rc = ensure(h->keys, cnt * 8, "coo keys")) || (rc = ensure(h->vals, cnt * 4, "coo vals")) ||
             (rc = ensure(h->keys_tmp, cnt * 8, "coo keys tmp")) || (rc = ensure(h->vals_tmp, cnt * 4, "coo vals tmp")) ||
-            (rc = ensure(h->sort_temp, radix_sort_temp_bytes(cnt), "sort temp")))
+            (rc = ensure(h->sort_temp, radix_sort_temp_bytes(cnt, 2 * B), "sort temp")))
             return rc;
         CK(cudaMemsetAsync(&h->d_ctr->coo_nnz, 0, sizeof(unsigned long long), st), "memset nnz");
         CK(launch_union(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, B,
@@ -840,7 +840,8 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
         int launches = 0;
         CK(radix_sort_pairs(static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
                             static_cast<unsigned long long*>(h->keys_tmp.p), static_cast<float*>(h->vals_tmp.p), cnt,
-                            2 * B, h->sort_temp.p, h->sort_temp.bytes, st, &h->coo_keys, &h->coo_vals, &launches),
+                            2 * B, h->sort_temp.p, h->sort_temp.bytes, &h->d_ctr->status, st, &h->coo_keys,
+                            &h->coo_vals, &launches),
            "radix sort");
         h->kernel_launches += launches;
         h->coo_key_bits = B;

@@ -210,11 +210,13 @@ cudaError_t launch_coo_unpack(const unsigned long long* keys, const float* vals,
                               const DeviceCounters* ctr, long long cap, int32_t* row, int32_t* col, float* w,
                               int64_t* nnz_out, cudaStream_t s);
 
-// ---- sort.cu: LSD radix sort of (u64 key, float value) on the low `bits` key bits.
-size_t radix_sort_temp_bytes(long long count);
+// ---- sort.cu: LSD radix sort of (u64 key, float value) on the low `bits` key bits
+// (bits <= 64). A look-back wait that gives up writes kStatusTimeout to *status.
+size_t radix_sort_temp_bytes(long long count, int bits);
 cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned long long* keys_tmp,
                              float* vals_tmp, long long count, int bits, void* temp, size_t temp_bytes,
-                             cudaStream_t s, unsigned long long** keys_out, float** vals_out, int* launches);
+                             int32_t* status, cudaStream_t s, unsigned long long** keys_out, float** vals_out,
+                             int* launches);
 
 // ---- validate.cu
 // Device-side CSR validation; writes 0 to *bad if the graph is valid.

@@ -2,12 +2,17 @@
 // bits, 8 bits per pass. Used to order the fuzzy-union COO by (row, col):
 // the key of entry (i, j) is (i << B) | j with B = ceil(log2 n).
 //
-// Each pass: (1) a tile histogram of the digit (256 bins per 4096-key tile,
-// stored digit-major), (2) one CTA per digit scans that digit's tile counts
-// and records the digit total, (3) a stable scatter: each tile adds the
-// prefix of the digit totals to its tile offsets, then ranks its keys in
-// input order with warp match/ballot ranks plus per-warp digit counts in
-// shared memory.
+// One-sweep organisation (the decoupled look-back of Merrill and Garland's
+// single-pass scan, applied per digit as in Adinets and Merrill's Onesweep
+// radix sort): one kernel counts the digits of every pass in a single read
+// of the keys; then one kernel per pass, in which each CTA takes the next
+// tile id from a counter, ranks its 2048 keys by digit (stable: warp w owns
+// the w-th 256-key segment of the tile, ranked with warp match), publishes
+// its per-digit counts, adds the counts of the tiles before it by looking
+// back over their published words, and scatters. A tile only waits on tiles
+// with smaller ids, which were handed out earlier to CTAs already running,
+// so the waits end; each is bounded in time all the same and reports
+// GUMAP_ERR_TIMEOUT in the caller's status word when it gives up.
 #include "gumap_internal.cuh"
 
 namespace gumap {
@@ -15,178 +20,196 @@ namespace gumap {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
-constexpr int kTile = kThreads * kItems;
 constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 8;                      // keys per lane
+constexpr int kTile = kThreads * kItems;       // 2048 keys per tile
+constexpr int kSeg = 32 * kItems;              // keys of one warp's segment
+constexpr int kMaxPasses = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
+// published word of (tile, digit): flag in the top two bits, count below
+constexpr unsigned long long kFlagAggregate = 1ull << 62;  // this tile's count only
+constexpr unsigned long long kFlagInclusive = 2ull << 62;  // count of this tile and all before it
+constexpr unsigned long long kCountMask = (1ull << 62) - 1ull;
+constexpr unsigned long long kLookbackLimitNs = 1000ull * 1000ull * 1000ull;
 
-__global__ void __launch_bounds__(kThreads) hist_kernel(const unsigned long long* __restrict__ keys,
-                                                        long long count, int shift, int num_tiles,
-                                                        unsigned int* __restrict__ hist) {
-    __shared__ unsigned int h[256];
-    const int tid = threadIdx.x;
-    h[tid] = 0u;
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * kTile;
-    unsigned int dg[kItems];
-#pragma unroll
-    for (int c = 0; c < kItems; ++c) {  // all loads in flight before the counting
-        const long long i = base + c * kThreads + tid;
-        dg[c] = i < count ? (unsigned)(__ldcs(keys + i) >> shift) & 0xFFu : 256u;
-    }
-#pragma unroll
-    for (int c = 0; c < kItems; ++c)
-        if (dg[c] < 256u) atomicAdd(&h[dg[c]], 1u);
-    __syncthreads();
-    hist[(size_t)tid * num_tiles + blockIdx.x] = h[tid];
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// One CTA per digit: exclusive scan, in place, of that digit's per-tile
-// counts (the tile offsets within the digit's output range), and the digit's
-// total into totals[digit]. 4096 entries per round: each thread scans 4
-// consecutive entries, warps scan with shuffles, warp totals are scanned by
-// warp 0, a running carry links the rounds. Every load is coalesced.
-__global__ void __launch_bounds__(1024) scan_kernel(unsigned int* __restrict__ hist, long long len,
-                                                    unsigned int* __restrict__ totals) {
-    __shared__ unsigned int wsum[32];
-    __shared__ unsigned int carry_s;
-    unsigned int* data = hist + (size_t)blockIdx.x * len;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) carry_s = 0u;
+// Counts of every digit of every pass, one read of the keys: hist[p][d].
+__global__ void __launch_bounds__(kThreads) hist_all_kernel(const unsigned long long* __restrict__ keys,
+                                                            long long count, int passes,
+                                                            unsigned int* __restrict__ hist) {
+    __shared__ unsigned int h[kMaxPasses][256];
+    for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0u;
     __syncthreads();
-    for (long long base = 0; base < len; base += 4096) {
-        const long long i0 = base + 4ll * tid;
-        unsigned int x[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = (i0 + q < len) ? data[i0 + q] : 0u;
-        const unsigned int t = x[0] + x[1] + x[2] + x[3];
-        unsigned int inc = t;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const unsigned int y = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc += y;
-        }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned int w = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const unsigned int y = __shfl_up_sync(kFull, w, o);
-                if (lane >= o) w += y;
-            }
-            wsum[lane] = w;  // inclusive over warps
-        }
-        __syncthreads();
-        const unsigned int carry = carry_s;
-        unsigned int run = carry + (warp > 0 ? wsum[warp - 1] : 0u) + (inc - t);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (i0 + q < len) data[i0 + q] = run;
-            run += x[q];
-        }
-        __syncthreads();
-        if (tid == 0) carry_s = carry + wsum[31];
-        __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = __ldg(keys + i);
+        for (int p = 0; p < passes; ++p) atomicAdd(&h[p][(unsigned)(k >> (8 * p)) & 0xFFu], 1u);
     }
-    if (tid == 0) totals[blockIdx.x] = carry_s;
+    __syncthreads();
+    for (int p = 0; p < passes; ++p)
+        if (h[p][threadIdx.x]) atomicAdd(&hist[p * 256 + threadIdx.x], h[p][threadIdx.x]);
 }
 
-__global__ void __launch_bounds__(kThreads) scatter_kernel(const unsigned long long* __restrict__ kin,
-                                                           const float* __restrict__ vin,
-                                                           unsigned long long* __restrict__ kout,
-                                                           float* __restrict__ vout, long long count, int shift,
-                                                           int num_tiles, const unsigned int* __restrict__ offs,
-                                                           const unsigned int* __restrict__ totals) {
-    __shared__ unsigned int run[256];
-    __shared__ unsigned int wcnt[kWarps][256];
-    __shared__ unsigned int wtot[kWarps];
-    const int tid = threadIdx.x;
-    const int warp = tid >> 5;
-    const int lane = tid & 31;
+// One pass (digit at bit `shift`). hist: this pass's digit counts; tile_ctr:
+// this pass's tile counter; pub: this pass's published words [tiles][256];
+// all zeroed before the first pass.
+__global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long long* __restrict__ kin,
+                                                            const float* __restrict__ vin,
+                                                            unsigned long long* __restrict__ kout,
+                                                            float* __restrict__ vout, long long count, int shift,
+                                                            const unsigned int* __restrict__ hist,
+                                                            unsigned int* tile_ctr, unsigned long long* pub,
+                                                            int32_t* status) {
+    __shared__ unsigned int s_tile;
+    __shared__ unsigned int wcnt[kWarps][256];  // per-warp digit counts, then per-warp offsets
+    __shared__ unsigned long long gbase[256];   // where digit d of this tile starts in the output
+    __shared__ unsigned int wsum[kWarps];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
-    // start of digit tid's output range: exclusive prefix of the digit totals
-    const unsigned int tot = totals[tid];
-    unsigned int inc = tot;
+    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0u;
+    __syncthreads();
+    const long long tile = s_tile;
+    const long long seg = tile * kTile + (long long)warp * kSeg;
+
+    // load the warp's segment (coalesced), then rank it: rank[c] is the
+    // key's position among the segment's keys of the same digit
+    unsigned long long key[kItems];
+    float val[kItems];
+    int dig[kItems];
+    unsigned int rank[kItems];
+#pragma unroll
+    for (int c = 0; c < kItems; ++c) {
+        const long long i = seg + c * 32 + lane;
+        key[c] = i < count ? __ldcs(kin + i) : 0ull;
+        val[c] = i < count ? __ldcs(vin + i) : 0.0f;
+        dig[c] = i < count ? (int)((key[c] >> shift) & 0xFFull) : 256;  // invalid keys rank apart
+    }
+#pragma unroll
+    for (int c = 0; c < kItems; ++c) {
+        const int d = dig[c];
+        const unsigned peers = __match_any_sync(kFull, d);
+        const unsigned before = d < 256 ? wcnt[warp][d] : 0u;
+        rank[c] = before + __popc(peers & lt);
+        __syncwarp();
+        if (d < 256 && (peers & lt) == 0u) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    // digit tid: offsets of each warp's run within the tile, and the tile total
+    unsigned int tile_count = 0u;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) {
+        const unsigned int cnt = wcnt[w][tid];
+        wcnt[w][tid] = tile_count;
+        tile_count += cnt;
+    }
+    unsigned long long* my = pub + tile * 256 + tid;
+    if (tile == 0) {
+        *reinterpret_cast<volatile unsigned long long*>(my) = kFlagInclusive | tile_count;
+    } else {
+        *reinterpret_cast<volatile unsigned long long*>(my) = kFlagAggregate | tile_count;
+    }
+
+    // start of digit tid in the output: exclusive scan of the pass's digit counts
+    const unsigned int hc = hist[tid];
+    unsigned int inc = hc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned int y = __shfl_up_sync(kFull, inc, o);
         if (lane >= o) inc += y;
     }
-    if (lane == 31) wtot[warp] = inc;
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0u;
+    if (lane == 31) wsum[warp] = inc;
     __syncthreads();
-    unsigned int before = inc - tot;
-    for (int w = 0; w < warp; ++w) before += wtot[w];
-    run[tid] = before + offs[(size_t)tid * num_tiles + blockIdx.x];
-    __syncthreads();
-    const long long base = (long long)blockIdx.x * kTile;
-    // the tile's keys and values are loaded up front: one memory latency, not 16
-    unsigned long long keys[kItems];
-    float vals[kItems];
-#pragma unroll
-    for (int c = 0; c < kItems; ++c) {
-        const long long i = base + c * kThreads + tid;
-        keys[c] = i < count ? __ldcs(kin + i) : 0ull;
-        vals[c] = i < count ? __ldcs(vin + i) : 0.0f;
+    unsigned long long start = inc - hc;
+    for (int w = 0; w < warp; ++w) start += wsum[w];
+
+    // look back over the tiles before this one
+    unsigned long long prefix = 0ull;
+    if (tile > 0) {
+        long long t = tile - 1;
+        unsigned long long t0 = 0ull;
+        bool timed = false;
+        while (t >= 0) {
+            const unsigned long long v = *reinterpret_cast<volatile unsigned long long*>(pub + t * 256 + tid);
+            if ((v >> 62) == 0ull) {  // not published yet
+                if (!timed) {
+                    t0 = globaltimer_ns();
+                    timed = true;
+                } else if (globaltimer_ns() - t0 > kLookbackLimitNs) {
+                    atomicExch(status, kStatusTimeout);
+                    break;
+                }
+                continue;
+            }
+            timed = false;
+            prefix += v & kCountMask;
+            if ((v >> 62) == 2ull) break;
+            --t;
+        }
+        *reinterpret_cast<volatile unsigned long long*>(my) = kFlagInclusive | (prefix + tile_count);
     }
+    gbase[tid] = start + prefix;
+    __syncthreads();
+
 #pragma unroll
     for (int c = 0; c < kItems; ++c) {
-        const long long i = base + c * kThreads + tid;
-        const bool valid = i < count;
-        const unsigned long long key = keys[c];
-        const float val = vals[c];
-        const int d = valid ? (int)((key >> shift) & 0xFFull) : 256;  // invalid lanes group apart
-        const unsigned peers = __match_any_sync(kFull, d);
-        const unsigned rank = __popc(peers & lt);
-        if (valid && rank == 0u) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            unsigned int pos = run[d] + rank;
-            for (int w = 0; w < warp; ++w) pos += wcnt[w][d];
-            kout[pos] = key;
-            vout[pos] = val;
+        const int d = dig[c];
+        if (d < 256) {
+            const unsigned long long pos = gbase[d] + wcnt[warp][d] + rank[c];
+            kout[pos] = key[c];
+            vout[pos] = val[c];
         }
-        __syncthreads();
-        unsigned int tot = 0u;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            tot += wcnt[w][tid];
-            wcnt[w][tid] = 0u;
-        }
-        run[tid] += tot;
-        __syncthreads();
     }
 }
+
+int passes_for(int bits) { return (bits + 7) / 8; }
+
+long long tiles_for(long long count) { return (count + kTile - 1) / kTile; }
 
 }  // namespace
 
-size_t radix_sort_temp_bytes(long long count) {
-    const long long tiles = (count + kTile - 1) / kTile;
-    return (size_t)(256 * (tiles > 0 ? tiles : 1) + 256) * sizeof(unsigned int);  // + digit totals
+size_t radix_sort_temp_bytes(long long count, int bits) {
+    const int P = passes_for(bits > 0 ? bits : 1);
+    const long long tiles = tiles_for(count > 0 ? count : 1);
+    // published words (8-byte aligned first), digit counts, tile counters
+    return (size_t)P * (size_t)tiles * 256 * sizeof(unsigned long long) + (size_t)P * 256 * sizeof(unsigned int) +
+           (size_t)P * sizeof(unsigned int);
 }
 
 cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned long long* keys_tmp, float* vals_tmp,
-                             long long count, int bits, void* temp, size_t temp_bytes, cudaStream_t s,
-                             unsigned long long** keys_out, float** vals_out, int* launches) {
+                             long long count, int bits, void* temp, size_t temp_bytes, int32_t* status,
+                             cudaStream_t s, unsigned long long** keys_out, float** vals_out, int* launches) {
     *keys_out = keys;
     *vals_out = vals;
     if (count <= 1 || bits <= 0) return cudaSuccess;
-    if (count > 0xFFFFFFFFll) return cudaErrorInvalidValue;  // 32-bit output offsets
-    const long long tiles = (count + kTile - 1) / kTile;
-    if (temp_bytes < radix_sort_temp_bytes(count)) return cudaErrorInvalidValue;
-    unsigned int* hist = static_cast<unsigned int*>(temp);
-    unsigned int* totals = hist + 256 * tiles;
+    if (bits > 8 * kMaxPasses) return cudaErrorInvalidValue;
+    const int P = passes_for(bits);
+    const long long tiles = tiles_for(count);
+    const size_t need = radix_sort_temp_bytes(count, bits);
+    if (temp_bytes < need) return cudaErrorInvalidValue;
+    unsigned long long* pub = static_cast<unsigned long long*>(temp);
+    unsigned int* hist = reinterpret_cast<unsigned int*>(pub + (size_t)P * tiles * 256);
+    unsigned int* tile_ctr = hist + P * 256;
+    cudaError_t e = cudaMemsetAsync(temp, 0, need, s);
+    if (e != cudaSuccess) return e;
+    long long hgrid = (count + kThreads * 16 - 1) / (kThreads * 16);
+    if (hgrid > 152 * 8) hgrid = 152 * 8;
+    hist_all_kernel<<<(unsigned)hgrid, kThreads, 0, s>>>(keys, count, P, hist);
+    if (launches) *launches += 1;
     unsigned long long *ka = keys, *kb = keys_tmp;
     float *va = vals, *vb = vals_tmp;
-    for (int shift = 0; shift < bits; shift += 8) {
-        hist_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, count, shift, (int)tiles, hist);
-        scan_kernel<<<256, 1024, 0, s>>>(hist, tiles, totals);
-        scatter_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, va, kb, vb, count, shift, (int)tiles, hist, totals);
-        if (launches) *launches += 3;
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
+    for (int p = 0; p < P; ++p) {
+        onesweep_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, va, kb, vb, count, 8 * p, hist + p * 256,
+                                                             tile_ctr + p, pub + (size_t)p * tiles * 256, status);
+        if (launches) *launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         unsigned long long* tk = ka;
         ka = kb;
         kb = tk;
