@@ -439,9 +439,11 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
     const int W = S / 32;
     const size_t words = (size_t)h->n * W;
     int rc;
-    // bitsets F, N, S, then 4 frontier queues and the queue-entry levels (n ints each)
-    if ((rc = ensure(h->bits, words * 3 * sizeof(uint32_t) + 5 * (size_t)h->n * sizeof(int32_t), "bitsets")))
-        return rc;
+    // bitsets F, N, S, then 4 frontier queues and the queue-entry levels (n ints each), then the
+    // pull items' saturation states (n x W/2 bytes: enough for either item width), 16-byte aligned
+    const size_t sat_off = (words * 3 * sizeof(uint32_t) + 5 * (size_t)h->n * sizeof(int32_t) + 15) & ~(size_t)15;
+    const size_t sat_bytes = ((size_t)h->n * (size_t)(W / 2) + 15) & ~(size_t)15;
+    if ((rc = ensure(h->bits, sat_off + sat_bytes, "bitsets"))) return rc;
     if ((rc = ensure(h->act, (size_t)W * 4, "act"))) return rc;
     if ((rc = ensure(h->need, (size_t)W * 4, "need"))) return rc;
     if ((rc = ensure(h->cnt, (size_t)S * 4, "cnt"))) return rc;
@@ -478,6 +480,7 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
         a.ctas_per_sm = h->opt_ctas_per_sm;
         a.queue = reinterpret_cast<int32_t*>(base + 3 * words);
         a.inq = a.queue + 4 * (size_t)h->n;
+        a.sat = reinterpret_cast<uint8_t*>(h->bits.p) + sat_off;
         const int grid = msbfs_grid_for(a, h->coop_grid[a.pull_width == 2][a.ctas_per_sm == 4]);
         const int cap = h->stage_cap[a.ctas_per_sm == 4];
         if (h->opt_stage && h->n > h->n_heavy && cap > 0) {

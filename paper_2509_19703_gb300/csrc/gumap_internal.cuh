@@ -91,6 +91,11 @@ struct MsbfsArgs {
     int32_t* queue;          // [4][n] frontier queues, slot d % 4
     int32_t* inq;            // [n] level at which the vertex last entered a queue
     int32_t pull_width;      // words per pull item: 4 (128 bits; also when 0) or 2 (64 bits)
+    // per pull item (v, group), [n][W / pull_width] bytes, 16-byte padded, zeroed by the kernel:
+    // 0 = active; 1 = every active source has reached it (permanent: S only grows, act only
+    // shrinks), its N word was written 0 once; 2 = both N buffers hold 0 for it, so later pulls
+    // skip it. NULL: no skipping.
+    uint8_t* sat;
     int32_t ctas_per_sm;     // kernel build: 3 (also when 0) or 4 resident CTAs per SM
     // Staged pull (staged = 1): the rows of the light vertices in processing
     // order (ocol) with per-position (vertex, offset into ocol) pairs (meta:

@@ -177,6 +177,14 @@ __device__ __forceinline__ uint4 warp_or4(uint4 a) {
 
 // ---------------------------------------------------------------- phases
 
+// Zeroes the pull items' saturation states (see MsbfsArgs::sat).
+__device__ __forceinline__ void clear_sat(const MsbfsArgs& a, long long tid, long long nthr) {
+    if (!a.sat) return;
+    const long long items = (long long)a.n * (a.W / (a.pull_width == 2 ? 2 : 4));
+    uint4* s4 = reinterpret_cast<uint4*>(a.sat);
+    for (long long i = tid; i < (items + 15) / 16; i += nthr) s4[i] = make_uint4(0u, 0u, 0u, 0u);
+}
+
 // Phase 0: clear S and N, prefill the block's output rows with padding,
 // mark valid source bits in act/need.
 __device__ void phase_init(const MsbfsArgs& a) {
@@ -195,6 +203,7 @@ __device__ void phase_init(const MsbfsArgs& a) {
     }
     if (a.inq)
         for (long long i = tid; i < a.n; i += nthr) a.inq[i] = 0;
+    clear_sat(a, tid, nthr);
     for (long long i = tid; i < a.W; i += nthr) {
         long long lo = i * 32;
         uint32_t m;
@@ -269,6 +278,7 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
     const long long src_hi = (long long)a.src_lo + a.nb;
     int any = 0;
     unsigned long long fe = 0ull;
+    clear_sat(a, gtid, nthr);
     for (long long v = gwarp; v < a.n; v += nwarps) {
         const int r0 = __ldg(a.row_ptr + v), r1 = __ldg(a.row_ptr + v + 1);
         int lo = r0, hi = r1;  // first neighbour >= src_lo
@@ -457,10 +467,20 @@ __device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* _
                                                 typename PullVec<GW>::T* __restrict__ SV,
                                                 const typename PullVec<GW>::T* __restrict__ actV, int G, int g, int v,
                                                 const int32_t* __restrict__ col, int e0, int e1, bool fold,
-                                                unsigned long long& fe, unsigned long long& ue, int& any) {
+                                                uint8_t* __restrict__ sat, unsigned long long& fe,
+                                                unsigned long long& ue, int& any) {
     using VT = typename PullVec<GW>::T;
     const VT zero = vzero(VT{});
     const size_t off = (size_t)v * G + g;
+    if (sat) {  // a saturated item: zero the N buffer once more, then skip it for good
+        const uint8_t st = sat[off];
+        if (st == 2) return;
+        if (st == 1) {
+            NV[off] = zero;
+            sat[off] = 2;
+            return;
+        }
+    }
     const VT s0 = vld(SV + off);
     const VT seen = fold ? vor(s0, vld(FV + off)) : s0;
     const VT todo = vandnot(vld(actV + g), seen);
@@ -487,6 +507,7 @@ __device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* _
     const VT s1 = vor(seen, acc);
     if (vnz(vandnot(s1, s0))) SV[off] = s1;
     any |= vnz(acc) ? 1 : 0;
+    if (sat && !vnz(todo)) sat[off] = 1;
 }
 
 // Pull step of level d (see file comment), with items of GW words. At level
@@ -520,6 +541,17 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const int g = (int)(it - (long long)h * G);
         const int v = __ldg(a.heavy + h);
         const size_t off = (size_t)v * G + g;
+        if (a.sat) {  // the whole warp reads the same state: uniform branches
+            const uint8_t st = a.sat[off];
+            if (st == 2) continue;
+            if (st == 1) {
+                if (lane == 0) {
+                    NV[off] = zero;
+                    a.sat[off] = 2;
+                }
+                continue;
+            }
+        }
         const VT s0 = vld(SV + off);
         const VT seen = fold ? vor(s0, vld(FV + off)) : s0;
         const VT todo = vandnot(vld(actV + g), seen);
@@ -547,6 +579,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
             const VT s1 = vor(seen, acc);
             if (vnz(vandnot(s1, s0))) SV[off] = s1;
             any |= vnz(acc) ? 1 : 0;
+            if (a.sat && !vnz(todo)) a.sat[off] = 1;
         }
     }
 
@@ -558,7 +591,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
             const int g = (int)(t - (long long)li * G);
             const int v = __ldg(a.light + li);
             pull_light_item<GW, NB, false>(FV, NV, SV, actV, G, g, v, a.col, __ldg(a.row_ptr + v),
-                                       __ldg(a.row_ptr + v + 1), fold, fe, ue, any);
+                                           __ldg(a.row_ptr + v + 1), fold, a.sat, fe, ue, any);
         }
     } else {  // this CTA's slice of positions, rows from shared memory (mode 1) or global (mode 2)
         const long long total = (long long)sv.P * G;
@@ -567,7 +600,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
             const int g = (int)(t - (long long)pi * G);
             const int2 m0 = sv.meta[pi], m1 = sv.meta[pi + 1];
             pull_light_item<GW, NB, true>(FV, NV, SV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase, fold,
-                                      fe, ue, any);
+                                          a.sat, fe, ue, any);
         }
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
@@ -836,8 +869,16 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
     bool go = ld_volatile_u32(&a.ctr->lvl_any[1]) != 0u;
     if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) go = false;
     int last_pull = 0;  // u_edges[0] holds the "everything unvisited" estimate
+    // The extraction of level d runs in the same phase as the next level's
+    // pull (or push preparation): both only read level d's buffer (now the
+    // frontier Fc), so one grid barrier per level is saved. In the partial
+    // form the extraction also retires finished sources from act while that
+    // pull reads act; a pull that still sees a retired source propagates it
+    // one level more, which changes no list (the source's list is final).
+    int pend = 0;  // level whose extraction is still to run (0: none)
     for (int d = 2; go && d <= a.n; ++d) {
         const int need_now = ld_volatile_i32(&a.ctr->n_need);
+        if (need_now == 0) pend = 0;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             // slots of level d + 1 (last used by level d - 3)
             a.ctr->lvl_any[(d + 1) % 3] = 0u;
@@ -860,6 +901,7 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
         }
         if (push) {
             phase_push_prep(a, Fc, Nc, d);
+            if (pend) phase_extract(a, Fc, pend);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             phase_push(a, Fc, Nc, d);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
@@ -867,21 +909,24 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
             if (timer) ++s_time[kPushes];
         } else {
             phase_pull<GW, NB, STAGED>(a, Fc, Nc, d % 3, d, sv);
+            if (pend) phase_extract(a, Fc, pend);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             lap(kPull);
             last_pull = d;
         }
+        pend = 0;
         if (ld_volatile_u32(&a.ctr->lvl_any[d % 3]) == 0u) break;
         last = d;
-        if (need_now > 0) {
-            phase_extract(a, Nc, d);
-            if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
-            lap(kExtract);
-            if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) break;
-        }
+        if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) break;
+        pend = d;
         uint32_t* t = Fc;
         Fc = Nc;
         Nc = t;
+    }
+    if (pend) {  // the loop ran out of levels with an extraction pending (it breaks before, in practice)
+        phase_extract(a, Fc, pend);
+        if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
+        lap(kExtract);
     }
     if (timer) {
         a.ctr->levels = last;
