@@ -23,10 +23,12 @@
 // longest items start first and the short ones fill the tail before the
 // grid barrier.
 //
-// Level 1 is a push from the sources (their adjacency rows) into N only,
-// and its kNN entries are the first k entries of each source's sorted CSR
-// row; level 2 folds the level-1 frontier into S (one stream instead of an
-// atomic per edge).
+// Level 1 of a block of consecutive sources (every run over all vertices)
+// is a pull from the sorted rows that writes N and S in full; for an
+// explicit source list it is a push from the sources' rows into N only, and
+// level 2 folds the level-1 frontier into S (one stream instead of an atomic
+// per edge). Its kNN entries are the first k entries of each source's sorted
+// CSR row.
 // For later levels the extraction phase scans each word column of N in
 // vertex order, transposes 32x32 bit tiles with warp ballots, and appends
 // to every incomplete source the vertices it reached at this level in
@@ -256,9 +258,9 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
 // vertices src_lo .. src_lo + nb - 1 (every run over all vertices). Level 1
 // is computed as a pull instead of pushed: N[v] = the block's sources
 // adjacent to v, read off v's sorted row (one warp per vertex, 4096 source
-// bits per round, each neighbour read once), and S[v] = v's own bit; both
-// rows are written in full, so nothing is cleared first and no atomics touch
-// the bitsets. Each source's level-1 kNN entries (the first k of its row)
+// bits per round, each neighbour read once), and S[v] = v's own bit and
+// N[v]; both rows are written in full, so nothing is cleared first and no
+// atomics touch the bitsets. Each source's level-1 kNN entries (the first k of its row)
 // and padding are written by one warp, the act/need masks one 32-source word
 // per warp. The per-launch counters were zeroed by the host.
 __device__ void phase_init_identity(const MsbfsArgs& a) {
@@ -318,7 +320,7 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
                     sbits.z = wi == 2 ? bit : 0u;
                     sbits.w = wi == 3 ? bit : 0u;
                 }
-                S4[off] = sbits;
+                S4[off] = or4(sbits, nbits);  // S holds levels 0 and 1: level 2 needs no fold
                 if (clear_f) F4[off] = z;
                 if (nz4(nbits)) {
                     any = 1;
@@ -529,7 +531,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     const VT* FV = reinterpret_cast<const VT*>(Fc);
     VT* NV = reinterpret_cast<VT*>(Nc);
     VT* SV = reinterpret_cast<VT*>(a.S);
-    const bool fold = d == 2;
+    const bool fold = d == 2 && !a.identity;  // the level-1 frontier is not yet in S
     const VT* actV = reinterpret_cast<const VT*>(a.act);
     const VT zero = vzero(VT{});
     int any = 0;
@@ -655,7 +657,8 @@ __device__ void phase_push_prep(const MsbfsArgs& a, const uint32_t* __restrict__
 // u's neighbours v, each ORing F[u][g] & act & ~S[v] into N[v][g] and S[v][g];
 // v joins queue d the first time it gains a bit. Bits that another warp
 // adds to S[v] during the level are already in N[v], so reading S[v] while
-// it grows loses nothing. At level 2 the level-1 frontier is not yet in S:
+// it grows loses nothing. At level 2 of an explicit source list the
+// level-1 frontier is not yet in S:
 // each queue item folds F[u][g] into S[u][g] (atomically, as other warps
 // may be adding to the same row) and the mask also excludes F[v].
 __device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc, int d) {
@@ -666,7 +669,7 @@ __device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
     const uint4* S4 = reinterpret_cast<const uint4*>(a.S);
     const uint4* act4 = reinterpret_cast<const uint4*>(a.act);
-    const bool fold = d == 2;
+    const bool fold = d == 2 && !a.identity;  // the level-1 frontier is not yet in S
     const int32_t* qin = a.queue + (size_t)((d - 1) % 4) * a.n;
     int32_t* qout = a.queue + (size_t)(d % 4) * a.n;
     const long long items = (long long)ld_volatile_i32(&a.ctr->qcnt[(d - 1) % 4]) * G;
