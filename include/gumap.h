@@ -67,6 +67,8 @@ extern "C" {
 #define GUMAP_WEIGHTS_UNION    0x0u /* out_w = fuzzy-union weight w_ij (default; sources must be NULL) */
 #define GUMAP_WEIGHTS_DIRECTED 0x1u /* out_w = directed similarity a_ij of the source's own list */
 #define GUMAP_CSR_ON_DEVICE    0x2u /* row_ptr / col_idx passed to gumap_knn_create are device pointers */
+#define GUMAP_EMIT_APSP        0x4u /* full form only: the handle may also emit all-pairs distance rows
+                                       (gumap_knn_apsp)                                              */
 
 #define GUMAP_MAX_K    256
 #define GUMAP_DIST_INF 0xFFFFu
@@ -112,7 +114,7 @@ typedef struct gumap_knn gumap_knn;
  *   nnz      number of directed entries (2 |E|), 0 <= nnz < 2^31.
  *   k        neighbourhood size, 1 <= k <= min(n - 1, GUMAP_MAX_K) (k = 1 if n = 1 is rejected).
  *   mode     GUMAP_FULL or GUMAP_PARTIAL.
- *   flags    GUMAP_WEIGHTS_* | GUMAP_CSR_ON_DEVICE.
+ *   flags    GUMAP_WEIGHTS_* | GUMAP_CSR_ON_DEVICE | GUMAP_EMIT_APSP (full form only).
  *   device   CUDA device ordinal; it becomes current on the calling thread.
  *
  * Host CSR (default) is validated on the host; device CSR is validated by a
@@ -177,6 +179,27 @@ int gumap_batch_create(gumap_knn **h, int32_t n_graphs, const int32_t *vertex_of
  */
 int gumap_knn_run(gumap_knn *h, const int32_t *sources, int32_t n_src, int32_t *out_idx,
                   uint16_t *out_dist, float *out_w, void *stream);
+
+/*
+ * gumap_knn_apsp - the hop distance from each source to every vertex: the
+ * rows of the all-pairs shortest-path matrix S of Algorithm 1 (C0,
+ * "S = AllPairsShortestPath(G)"; here row by row for the given sources),
+ * from the same bit-parallel BFS run to completion, together with the
+ * source's kNN list as gumap_knn_run writes it (no weights are computed).
+ * The handle must have been created with GUMAP_EMIT_APSP (full form).
+ *
+ *   sources   device int32[n_src], or NULL for all n vertices (n_src == n)
+ *   out_idx   device int32[n_src][k], out_dist device uint16[n_src][k]: as gumap_knn_run
+ *   out_apsp  device uint16[n_src][n], row i for source i: 0 at the source, hop distances,
+ *             0xFFFF for vertices the source cannot reach (n must be at most 65535, so every
+ *             distance fits below 0xFFFF: INVALID_ARG otherwise)
+ *
+ * Asynchronous on `stream`; rows are written in place (caller-owned).
+ * Errors: INVALID_ARG (flag missing, NULL output, bad sources), OOM, CUDA;
+ * device-side errors via gumap_knn_check().
+ */
+int gumap_knn_apsp(gumap_knn *h, const int32_t *sources, int32_t n_src, int32_t *out_idx, uint16_t *out_dist,
+                   uint16_t *out_apsp, void *stream);
 
 /*
  * gumap_knn_rho_sigma - copy rho_i and sigma_i of the last run (Section 2.1)

@@ -431,9 +431,10 @@ int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut**
     return GUMAP_OK;
 }
 
-// identity: src is the handle's 0 .. n-1 (all vertices as sources)
+// identity: src is the handle's 0 .. n-1 (all vertices as sources); apsp: the
+// all-pairs rows [n_src][n] (preset to 0xFFFF) or NULL
 int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
-              cudaStream_t st) {
+              cudaStream_t st, uint16_t* apsp = nullptr) {
     const int S = choose_block_bits(h, n_src);
     if (S % 128 != 0 || S <= 0) return fail(GUMAP_ERR_INVALID_ARG, "block bits must be a positive multiple of 128");
     const int W = S / 32;
@@ -473,6 +474,8 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
         a.out_dist = out_dist + (size_t)b * S * h->k;
         a.k = h->k;
         a.partial = h->mode == GUMAP_PARTIAL ? 1 : 0;
+        a.apsp = apsp ? apsp + (size_t)b * S * (size_t)h->n : nullptr;
+        a.apsp_ld = h->n;
         a.ctr = h->d_ctr;
         a.direction = h->opt_direction;
         a.push_div = h->opt_push_div;
@@ -618,7 +621,10 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     if (nnz < 0 || nnz > 0x7FFFFFFFll) return fail(GUMAP_ERR_INVALID_ARG, "nnz out of range");
     if (k < 1 || k > GUMAP_MAX_K || k > n - 1) return fail(GUMAP_ERR_INVALID_ARG, "k must be in [1, min(n-1, %d)]", GUMAP_MAX_K);
     if (mode != GUMAP_FULL && mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "bad mode");
-    if (flags & ~(GUMAP_WEIGHTS_DIRECTED | GUMAP_CSR_ON_DEVICE)) return fail(GUMAP_ERR_INVALID_ARG, "unknown flag");
+    if (flags & ~(GUMAP_WEIGHTS_DIRECTED | GUMAP_CSR_ON_DEVICE | GUMAP_EMIT_APSP))
+        return fail(GUMAP_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & GUMAP_EMIT_APSP) && mode != GUMAP_FULL)
+        return fail(GUMAP_ERR_INVALID_ARG, "all-pairs rows need the full form");
     if (2ll * n * k > 0x7FFFFFFFll * 2) return fail(GUMAP_ERR_INVALID_ARG, "n * k too large");
     int ndev = 0;
     CK(cudaGetDeviceCount(&ndev), "cudaGetDeviceCount");
@@ -851,6 +857,25 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
         h->last_union = true;
     }
     return GUMAP_OK;
+}
+
+int gumap_knn_apsp(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
+                   uint16_t* out_apsp, void* stream) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    if (!(h->flags & GUMAP_EMIT_APSP)) return fail(GUMAP_ERR_INVALID_ARG, "handle not created with GUMAP_EMIT_APSP");
+    if (h->batch) return fail(GUMAP_ERR_INVALID_ARG, "all-pairs rows of a batch handle are not available");
+    if (h->n > 65535) return fail(GUMAP_ERR_INVALID_ARG, "all-pairs rows need n <= 65535 (uint16 distances)");
+    if (n_src < 0) return fail(GUMAP_ERR_INVALID_ARG, "n_src < 0");
+    if (n_src == 0) return GUMAP_OK;
+    if (!sources && n_src != h->n) return fail(GUMAP_ERR_INVALID_ARG, "sources == NULL requires n_src == n");
+    if (!out_idx || !out_dist || !out_apsp) return fail(GUMAP_ERR_INVALID_ARG, "NULL output");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaMemsetAsync(out_apsp, 0xFF, (size_t)n_src * (size_t)h->n * sizeof(uint16_t), st), "preset rows");
+    h->last_n_src = -1;  // no weights: rho_sigma and coo refer to no run
+    h->last_union = false;
+    h->last_engine = GUMAP_ENGINE_MSBFS;
+    return run_msbfs(h, sources ? sources : h->d_identity, sources == nullptr, n_src, out_idx, out_dist, st, out_apsp);
 }
 
 int gumap_selftest_wait_timeout(int device, double limit_s) {

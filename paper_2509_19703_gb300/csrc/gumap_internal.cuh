@@ -83,6 +83,10 @@ struct MsbfsArgs {
     uint16_t* out_dist;      // [nb][k]
     int32_t k;
     int32_t partial;         // 1: stop each source once its list is complete
+    // optional all-pairs output (full form): row j of the block at apsp + j * apsp_ld, uint16 hop
+    // distances, preset to 0xFFFF by the host; NULL: not requested
+    uint16_t* apsp;
+    long long apsp_ld;
     DeviceCounters* ctr;
     // direction-optimising levels: 0 = choose per level, 1 = pull only,
     // 2 = push from level 2 on; queue/inq may be NULL only with 1

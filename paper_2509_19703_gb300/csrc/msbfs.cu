@@ -343,6 +343,11 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
             od[t] = t < take ? (uint16_t)1 : kDistInf;
         }
         if (lane == 0) a.cnt[jj] = take;
+        if (a.apsp) {  // distances 0 and 1 of the all-pairs row
+            uint16_t* row = a.apsp + (size_t)jj * a.apsp_ld;
+            if (lane == 0) row[s] = 0;
+            for (int e = e0 + lane; e < e1; e += 32) row[__ldg(a.col + e)] = 1;
+        }
     }
     // act / need, one word of 32 sources per warp: a source whose row holds
     // k entries has its list; one with an empty row is finished and silent
@@ -400,6 +405,11 @@ __device__ void phase_seed(const MsbfsArgs& a) {
         for (int t = lane; t < take; t += 32) {
             oi[t] = __ldg(a.col + e0 + t);
             od[t] = 1;
+        }
+        if (a.apsp && ok) {  // distances 0 and 1 of the all-pairs row
+            uint16_t* row = a.apsp + (size_t)j * a.apsp_ld;
+            if (lane == 0) row[s] = 0;
+            for (int e = e0 + lane; e < e1; e += 32) row[__ldg(a.col + e)] = 1;
         }
         if (lane == 0) {
             a.cnt[j] = take;
@@ -729,15 +739,18 @@ __device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
 }
 
 // Extraction of level d: one warp per 32-source word column with incomplete
-// sources. Lane b owns source 32*w + b.
+// sources (every column when the all-pairs rows are requested: each newly
+// reached (source, vertex) pair gets its distance d there). Lane b owns
+// source 32*w + b.
 __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int Wv = (a.nb + 31) >> 5;
+    const bool ap = a.apsp != nullptr;
     for (long long w = warp; w < Wv; w += nwarps) {
         const uint32_t need0 = ld_volatile_u32(a.need + w);
-        if (need0 == 0u) continue;
+        if (need0 == 0u && !ap) continue;
         const long long j = w * 32 + lane;
         const bool mine_need = (need0 >> lane) & 1u;
         int c = mine_need ? __ldcg(a.cnt + j) : a.k;
@@ -746,7 +759,7 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
         int32_t* oi = a.out_idx + (size_t)j * a.k;
         uint16_t* od = a.out_dist + (size_t)j * a.k;
         // four 32-vertex tiles per round, their loads issued together
-        for (int v00 = 0; v00 < a.n && needw != 0u; v00 += 128) {
+        for (int v00 = 0; v00 < a.n && (needw != 0u || ap); v00 += 128) {
             uint32_t xs[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -755,7 +768,8 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
             }
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t x = xs[q] & needw;
+                // a lane whose source needs no entries has c == k and appends none
+                const uint32_t x = ap ? xs[q] : (xs[q] & needw);
                 if (__ballot_sync(kFull, x != 0u) == 0u) continue;
                 uint32_t mine = 0u;
 #pragma unroll
@@ -765,6 +779,10 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
                 }
                 if (mine) found = true;
                 const int v0 = v00 + 32 * q;
+                if (ap && mine) {
+                    uint16_t* row = a.apsp + (size_t)j * a.apsp_ld + v0;
+                    for (uint32_t m = mine; m; m &= m - 1u) row[__ffs(m) - 1] = (uint16_t)d;
+                }
                 while (mine && c < a.k) {
                     const int i = __ffs(mine) - 1;
                     mine &= mine - 1u;
@@ -881,7 +899,7 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
     int pend = 0;  // level whose extraction is still to run (0: none)
     for (int d = 2; go && d <= a.n; ++d) {
         const int need_now = ld_volatile_i32(&a.ctr->n_need);
-        if (need_now == 0) pend = 0;
+        if (need_now == 0 && !a.apsp) pend = 0;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             // slots of level d + 1 (last used by level d - 3)
             a.ctr->lvl_any[(d + 1) % 3] = 0u;

@@ -20,7 +20,7 @@ from . import _build
 
 # modes, flags, engines, options (mirror include/gumap.h)
 FULL, PARTIAL = 0, 1
-WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE = 0x0, 0x1, 0x2
+WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE, EMIT_APSP = 0x0, 0x1, 0x2, 0x4
 ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER, ENGINE_BATCH = 0, 1, 2, 3, 4
 OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
 OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH, OPT_CTAS_PER_SM, OPT_STAGE = 6, 7, 8, 9, 10
@@ -101,6 +101,7 @@ def load():
             sig = {
                 "gumap_knn_create": [ctypes.POINTER(vp), vp, vp, i32, i64, i32, ctypes.c_int, u32, ctypes.c_int],
                 "gumap_knn_run": [vp, vp, i32, vp, vp, vp, vp],
+                "gumap_knn_apsp": [vp, vp, i32, vp, vp, vp, vp],
                 "gumap_knn_rho_sigma": [vp, vp, vp, vp],
                 "gumap_knn_coo": [vp, vp, vp, vp, vp, vp],
                 "gumap_knn_check": [vp, vp],
@@ -217,6 +218,14 @@ def gumap_knn_run(h, sources, n_src: int, out_idx, out_dist, out_w, stream=None)
     _check(load().gumap_knn_run(h, _dptr(sources, torch.int32, "sources"), int(n_src),
                                 _dptr(out_idx, torch.int32, "out_idx"), _dptr(out_dist, torch.int16, "out_dist"),
                                 _dptr(out_w, torch.float32, "out_w"), _stream(stream)), "gumap_knn_run")
+
+
+def gumap_knn_apsp(h, sources, n_src: int, out_idx, out_dist, out_apsp, stream=None):
+    """All-pairs hop-distance rows (CUDA int16 tensor [n_src, n], uint16 bit
+    pattern) plus the kNN lists, for a handle created with EMIT_APSP."""
+    _check(load().gumap_knn_apsp(h, _dptr(sources, torch.int32, "sources"), int(n_src),
+                                 _dptr(out_idx, torch.int32, "out_idx"), _dptr(out_dist, torch.int16, "out_dist"),
+                                 _dptr(out_apsp, torch.int16, "out_apsp"), _stream(stream)), "gumap_knn_apsp")
 
 
 def gumap_knn_rho_sigma(h, rho, sigma, stream=None):
@@ -415,6 +424,15 @@ class KnnGraph:
         n_src = self.n if sources is None else int(sources.shape[0])
         out = out or self.alloc_outputs(n_src)
         gumap_knn_run(self.h, sources, n_src, out["idx"], out["dist"], out["w"], stream)
+        return out
+
+    def apsp(self, sources=None, stream=None) -> dict:
+        """All-pairs hop-distance rows of the sources ([n_src, n], uint16 bit
+        pattern in int16) and their kNN lists; the handle needs EMIT_APSP."""
+        n_src = self.n if sources is None else int(sources.shape[0])
+        out = self.alloc_outputs(n_src)
+        out["apsp"] = torch.empty((n_src, self.n), dtype=torch.int16, device=torch.device("cuda", self.device))
+        gumap_knn_apsp(self.h, sources, n_src, out["idx"], out["dist"], out["apsp"], stream)
         return out
 
     def rho_sigma(self, n_src: int | None = None, stream=None):

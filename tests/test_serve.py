@@ -74,7 +74,25 @@ def test_results_identical_alone_and_in_the_mix():
         check_all(s, reqs)
         st = gumap.gumap_server_get_stats(s)
         assert st["completed"] == len(mix) and st["failed"] == 0
-        assert st["launches"] < len(mix)  # small requests were batched together
+    finally:
+        gumap.gumap_server_destroy(s)
+
+
+def test_a_backlog_is_batched():
+    """With one worker stream busy on a large full-form graph, the small
+    requests that arrive meanwhile wait together and leave in few batched
+    launches (how many arrive while a stream is busy is a matter of timing
+    otherwise, so the test makes the backlog certain)."""
+    big = (gg.barabasi_albert(60000, 4, 104), 15, gumap.FULL)
+    small = request_mix(40, 105)
+    s = gumap.gumap_server_create(0, 4 << 30, n_streams=1)
+    try:
+        reqs = [(gumap.gumap_serve_submit(s, g.row_ptr, g.col, g.n, g.nnz, k, m), (g, k, m))
+                for g, k, m in [big] + small]
+        check_all(s, reqs)
+        st = gumap.gumap_server_get_stats(s)
+        assert st["completed"] == 1 + len(small) and st["failed"] == 0
+        assert st["launches"] < 1 + len(small) // 2, st  # the small requests were batched together
     finally:
         gumap.gumap_server_destroy(s)
 
