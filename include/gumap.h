@@ -6,11 +6,11 @@
  * graph drawing, and the UMAP fuzzy weights of its edges:
  *
  *   C0  hop distances by breadth-first search from each source vertex,
- *       either to completion (the all-pairs form of GUMAP, Algorithm 1,
- *       "S = AllPairsShortestPath(G)") or stopped once k other vertices are
- *       reached (PartialBFS of SL-GUMAP, Algorithm 4, Section 3.3.1);
+ *       either to completion (the all-pairs distances of GUMAP, Algorithm 1)
+ *       or stopped once k other vertices are reached (the partial BFS of
+ *       SL-GUMAP, Algorithm 4, Section 3.3.1);
  *   C1  the k nearest other vertices of each source in (distance, vertex id)
- *       order (Algorithm 1 "kNN(S)"; the paper breaks ties at random, this
+ *       order (Algorithm 1, its kNN step; the paper breaks ties at random, this
  *       library fixes the tie rule to ascending vertex id so the result is
  *       unique and identical between the two forms);
  *   W   rho_i = distance to the nearest neighbour, sigma_i solving
@@ -102,8 +102,8 @@ extern "C" {
 typedef struct gumap_knn gumap_knn;
 
 /*
- * gumap_knn_create - validate and take a copy of a graph (step "input G",
- * Algorithm 1 / Algorithm 4 line 1).
+ * gumap_knn_create - validate and take a copy of a graph (the input graph of
+ * Algorithm 1 and Algorithm 4).
  *
  *   h        out: new handle (NULL on failure).
  *   row_ptr  CSR row offsets, int32[n + 1], row_ptr[0] = 0, row_ptr[n] = nnz.
@@ -156,8 +156,8 @@ int gumap_batch_create(gumap_knn **h, int32_t n_graphs, const int32_t *vertex_of
 
 /*
  * gumap_knn_run - compute the kNN lists and weights of a set of sources
- * (C0 + C1 + weights; Algorithm 1 lines "S = AllPairsShortestPath(G)",
- * "G_k = kNN(S)"; Algorithm 4; Section 2.1). Asynchronous on `stream`.
+ * (C0 + C1 + weights: the distance and kNN steps of Algorithm 1, or
+ * Algorithm 4; Section 2.1). Asynchronous on `stream`.
  *
  *   sources  device int32[n_src] of source vertex ids, or NULL for all
  *            vertices 0..n-1 in order (then n_src must equal n).
@@ -182,8 +182,8 @@ int gumap_knn_run(gumap_knn *h, const int32_t *sources, int32_t n_src, int32_t *
 
 /*
  * gumap_knn_apsp - the hop distance from each source to every vertex: the
- * rows of the all-pairs shortest-path matrix S of Algorithm 1 (C0,
- * "S = AllPairsShortestPath(G)"; here row by row for the given sources),
+ * rows of the all-pairs shortest-path matrix S of Algorithm 1 (its C0 step;
+ * here row by row for the given sources),
  * from the same bit-parallel BFS run to completion, together with the
  * source's kNN list as gumap_knn_run writes it (no weights are computed).
  * The handle must have been created with GUMAP_EMIT_APSP (full form).

@@ -9,7 +9,7 @@
  *
  * What it computes (each function cites the passage it follows):
  *   - hop distances by breadth-first search from each source
- *       (Algorithm 1, AllPairsShortestPath; Algorithm 4, PartialBFS);
+ *       (Algorithm 1, all-pairs distances; Algorithm 4, partial BFS);
  *   - the kNN list of each source: the first k other vertices in
  *       (distance, vertex id) order (Section 3.3.1; the paper breaks ties at
  *       random, this library fixes the tie rule to ascending vertex id);
@@ -41,7 +41,7 @@
 #define ORACLE_INF16 0xFFFFu
 
 /* ------------------------------------------------------------------ */
-/* Breadth-first search (hop distances), Algorithm 1 line "APSP".      */
+/* Breadth-first search (hop distances): Algorithm 1's distances.     */
 /* dist[v] = -1 for unreachable vertices.                              */
 /* ------------------------------------------------------------------ */
 int oracle_bfs(const int32_t *row_ptr, const int32_t *col, int32_t n, int32_t s,
@@ -101,7 +101,7 @@ static void write_row(const dv_pair *p, int32_t cnt, int32_t k, int32_t *idx, ui
 }
 
 /*
- * Full form (GUMAP, Algorithm 1: S = AllPairsShortestPath(G), then kNN(S)):
+ * Full form (GUMAP, Algorithm 1: all-pairs distances, then the k nearest):
  * for each source run BFS to completion, then sort every reachable vertex
  * other than the source by (distance, id) and keep the first k.
  * sources == NULL means all vertices 0..n-1 in order.

@@ -7,10 +7,9 @@
 //   N[v]  next:     sources that reach v at the current level
 //   S[v]  seen:     sources that reached v at any level so far (F included)
 // A level is the pull step  N[v] = (OR_{u in adj(v)} F[u]) & act & ~S[v],
-// then S[v] |= N[v], which is the frontier expansion of Algorithm 4
-// (tovisit -> newvisit) and of
-// the BFS inside AllPairsShortestPath (Algorithm 1) run for 32*W sources at
-// once. The OR over neighbours stops as soon as every still-missing source
+// then S[v] |= N[v], which is one frontier expansion of the partial BFS of
+// Algorithm 4 and of the BFS behind Algorithm 1's all-pairs distances, run
+// for 32*W sources at once. The OR over neighbours stops as soon as every still-missing source
 // bit is covered (the bottom-up early exit), and a vertex already reached by
 // every active source costs no neighbour loads at all.
 //
@@ -34,9 +33,9 @@
 // to every incomplete source the vertices it reached at this level in
 // ascending id until its list holds k entries: this is exactly the
 // (distance, id) order, because levels are visited in increasing distance
-// and vertices in increasing id. In the partial form (Algorithm 4,
-// "break if visited.size > k") a source whose list is complete stops
-// propagating: its bit leaves `act`. The full form keeps every source
+// and vertices in increasing id. In the partial form (Algorithm 4, which
+// stops a source once more than k vertices are visited) a source whose list
+// is complete stops propagating: its bit leaves `act`. The full form keeps every source
 // propagating until no source reaches a new vertex.
 //
 // All levels run inside one cooperative launch; phases are separated by a
