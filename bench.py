@@ -27,6 +27,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -43,7 +44,7 @@ WORKLOAD = ("full-APSP GUMAP kNN + UMAP weights + fuzzy union + sorted COO, k=15
             "BA n=20000 m0=5 seed 1 and G(n=5000, p=0.1) seed 2")
 FLUSH_BYTES = 512 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "msbfs_kernel_traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_2509_19703_gb300", "csrc", "msbfs.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2509_19703_gb300", "csrc", f) for f in ("msbfs.cu", "gumap_internal.cuh")]
 
 
 def parse_args():
@@ -173,8 +174,17 @@ def measured_peak_gbs():
 
 
 def kernel_sha():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    """sha256 of the MS-BFS kernel's code (its source and the header of its
+    argument structures) with comments and whitespace removed, so an edit of
+    a comment does not void a traffic record taken on the same code."""
+    code = ""
+    for path in KERNEL_SRCS:
+        with open(path) as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        code += re.sub(r"\s+", "", src)
+    return hashlib.sha256(code.encode()).hexdigest()
 
 
 def recorded_traffic():
@@ -185,7 +195,7 @@ def recorded_traffic():
             rec = json.load(f)
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_sha256") != kernel_sha():
+    if rec.get("kernel_code_sha256") != kernel_sha():
         return None
     return rec.get("dram_bytes_per_launch")
 

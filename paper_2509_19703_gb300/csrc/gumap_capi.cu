@@ -177,6 +177,7 @@ struct gumap_knn {
         int bytes;         // shared memory of the largest CTA share, rounded up to 1 KB
     };
     std::vector<SliceCut> cuts;
+    int first_grid = -1;  // a grid size launched once without its layout (built on its second launch)
     int64_t staged_launches = 0;
     std::vector<int32_t> deg;    // host copy of the vertex degrees
     DeviceCounters* d_ctr = nullptr;
@@ -486,7 +487,14 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
         a.sat = reinterpret_cast<uint8_t*>(h->bits.p) + sat_off;
         const int grid = msbfs_grid_for(a, h->coop_grid[a.pull_width == 2][a.ctas_per_sm == 4]);
         const int cap = h->stage_cap[a.ctas_per_sm == 4];
-        if (h->opt_stage && h->n > h->n_heavy && cap > 0) {
+        // The layout costs host work, uploads and a stream synchronisation, so a
+        // grid size's first launch reads the rows from the CSR and its second
+        // launch builds the layout: a handle that runs once never pays for it.
+        bool layout = false;
+        for (const auto& c : h->cuts) layout = layout || c.grid == grid;
+        if (!layout && h->first_grid != grid) {
+            h->first_grid = grid;
+        } else if (h->opt_stage && h->n > h->n_heavy && cap > 0) {
             const gumap_knn::SliceCut* c = nullptr;
             if ((rc = get_cut(h, grid, st, &c))) return rc;
             if (c->bytes <= cap) {
@@ -596,7 +604,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     if (!h) return GUMAP_OK;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();  // nothing queued may still use the buffers handed back below
-    pool_free(h->d_rp, sizeof(int32_t) * ((size_t)h->n + 1));
+    pool_free(h->d_rp, sizeof(int32_t) * ((size_t)h->n + 2));
     pool_free(h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz, 1));
     pool_free(h->d_identity, sizeof(int32_t) * (size_t)h->n);
     pool_free(h->d_order, sizeof(int32_t) * (size_t)h->n);
@@ -656,7 +664,8 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     cudaError_t e;
 
     const cudaMemcpyKind kind = (flags & GUMAP_CSR_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    if ((e = pool_alloc((void**)&h->d_rp, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess ||
+    // row_ptr plus one slot for the device validation's verdict
+    if ((e = pool_alloc((void**)&h->d_rp, sizeof(int32_t) * ((size_t)n + 2))) != cudaSuccess ||
         (e = pool_alloc((void**)&h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
         (e = pool_alloc((void**)&h->d_identity, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
         (e = pool_alloc((void**)&h->d_ctr, sizeof(DeviceCounters))) != cudaSuccess) {
@@ -670,32 +679,27 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
         gumap_knn_destroy(h);
         return cuda_fail(e, "upload");
     }
-    if (flags & GUMAP_CSR_ON_DEVICE) {
-        int32_t bad = 0;
-        if ((e = launch_validate_csr(h->d_rp, h->d_col, n, nnz, &h->d_ctr->status, 0)) != cudaSuccess ||
-            (e = cudaMemcpy(&bad, &h->d_ctr->status, sizeof(int32_t), cudaMemcpyDeviceToHost)) != cudaSuccess) {
-            gumap_knn_destroy(h);
-            return cuda_fail(e, "device CSR validation");
-        }
-        cudaMemset(&h->d_ctr->status, 0, sizeof(int32_t));
-        if (bad) {
-            gumap_knn_destroy(h);
-            return fail(GUMAP_ERR_INVALID_GRAPH, "invalid CSR (device validation)");
-        }
-    }
     if ((e = pool_alloc((void**)&h->d_order, sizeof(int32_t) * (size_t)n)) != cudaSuccess) {
         gumap_knn_destroy(h);
         return cuda_fail(e, "cudaMalloc");
     }
     {
-        std::vector<int32_t> rp_dev;  // row_ptr read back when the CSR came on the device
+        // A CSR on the device is validated there; the verdict lands in the slot
+        // after row_ptr, so one readback brings back both (the host needs
+        // row_ptr for the degrees).
+        std::vector<int32_t> rp_dev;
         const int32_t* rp = row_ptr;
         if (flags & GUMAP_CSR_ON_DEVICE) {
-            rp_dev.resize((size_t)n + 1);
-            if ((e = cudaMemcpy(rp_dev.data(), h->d_rp, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost)) !=
-                cudaSuccess) {
+            rp_dev.resize((size_t)n + 2);
+            if ((e = launch_validate_csr(h->d_rp, h->d_col, n, nnz, h->d_rp + n + 1, 0)) != cudaSuccess ||
+                (e = cudaMemcpy(rp_dev.data(), h->d_rp, sizeof(int32_t) * ((size_t)n + 2), cudaMemcpyDeviceToHost)) !=
+                    cudaSuccess) {
                 gumap_knn_destroy(h);
-                return cuda_fail(e, "row_ptr readback");
+                return cuda_fail(e, "device CSR validation");
+            }
+            if (rp_dev[(size_t)n + 1]) {
+                gumap_knn_destroy(h);
+                return fail(GUMAP_ERR_INVALID_GRAPH, "invalid CSR (device validation)");
             }
             rp = rp_dev.data();
         }

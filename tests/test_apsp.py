@@ -37,7 +37,7 @@ def u16(t):
     return t.cpu().numpy().view(np.uint16)
 
 
-def apsp_gpu(g, k, sources=None, block_bits=None, options=()):
+def apsp_gpu(g, k, sources=None, block_bits=None, options=(), repeat=1):
     with gumap.KnnGraph.from_graph(g, k, mode=gumap.FULL, flags=gumap.EMIT_APSP) as kg:
         kg.set_option(gumap.OPT_ENGINE, MSBFS)
         if block_bits is not None:
@@ -45,7 +45,8 @@ def apsp_gpu(g, k, sources=None, block_bits=None, options=()):
         for opt, val in options:
             kg.set_option(opt, val)
         src = None if sources is None else torch.as_tensor(np.asarray(sources, dtype=np.int32), device="cuda")
-        out = kg.apsp(src)
+        for _ in range(repeat):  # the staged layout of a grid size is built on its second launch
+            out = kg.apsp(src)
         kg.check()
         return u16(out["apsp"]), out["idx"].cpu().numpy(), gumap.dist_u16(out["dist"])
 
@@ -67,7 +68,7 @@ def test_every_row_matches_the_oracle(g):
                          ids=["default", "unstaged", "push"])
 def test_rows_on_every_build(options):
     g = gg.barabasi_albert(2500, 4, 61)
-    got, _, _ = apsp_gpu(g, 15, options=options)
+    got, _, _ = apsp_gpu(g, 15, options=options, repeat=2)
     assert np.array_equal(got, oracle.apsp(g))
 
 
