@@ -76,7 +76,7 @@ extern "C" {
 /* ---------------------------------------------------------------- engines */
 #define GUMAP_ENGINE_AUTO     0 /* pick by graph size, mode and the tuned table */
 #define GUMAP_ENGINE_MSBFS    1 /* bit-parallel multi-source BFS, bitsets in global memory (L2) */
-#define GUMAP_ENGINE_MSBFS_SM 2 /* bit-parallel multi-source BFS, bitsets in one CTA's shared memory */
+#define GUMAP_ENGINE_MSBFS_SM 2 /* reserved, not accepted (small graphs in shared memory: GUMAP_ENGINE_BATCH) */
 #define GUMAP_ENGINE_FRONTIER 3 /* partial form only: warp per source, bounded merge of sorted rows */
 #define GUMAP_ENGINE_BATCH    4 /* batch handles: one persistent launch, one CTA per (graph, source block) */
 
