@@ -438,6 +438,7 @@ def run_batch_workload(args):
         return statistics.median(ts)
 
     kb, _ = gumap.KnnGraph.batch(graphs, K_NEIGHBOURS, modes)
+    tuned = kb.autotune()  # the widest unit (source-block width), timed before any timed step
     out = kb.alloc_outputs(kb.n)
     for _ in range(args.warmup):
         kb.run(out=out)
@@ -469,6 +470,7 @@ def run_batch_workload(args):
             "config": {"workload": "config 4: 2000 seeded graphs, n log-uniform in [100, 20000], grid / BA 2..8 / "
                                    "G(n,p) mean degree 4..40 / random tree, full or partial 50/50, k=15",
                        "graphs": len(graphs), "vertices": n_total, "units": st["n_blocks"],
+                       "autotuned": {key: tuned[key] for key in ("batch_width", "best_ms", "default_ms")},
                        "l2": "flushed (512 MB write) before each timed step"},
             "one_launch_per_graph": {"graphs_per_s": len(graphs) / (ms_single * 1e-3), "ms_per_step": ms_single},
             "speedup_vs_one_launch_per_graph": ms_single / ms_batch,

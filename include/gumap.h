@@ -93,6 +93,8 @@ extern "C" {
 #define GUMAP_OPT_PULL_WIDTH  8 /* value: 32-bit words per MS-BFS pull item, 4 (default) or 2     */
 #define GUMAP_OPT_CTAS_PER_SM 9 /* value: resident 256-thread MS-BFS CTAs per SM the kernel is built
                                    for: 3 (default, up to 80 registers a thread) or 4 (64)        */
+#define GUMAP_OPT_BATCH_WIDTH 11 /* value: batch handles: widest unit in 32-bit words (32 sources each),
+                                   1..64, 0 = 64 (default); re-plans the batch, synchronises      */
 #define GUMAP_OPT_STAGE      10 /* value: 1 (default) = each MS-BFS CTA bulk-copies its slice of the
                                    ordinary-degree rows into shared memory once per launch when
                                    every slice fits; 0 = neighbour ids always read from the CSR;
@@ -274,6 +276,8 @@ typedef struct {
     int64_t state_bytes;
     int32_t ctas_per_sm;
     int32_t stage;
+    int32_t push_div;        /* push threshold of the automatic direction (when direction == 0) */
+    int32_t batch_width;     /* batch handles: widest unit in words */
 } gumap_tune_result;
 
 /*
@@ -281,8 +285,9 @@ typedef struct {
  * timing gumap_knn_run (all vertices) on it: MS-BFS state budget (which
  * sets the source-block width), pull item width, heavy-vertex degree
  * multiplier, CTAs per SM (the CTA shape: registers per thread against
- * resident warps), staging of rows in shared memory and level direction for
- * the full form; engine for the partial form. The best settings are applied to the handle and, if cache_path is
+ * resident warps), staging of rows in shared memory and level direction
+ * with its push threshold for the full form; engine for the partial form;
+ * the widest unit (source-block width) for batch handles (no cache). The best settings are applied to the handle and, if cache_path is
  * not NULL, appended to that JSON-lines file under a key of the graph's
  * shape class (form, k, log2 n, log2 mean degree, hub ratio); a later
  * handle of the same class created while the environment variable

@@ -90,16 +90,16 @@ bool gumap::host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_
 // else frontier + next with the visited bitset in a global slab), ordered
 // longest first so the work queue's tail is short. Returns -1, or the index
 // of a graph too large for the engine.
-int32_t gumap::plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr,
+int32_t gumap::plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int64_t* graph_edges,
                           const int32_t* modes, std::vector<BatchUnit>& units_out, size_t& smem,
-                          long long& slab) {
+                          long long& slab, int32_t max_w) {
     std::vector<BatchUnit> units;
     std::vector<long long> cost;
     smem = 0;
     slab = 0;
     for (int32_t g = 0; g < n_graphs; ++g) {
         const int32_t lo = vertex_offsets[g], ng = vertex_offsets[g + 1] - lo;
-        const int32_t wmax = std::min<int32_t>(kMaxBatchW, (ng + 31) / 32);
+        const int32_t wmax = std::min<int32_t>(std::min<int32_t>(kMaxBatchW, std::max<int32_t>(max_w, 1)), (ng + 31) / 32);
         int32_t W = 0, vg = 0;
         for (int32_t w = wmax; w >= 1 && !W; --w)
             if (4ull * (3ull * ng * w + 34ull * w) <= kBatchSmemBudget) W = w;
@@ -112,7 +112,7 @@ int32_t gumap::plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const
         const size_t need = 4ull * ((vg ? 2ull : 3ull) * ng * W + 34ull * W);
         smem = std::max(smem, need);
         if (vg) slab = std::max<long long>(slab, (long long)ng * W);
-        const long long edges = (long long)row_ptr[lo + ng] - row_ptr[lo];
+        const long long edges = graph_edges[g];
         for (int32_t s = 0; s < ng; s += 32 * W) {
             BatchUnit u{};
             u.v0 = lo;
@@ -220,6 +220,9 @@ struct gumap_knn {
     int batch_grid = 0;
     long long vslab_words = 0;
     DevBuf vslab;
+    std::vector<int32_t> batch_offsets, batch_modes;  // the batch's graphs, kept to re-plan
+    std::vector<int64_t> batch_edges;
+    int32_t batch_width = 0;  // GUMAP_OPT_BATCH_WIDTH in force
 
     // stats
     int64_t bfs_launches = 0;
@@ -724,6 +727,43 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     return GUMAP_OK;
 }
 
+// Cuts a batch handle's graphs into units of at most max_w words (32 max_w
+// sources) and sets up the launch: shared memory, grid, visited slab, unit
+// table. The device must be done with the previous plan's buffers.
+int apply_batch_plan(gumap_knn* h, int32_t max_w) {
+    std::vector<BatchUnit> sorted;
+    size_t smem = 0;
+    long long slab = 0;
+    const int32_t ng = (int32_t)h->batch_modes.size();
+    const int32_t big =
+        plan_batch(ng, h->batch_offsets.data(), h->batch_edges.data(), h->batch_modes.data(), sorted, smem, slab, max_w);
+    if (big >= 0)
+        return fail(GUMAP_ERR_TOO_LARGE, "graph %d (%d vertices) does not fit the batched engine", big,
+                    h->batch_offsets[(size_t)big + 1] - h->batch_offsets[(size_t)big]);
+    cudaError_t e;
+    CK(batch_prepare(smem), "batch kernel attributes");
+    int per_sm = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_ptr(), batch_threads(), smem),
+       "batch occupancy");
+    if (per_sm < 1) return fail(GUMAP_ERR_CUDA, "batch kernel cannot be resident");
+    h->batch_grid = h->num_sms * per_sm;
+    h->batch_smem = smem;
+    h->vslab_words = slab;
+    int rc;
+    if (slab > 0 && (rc = ensure(h->vslab, (size_t)slab * 4 * h->batch_grid, "batch slab"))) return rc;
+    pool_free(h->d_units, sizeof(BatchUnit) * (size_t)std::max<int32_t>(h->n_units, 1));
+    h->d_units = nullptr;
+    h->n_units = (int32_t)sorted.size();  // sizes the block handed back by destroy
+    if ((e = pool_alloc((void**)&h->d_units, sizeof(BatchUnit) * sorted.size())) != cudaSuccess) {
+        h->n_units = 0;
+        return cuda_fail(e, "batch units");
+    }
+    CK(cudaMemcpy(h->d_units, sorted.data(), sizeof(BatchUnit) * sorted.size(), cudaMemcpyHostToDevice),
+       "batch units");
+    h->batch_width = max_w;
+    return GUMAP_OK;
+}
+
 int gumap_batch_create(gumap_knn** out, int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr,
                        const int32_t* col_idx, int64_t nnz, int32_t k, const int32_t* modes, uint32_t flags,
                        int device) {
@@ -750,42 +790,15 @@ int gumap_batch_create(gumap_knn** out, int32_t n_graphs, const int32_t* vertex_
             }
         }
     }
-    std::vector<BatchUnit> sorted;
-    size_t smem = 0;
-    long long slab = 0;
-    const int32_t big = plan_batch(n_graphs, vertex_offsets, row_ptr, modes, sorted, smem, slab);
-    if (big >= 0) {
-        gumap_knn_destroy(h);
-        return fail(GUMAP_ERR_TOO_LARGE, "graph %d (%d vertices) does not fit the batched engine", big,
-                    vertex_offsets[big + 1] - vertex_offsets[big]);
-    }
-    cudaError_t e;
-    if ((e = batch_prepare(smem)) != cudaSuccess) {
-        gumap_knn_destroy(h);
-        return cuda_fail(e, "batch kernel attributes");
-    }
-    int per_sm = 0;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel_ptr(), batch_threads(), smem)) !=
-            cudaSuccess ||
-        per_sm < 1) {
-        gumap_knn_destroy(h);
-        return e != cudaSuccess ? cuda_fail(e, "batch occupancy") : fail(GUMAP_ERR_CUDA, "batch kernel cannot be resident");
-    }
-    h->batch_grid = h->num_sms * per_sm;
-    h->batch_smem = smem;
-    h->vslab_words = slab;
-    if (slab > 0 && (rc = ensure(h->vslab, (size_t)slab * 4 * h->batch_grid, "batch slab"))) {
+    h->batch_offsets.assign(vertex_offsets, vertex_offsets + n_graphs + 1);
+    h->batch_modes.assign(modes, modes + n_graphs);
+    h->batch_edges.resize((size_t)n_graphs);
+    for (int32_t g = 0; g < n_graphs; ++g)
+        h->batch_edges[(size_t)g] = (int64_t)row_ptr[vertex_offsets[g + 1]] - row_ptr[vertex_offsets[g]];
+    if ((rc = apply_batch_plan(h, kMaxBatchW))) {
         gumap_knn_destroy(h);
         return rc;
     }
-    h->n_units = (int32_t)sorted.size();  // sizes the block handed back by destroy
-    if ((e = pool_alloc((void**)&h->d_units, sizeof(BatchUnit) * sorted.size())) != cudaSuccess ||
-        (e = cudaMemcpy(h->d_units, sorted.data(), sizeof(BatchUnit) * sorted.size(), cudaMemcpyHostToDevice)) !=
-            cudaSuccess) {
-        gumap_knn_destroy(h);
-        return cuda_fail(e, "batch units");
-    }
-    h->n_units = (int32_t)sorted.size();
     h->batch = true;
     h->n_graphs = n_graphs;
     *out = h;
@@ -967,6 +980,12 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             if (value != 2 && value != 4) return fail(GUMAP_ERR_INVALID_ARG, "pull width must be 2 or 4 words");
             h->opt_pull_width = (int)value;
             return GUMAP_OK;
+        case GUMAP_OPT_BATCH_WIDTH:
+            if (!h->batch) return fail(GUMAP_ERR_INVALID_ARG, "batch width applies to batch handles");
+            if (value < 0 || value > kMaxBatchW) return fail(GUMAP_ERR_INVALID_ARG, "batch width must be in [0, 64]");
+            CK(cudaSetDevice(h->device), "cudaSetDevice");
+            CK(cudaDeviceSynchronize(), "sync");
+            return apply_batch_plan(h, value == 0 ? kMaxBatchW : (int32_t)value);
         case GUMAP_OPT_STAGE:
             if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "stage must be 0, 1 or 2");
             h->opt_stage = (int)value;

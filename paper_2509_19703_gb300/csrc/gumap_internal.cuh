@@ -174,8 +174,9 @@ constexpr size_t kBatchSmemBudget = 220000;
 
 // ---- gumap_capi.cu (host helpers shared with the server)
 bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, std::string& why);
-int32_t plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int32_t* row_ptr, const int32_t* modes,
-                   std::vector<BatchUnit>& units, size_t& smem, long long& slab);
+// graph_edges[g]: adjacency entries of graph g; max_w: widest unit allowed (words, <= kMaxBatchW).
+int32_t plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int64_t* graph_edges, const int32_t* modes,
+                   std::vector<BatchUnit>& units, size_t& smem, long long& slab, int32_t max_w = kMaxBatchW);
 
 // ---- pool.cu: the handles' device-memory pool
 cudaError_t pool_alloc(void** p, size_t bytes);

@@ -246,7 +246,9 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
     }
     int W = 0, nblocks = 0;  // full form of a large graph: MS-BFS blocks
     if (small) {
-        if (plan_batch(ng, offs.data(), rp_union.data(), modes.data(), units, smem, slab) >= 0) return false;
+        std::vector<int64_t> edges((size_t)ng);
+        for (int g = 0; g < ng; ++g) edges[(size_t)g] = group[g]->nnz;
+        if (plan_batch(ng, offs.data(), edges.data(), modes.data(), units, smem, slab) >= 0) return false;
     } else if (group[0]->mode == GUMAP_FULL) {
         const double budget = 96.0 * 1024 * 1024;
         long long S = (long long)(budget * 8.0 / (3.0 * (double)N)) / 128 * 128;

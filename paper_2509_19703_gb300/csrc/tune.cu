@@ -5,7 +5,9 @@
 // budget (it sets the source-block width), the pull item width, the degree
 // multiplier above which a vertex's items are warp-wide, then on the best of
 // those the CTAs per SM (the CTA shape), the staging of rows in shared
-// memory and the level direction; for the partial form the engine. Each candidate runs once to
+// memory and the automatic level direction at three push thresholds; for the
+// partial form the engine; for batch handles the widest unit (the
+// source-block width of the batched engine). Each candidate runs once to
 // warm up, then three times with the L2 flushed before each run; the median
 // device time decides. The winner is kept in a JSON-lines cache under a key
 // of the graph's shape class, so graphs of the same class start tuned.
@@ -30,6 +32,8 @@ struct Setting {
     long long state_bytes = 0;
     int ctas_per_sm = 3;
     int stage = 1;
+    int push_div = 8;
+    int batch_width = 0;  // batch handles only
 };
 
 std::string shape_key(const gumap_knn_info& in) {
@@ -53,9 +57,10 @@ bool read_cache(const char* path, const std::string& key, Setting* s) {
         double ms = 0;
         if (sscanf(line.c_str(),
                    "{\"key\": \"%199[^\"]\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, "
-                   "\"direction\": %d, \"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"ms\": %lf}",
+                   "\"direction\": %d, \"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, "
+                   "\"push_div\": %d, \"ms\": %lf}",
                    k, &t.engine, &t.pull_width, &t.heavy_mult, &t.direction, &t.state_bytes, &t.ctas_per_sm,
-                   &t.stage, &ms) == 9 &&
+                   &t.stage, &t.push_div, &ms) == 10 &&
             key == k) {
             *s = t;  // the last entry of a key wins
             found = true;
@@ -69,14 +74,15 @@ void append_cache(const char* path, const std::string& key, const Setting& s, do
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, \"direction\": %d, "
-            "\"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"ms\": %.6f}\n",
+            "\"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"push_div\": %d, \"ms\": %.6f}\n",
             key.c_str(), s.engine, s.pull_width, s.heavy_mult, s.direction, s.state_bytes, s.ctas_per_sm, s.stage,
-            ms);
+            s.push_div, ms);
     fclose(f);
 }
 
 int apply(gumap_knn* h, const gumap_knn_info& in, const Setting& s) {
     int rc;
+    if (in.batch) return gumap_knn_set_option(h, GUMAP_OPT_BATCH_WIDTH, s.batch_width);
     if ((rc = gumap_knn_set_option(h, GUMAP_OPT_ENGINE, s.engine))) return rc;
     if (s.engine == GUMAP_ENGINE_MSBFS || s.engine == GUMAP_ENGINE_AUTO) {
         const long long mean = in.n > 0 ? in.nnz / in.n : 0;
@@ -85,6 +91,7 @@ int apply(gumap_knn* h, const gumap_knn_info& in, const Setting& s) {
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_DIRECTION, s.direction))) return rc;
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_CTAS_PER_SM, s.ctas_per_sm))) return rc;
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_STAGE, s.stage))) return rc;
+        if ((rc = gumap_knn_set_option(h, GUMAP_OPT_PUSH_DIV, s.push_div))) return rc;
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_HEAVY_DEGREE, std::max<long long>(64, s.heavy_mult * mean))))
             return rc;
     }
@@ -110,12 +117,11 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
     gumap_knn_info in;
     int rc = gumap_knn_get_info(h, &in);
     if (rc) return rc;
-    if (in.batch) return GUMAP_ERR_INVALID_ARG;
     gumap_tune_result res;
     std::memset(&res, 0, sizeof(res));
     const std::string key = shape_key(in);
     Setting best;
-    if (cache_path && read_cache(cache_path, key, &best)) {
+    if (!in.batch && cache_path && read_cache(cache_path, key, &best)) {
         if ((rc = apply(h, in, best))) return rc;
         res.from_cache = 1;
         res.engine = best.engine;
@@ -125,6 +131,7 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
         res.state_bytes = best.state_bytes;
         res.ctas_per_sm = best.ctas_per_sm;
         res.stage = best.stage;
+        res.push_div = best.push_div;
         if (out) *out = res;
         return GUMAP_OK;
     }
@@ -175,7 +182,13 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
     };
 
     std::vector<Setting> cands;
-    if (in.mode == GUMAP_FULL) {
+    if (in.batch) {  // the widest unit: wide units share each level's sweep, narrow ones balance the CTAs
+        for (int w : {64, 32, 16, 8}) {
+            Setting s;
+            s.batch_width = w;
+            cands.push_back(s);
+        }
+    } else if (in.mode == GUMAP_FULL) {
         for (long long budget : {96ll << 20, 256ll << 20, 1024ll << 20})
             for (int width : {4, 2})
                 for (int hm : {2, 4, 8}) {
@@ -216,12 +229,17 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
             best = s;
         }
     }
-    if (in.mode == GUMAP_FULL) {  // then, one at a time on the best so far: CTA shape, staging, direction
-        for (int step = 0; step < 3; ++step) {
+    if (!in.batch && in.mode == GUMAP_FULL) {
+        // then, one at a time on the best so far: CTA shape, staging, and the
+        // automatic direction at three push thresholds
+        for (int step = 0; step < 5; ++step) {
             Setting s = best;
             if (step == 0) s.ctas_per_sm = best.ctas_per_sm == 4 ? 3 : 4;
             else if (step == 1) s.stage = best.stage ? 0 : 1;
-            else s.direction = 0;
+            else {
+                s.direction = 0;
+                s.push_div = step == 2 ? 8 : step == 3 ? 64 : 512;
+            }
             double ms = 0.0;
             if ((rc = apply(h, in, s)) || (rc = time_run(&ms))) {
                 cleanup();
@@ -236,7 +254,7 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
     }
     cleanup();
     if ((rc = apply(h, in, best))) return rc;
-    if (cache_path) append_cache(cache_path, key, best, best_ms);
+    if (cache_path && !in.batch) append_cache(cache_path, key, best, best_ms);
     res.best_ms = best_ms;
     res.default_ms = default_ms;
     res.engine = best.engine;
@@ -246,6 +264,8 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
     res.state_bytes = best.state_bytes;
     res.ctas_per_sm = best.ctas_per_sm;
     res.stage = best.stage;
+    res.push_div = best.push_div;
+    res.batch_width = best.batch_width;
     if (out) *out = res;
     return GUMAP_OK;
 }

@@ -24,6 +24,7 @@ WEIGHTS_UNION, WEIGHTS_DIRECTED, CSR_ON_DEVICE, EMIT_APSP = 0x0, 0x1, 0x2, 0x4
 ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER, ENGINE_BATCH = 0, 1, 2, 3, 4
 OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
 OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH, OPT_CTAS_PER_SM, OPT_STAGE = 6, 7, 8, 9, 10
+OPT_BATCH_WIDTH = 11
 DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
 MAX_K = 256
 DIST_INF = 0xFFFF
@@ -61,7 +62,8 @@ class _Tune(ctypes.Structure):
     _fields_ = [("from_cache", ctypes.c_int32), ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_double),
                 ("default_ms", ctypes.c_double), ("engine", ctypes.c_int32), ("pull_width", ctypes.c_int32),
                 ("heavy_mult", ctypes.c_int32), ("direction", ctypes.c_int32), ("state_bytes", ctypes.c_int64),
-                ("ctas_per_sm", ctypes.c_int32), ("stage", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("stage", ctypes.c_int32), ("push_div", ctypes.c_int32),
+                ("batch_width", ctypes.c_int32)]
 
 
 class _ServerOpts(ctypes.Structure):

@@ -22,9 +22,12 @@ def _cuda():
     gumap.load()
 
 
-def run_batch(graphs, k, modes, coo=True):
+def run_batch(graphs, k, modes, coo=True, width=None, tune=False):
     kb, offs = gumap.KnnGraph.batch(graphs, k, modes)
     with kb:
+        tuned = kb.autotune() if tune else None
+        if width is not None:
+            kb.set_option(gumap.OPT_BATCH_WIDTH, width)
         out = kb.run()
         rho, sigma = kb.rho_sigma()
         res = {}
@@ -35,7 +38,7 @@ def run_batch(graphs, k, modes, coo=True):
         torch.cuda.synchronize()
         res.update(idx=out["idx"].cpu().numpy(), dist=gumap.dist_u16(out["dist"]),
                    w=out["w"].cpu().numpy().astype(np.float64), rho=rho.cpu().numpy().astype(np.float64),
-                   sigma=sigma.cpu().numpy().astype(np.float64), stats=kb.stats())
+                   sigma=sigma.cpu().numpy().astype(np.float64), stats=kb.stats(), tuned=tuned)
     return res, offs
 
 
@@ -54,6 +57,21 @@ def test_batch_matches_oracle_on_the_union(k):
     assert_parity(res, oracle_ref(union, k, "partial"), f"batch k={k}")
     assert res["stats"]["engine"] == gumap.ENGINE_BATCH
     assert res["stats"]["bfs_launches"] == 1
+
+
+@pytest.mark.parametrize("width", [1, 4, 16, 64])
+def test_batch_width_keeps_the_rows(width):
+    """Units of at most `width` words (re-planned on the handle): same rows."""
+    graphs, modes = small_mix(40, 95)
+    res, _ = run_batch(graphs, 15, modes, width=width)
+    assert_parity(res, oracle_ref(gg.disjoint_union(graphs), 15, "partial"), f"batch width {width}")
+
+
+def test_batch_autotune_keeps_the_rows():
+    graphs, modes = small_mix(40, 96)
+    res, _ = run_batch(graphs, 15, modes, tune=True)
+    assert res["tuned"]["batch_width"] in (8, 16, 32, 64) and res["tuned"]["candidates"] == 4
+    assert_parity(res, oracle_ref(gg.disjoint_union(graphs), 15, "partial"), "tuned batch")
 
 
 def test_batch_rows_equal_single_graph_handles():
