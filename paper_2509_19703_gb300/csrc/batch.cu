@@ -7,7 +7,9 @@
 // unit's graph live in the CTA's shared memory (and the visited bitset too
 // when it fits, otherwise in a CTA-private slab of global memory), so a BFS
 // level costs one __syncthreads instead of a grid barrier and the neighbour
-// gathers are shared-memory loads. The per-level work is the same as the
+// gathers are shared-memory loads. Units of 4 or more words pull 128-bit
+// groups (a vertex's neighbour ids are then read once per 4 words). The
+// per-level work is the same as the
 // global engine (msbfs.cu): a pull N[v] = OR_{u in adj(v)} F[u] masked by
 // act & ~visited, with the early exit once every missing source bit is
 // covered (frontier expansion of Algorithm 4 / the BFS of Algorithm 1), and
@@ -113,6 +115,45 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchArgs a) {
             const int need_now = s_need;
             // ---- pull
             int any = 0;
+            if ((W & 3) == 0) {  // 128-bit items: a vertex's neighbour ids read once per 4 words
+                const int G4 = W >> 2;
+                const uint4* F4 = reinterpret_cast<const uint4*>(Fc);
+                uint4* N4 = reinterpret_cast<uint4*>(Nc);
+                uint4* V4 = reinterpret_cast<uint4*>(V);
+                const uint4* A4 = reinterpret_cast<const uint4*>(act);
+                for (int t = tid; t < n * G4; t += kThreads) {
+                    const int v = t / G4;
+                    const int g = t - v * G4;
+                    const uint4 f0 = F4[t], v4 = V4[t], am = A4[g];
+                    const uint4 vis = make_uint4(v4.x | f0.x, v4.y | f0.y, v4.z | f0.z, v4.w | f0.w);
+                    const uint4 todo = make_uint4(am.x & ~vis.x, am.y & ~vis.y, am.z & ~vis.z, am.w & ~vis.w);
+                    uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+                    if (todo.x | todo.y | todo.z | todo.w) {
+                        const int e0 = __ldg(a.row_ptr + v0 + v), e1 = __ldg(a.row_ptr + v0 + v + 1);
+                        for (int e = e0; e < e1; e += 4) {
+                            int u[4];
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) u[q] = e + q < e1 ? __ldg(a.col + e + q) - v0 : -1;
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (u[q] >= 0) {
+                                    const uint4 x = F4[u[q] * G4 + g];
+                                    acc.x |= x.x;
+                                    acc.y |= x.y;
+                                    acc.z |= x.z;
+                                    acc.w |= x.w;
+                                }
+                            if (((acc.x & todo.x) == todo.x) && ((acc.y & todo.y) == todo.y) &&
+                                ((acc.z & todo.z) == todo.z) && ((acc.w & todo.w) == todo.w))
+                                break;
+                        }
+                        acc = make_uint4(acc.x & todo.x, acc.y & todo.y, acc.z & todo.z, acc.w & todo.w);
+                    }
+                    N4[t] = acc;
+                    V4[t] = vis;
+                    any |= (acc.x | acc.y | acc.z | acc.w) != 0u;
+                }
+            } else
             for (int t = tid; t < nW; t += kThreads) {
                 const int v = t / W;
                 const int w = t - v * W;

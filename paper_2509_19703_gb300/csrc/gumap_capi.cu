@@ -109,9 +109,10 @@ int32_t gumap::plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const
                 if (4ull * (2ull * ng * w + 34ull * w) <= kBatchSmemBudget) W = w;
         }
         if (!W) return g;
+        if (W >= 4) W &= ~3;  // rows of 128-bit groups (16-byte aligned) for the batched pull
         const size_t need = 4ull * ((vg ? 2ull : 3ull) * ng * W + 34ull * W);
         smem = std::max(smem, need);
-        if (vg) slab = std::max<long long>(slab, (long long)ng * W);
+        if (vg) slab = std::max<long long>(slab, ((long long)ng * W + 3) & ~3ll);
         const long long edges = graph_edges[g];
         for (int32_t s = 0; s < ng; s += 32 * W) {
             BatchUnit u{};
