@@ -89,6 +89,46 @@ def library_path() -> str:
     return _build.LIB
 
 
+def _signatures() -> dict:
+    """ctypes argument and result types of every entry point of include/gumap.h."""
+    vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+    sig = {
+        "gumap_knn_create": [ctypes.POINTER(vp), vp, vp, i32, i64, i32, ctypes.c_int, u32, ctypes.c_int],
+        "gumap_knn_run": [vp, vp, i32, vp, vp, vp, vp],
+        "gumap_knn_apsp": [vp, vp, i32, vp, vp, vp, vp],
+        "gumap_knn_rho_sigma": [vp, vp, vp, vp],
+        "gumap_knn_coo": [vp, vp, vp, vp, vp, vp],
+        "gumap_knn_check": [vp, vp],
+        "gumap_knn_set_option": [vp, ctypes.c_int, i64],
+        "gumap_knn_get_stats": [vp, ctypes.POINTER(_Stats)],
+        "gumap_knn_reset_stats": [vp],
+        "gumap_knn_destroy": [vp],
+        "gumap_knn_run_noalloc": [vp, vp, i32, i64, i32, ctypes.c_int, vp, vp, vp, vp],
+        "gumap_batch_create": [ctypes.POINTER(vp), i32, vp, vp, vp, i64, i32, vp, u32, ctypes.c_int],
+        "gumap_server_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_uint64,
+                                ctypes.POINTER(_ServerOpts)],
+        "gumap_serve_submit": [vp, vp, vp, i32, i64, i32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
+        "gumap_serve_poll": [vp, ctypes.c_uint64, ctypes.POINTER(_Result)],
+        "gumap_serve_wait": [vp, ctypes.c_uint64, ctypes.POINTER(_Result), ctypes.c_double],
+        "gumap_serve_read": [vp, ctypes.c_uint64, vp, vp, vp, vp],
+        "gumap_serve_release": [vp, ctypes.c_uint64],
+        "gumap_server_get_stats": [vp, ctypes.POINTER(_ServerStats)],
+        "gumap_server_destroy": [vp],
+        "gumap_knn_get_info": [vp, ctypes.POINTER(_Info)],
+        "gumap_knn_autotune": [vp, ctypes.c_char_p, ctypes.POINTER(_Tune)],
+    }
+    out = {name: (args, ctypes.c_int) for name, args in sig.items()}
+    out.update({
+        "gumap_status_string": ([ctypes.c_int], ctypes.c_char_p),
+        "gumap_last_error": ([], ctypes.c_char_p),
+        "gumap_server_clock": ([vp], ctypes.c_double),
+        "gumap_selftest_wait_timeout": ([ctypes.c_int, ctypes.c_double], ctypes.c_int),
+        "gumap_pool_trim": ([ctypes.c_int], ctypes.c_int),
+        "gumap_pool_cached_bytes": ([], ctypes.c_int64),
+    })
+    return out
+
+
 def load():
     """Load libgumap.so (built by ``__graft_entry__.build()``); raises if absent."""
     global _lib
@@ -99,48 +139,10 @@ def load():
                 raise RuntimeError(f"libgumap.so not built at {path}: run __graft_entry__.build() "
                                    "(there is no CPU fallback)")
             lib = ctypes.CDLL(path)
-            vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
-            sig = {
-                "gumap_knn_create": [ctypes.POINTER(vp), vp, vp, i32, i64, i32, ctypes.c_int, u32, ctypes.c_int],
-                "gumap_knn_run": [vp, vp, i32, vp, vp, vp, vp],
-                "gumap_knn_apsp": [vp, vp, i32, vp, vp, vp, vp],
-                "gumap_knn_rho_sigma": [vp, vp, vp, vp],
-                "gumap_knn_coo": [vp, vp, vp, vp, vp, vp],
-                "gumap_knn_check": [vp, vp],
-                "gumap_knn_set_option": [vp, ctypes.c_int, i64],
-                "gumap_knn_get_stats": [vp, ctypes.POINTER(_Stats)],
-                "gumap_knn_reset_stats": [vp],
-                "gumap_knn_destroy": [vp],
-                "gumap_knn_run_noalloc": [vp, vp, i32, i64, i32, ctypes.c_int, vp, vp, vp, vp],
-                "gumap_batch_create": [ctypes.POINTER(vp), i32, vp, vp, vp, i64, i32, vp, u32, ctypes.c_int],
-                "gumap_server_create": [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_uint64,
-                                        ctypes.POINTER(_ServerOpts)],
-                "gumap_serve_submit": [vp, vp, vp, i32, i64, i32, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)],
-                "gumap_serve_poll": [vp, ctypes.c_uint64, ctypes.POINTER(_Result)],
-                "gumap_serve_wait": [vp, ctypes.c_uint64, ctypes.POINTER(_Result), ctypes.c_double],
-                "gumap_serve_read": [vp, ctypes.c_uint64, vp, vp, vp, vp],
-                "gumap_serve_release": [vp, ctypes.c_uint64],
-                "gumap_server_get_stats": [vp, ctypes.POINTER(_ServerStats)],
-                "gumap_server_destroy": [vp],
-                "gumap_knn_get_info": [vp, ctypes.POINTER(_Info)],
-                "gumap_knn_autotune": [vp, ctypes.c_char_p, ctypes.POINTER(_Tune)],
-            }
-            for name, args in sig.items():
+            for name, (args, res) in _signatures().items():
                 f = getattr(lib, name)
                 f.argtypes = args
-                f.restype = ctypes.c_int
-            lib.gumap_status_string.argtypes = [ctypes.c_int]
-            lib.gumap_status_string.restype = ctypes.c_char_p
-            lib.gumap_last_error.argtypes = []
-            lib.gumap_last_error.restype = ctypes.c_char_p
-            lib.gumap_server_clock.argtypes = [vp]
-            lib.gumap_server_clock.restype = ctypes.c_double
-            lib.gumap_selftest_wait_timeout.argtypes = [ctypes.c_int, ctypes.c_double]
-            lib.gumap_selftest_wait_timeout.restype = ctypes.c_int
-            lib.gumap_pool_trim.argtypes = [ctypes.c_int]
-            lib.gumap_pool_trim.restype = ctypes.c_int
-            lib.gumap_pool_cached_bytes.argtypes = []
-            lib.gumap_pool_cached_bytes.restype = ctypes.c_int64
+                f.restype = res
             _lib = lib
     return _lib
 

@@ -41,6 +41,59 @@ def test_library_exports_every_declared_symbol(lib_path):
     assert not missing, f"declared but not exported: {missing}"
 
 
+def declared_arities():
+    """Entry point -> number of parameters, from the declarations of include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"\b(gumap_\w+)\s*\(([^;{()]*)\)\s*;", text):
+            params = m.group(2).strip()
+            out[m.group(1)] = 0 if params in ("", "void") else len(params.split(","))
+    return out
+
+
+def test_binding_matches_the_header():
+    """The ctypes binding knows every declared entry point, with as many
+    arguments as the header declares (no load, no GPU)."""
+    from paper_2509_19703_gb300 import gumap
+
+    sigs = gumap._signatures()
+    decl = declared_arities()
+    assert set(decl) == set(sigs), (sorted(set(decl) - set(sigs)), sorted(set(sigs) - set(decl)))
+    wrong = {name: (n, len(sigs[name][0])) for name, n in decl.items() if len(sigs[name][0]) != n}
+    assert not wrong, wrong
+
+
+STRUCTS = {"_Stats": "gumap_knn_stats", "_Info": "gumap_knn_info", "_Tune": "gumap_tune_result",
+           "_ServerOpts": "gumap_server_opts", "_Result": "gumap_result", "_ServerStats": "gumap_server_stats"}
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes structure of the binding has the size and field offsets
+    of its C struct, as gcc lays it out from include/gumap.h."""
+    from paper_2509_19703_gb300 import gumap
+
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "gumap.h"', "int main(void) {"]
+    for py, c in STRUCTS.items():
+        lines.append(f'printf("{py} size %zu\\n", sizeof({c}));')
+        for field, _ in getattr(gumap, py)._fields_:
+            lines.append(f'printf("{py} {field} %zu\\n", offsetof({c}, {field}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        py, what, val = line.split()
+        got[(py, what)] = int(val)
+    for py in STRUCTS:
+        cls = getattr(gumap, py)
+        assert got[(py, "size")] == ctypes.sizeof(cls), py
+        for field, _ in cls._fields_:
+            assert got[(py, field)] == getattr(cls, field).offset, (py, field)
+
+
 def test_library_loads_and_answers_host_only_calls(lib_path):
     lib = ctypes.CDLL(lib_path)
     lib.gumap_status_string.restype = ctypes.c_char_p
