@@ -44,7 +44,7 @@ WORKLOAD = ("full-APSP GUMAP kNN + UMAP weights + fuzzy union + sorted COO, k=15
             "BA n=20000 m0=5 seed 1 and G(n=5000, p=0.1) seed 2")
 FLUSH_BYTES = 512 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "msbfs_kernel_traffic.json")
-KERNEL_SRCS = [os.path.join(ROOT, "paper_2509_19703_gb300", "csrc", f) for f in ("msbfs.cu", "gumap_internal.cuh")]
+KERNEL_SRCS = [os.path.join(ROOT, "paper_2509_19703_gb300", "csrc", "msbfs.cu")]
 
 
 def parse_args():
@@ -174,9 +174,9 @@ def measured_peak_gbs():
 
 
 def kernel_sha():
-    """sha256 of the MS-BFS kernel's code (its source and the header of its
-    argument structures) with comments and whitespace removed, so an edit of
-    a comment does not void a traffic record taken on the same code."""
+    """sha256 of the MS-BFS kernel's source with comments and whitespace
+    removed, so an edit of a comment does not void a traffic record taken on
+    the same code."""
     code = ""
     for path in KERNEL_SRCS:
         with open(path) as f:

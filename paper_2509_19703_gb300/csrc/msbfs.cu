@@ -9,34 +9,40 @@
 // A level is the pull step  N[v] = (OR_{u in adj(v)} F[u]) & act & ~S[v],
 // then S[v] |= N[v], which is one frontier expansion of the partial BFS of
 // Algorithm 4 and of the BFS behind Algorithm 1's all-pairs distances, run
-// for 32*W sources at once. The OR over neighbours stops as soon as every still-missing source
-// bit is covered (the bottom-up early exit), and a vertex already reached by
-// every active source costs no neighbour loads at all.
+// for 32*W sources at once. The OR over neighbours stops as soon as every
+// still-missing source bit is covered (the bottom-up early exit), and a
+// vertex already reached by every active source costs no neighbour loads.
+// Such a saturated item stays saturated (S only grows, act only shrinks):
+// after writing its N word 0 in both buffers it is skipped for good (one
+// state byte per item).
 //
 // Work of a level is the set of (vertex v, 128-bit group g) items. Items of
 // vertices of ordinary degree are one thread each (the neighbour loop is
 // short). Items of vertices whose degree is far above the mean (hubs of
 // scale-free graphs) are one warp each, the lanes splitting the neighbour
 // list and OR-reducing with shuffles, so no level waits on one thread
-// walking a hub's adjacency. Both lists run in decreasing degree, so the
-// longest items start first and the short ones fill the tail before the
-// grid barrier.
+// walking a hub's adjacency. Both lists run in decreasing degree. In the
+// staged build each CTA owns an interleaved slice of the ordinary vertices,
+// whose neighbour ids it bulk-copies (cp.async.bulk, completion on an
+// mbarrier) into shared memory once per launch.
 //
 // Level 1 of a block of consecutive sources (every run over all vertices)
 // is a pull from the sorted rows that writes N and S in full; for an
 // explicit source list it is a push from the sources' rows into N only, and
-// level 2 folds the level-1 frontier into S (one stream instead of an atomic
-// per edge). Its kNN entries are the first k entries of each source's sorted
-// CSR row.
-// For later levels the extraction phase scans each word column of N in
-// vertex order, transposes 32x32 bit tiles with warp ballots, and appends
-// to every incomplete source the vertices it reached at this level in
-// ascending id until its list holds k entries: this is exactly the
-// (distance, id) order, because levels are visited in increasing distance
-// and vertices in increasing id. In the partial form (Algorithm 4, which
-// stops a source once more than k vertices are visited) a source whose list
-// is complete stops propagating: its bit leaves `act`. The full form keeps every source
-// propagating until no source reaches a new vertex.
+// level 2 folds the level-1 frontier into S. Its kNN entries are the first
+// k entries of each source's sorted CSR row. For later levels the
+// extraction scans each word column of N in vertex order, transposes 32x32
+// bit tiles with warp ballots, and appends to every incomplete source the
+// vertices it reached at this level in ascending id until its list holds k
+// entries: this is exactly the (distance, id) order, because levels are
+// visited in increasing distance and vertices in increasing id. It runs in
+// the same phase as the next level's pull, which only reads the same
+// buffer. When all-pairs rows are requested every column is scanned and
+// each newly reached (source, vertex) pair gets its distance. In the
+// partial form (Algorithm 4, which stops a source once more than k
+// vertices are visited) a source whose list is complete stops propagating:
+// its bit leaves `act`. The full form keeps every source propagating until
+// no source reaches a new vertex.
 //
 // All levels run inside one cooperative launch; phases are separated by a
 // grid barrier whose waits are bounded in time (kWaitLimitNs).
