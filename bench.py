@@ -58,9 +58,10 @@ def parse_args():
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample budget")
     p.add_argument("--only", choices=["ba20k", "er5k"], default=None,
                    help="run one of the two graphs (for profiler captures; not a bench line)")
-    p.add_argument("--workload", choices=["config2", "batch", "serve"], default="config2",
-                   help="config2: the headline line; batch: the 2000-graph batching comparison; "
-                        "serve: the request-stream latency sweep")
+    p.add_argument("--workload", choices=["config2", "partial", "batch", "serve"], default="config2",
+                   help="config2: the headline line; partial: the partial form on the 1,000,000-vertex "
+                        "graphs; batch: the 2000-graph batching comparison; serve: the request-stream "
+                        "latency sweep")
     p.add_argument("--batch-graphs", type=int, default=2000)
     p.add_argument("--serve-requests", type=int, default=1000)
     p.add_argument("--serve-n-cap", type=int, default=200000)
@@ -209,6 +210,39 @@ def msbfs_alg_bytes(g, block_bits, level_sum, launches):
     W = block_bits // 32
     per_level = 12 * g.n * W + 4 * (g.n + 1) + 4 * g.nnz
     return level_sum * per_level + launches * 8 * g.n * W
+
+
+def partial_work(g, idx, dist):
+    """Traversal work of the partial form per source, from its kNN list:
+    (adjacency entries scanned, rows expanded). The expanded vertices are the
+    source and every vertex closer than D_s, the distance of the list's last
+    entry: fewer than k vertices lie closer than D_s, so all of them are in
+    the list. A padded list (the component ran out) expands its whole
+    component. Sources are 0..n-1 in row order."""
+    import numpy as np
+    deg = np.diff(g.row_ptr).astype(np.int64)
+    d = np.asarray(dist).view(np.uint16) if np.asarray(dist).dtype == np.int16 else np.asarray(dist)
+    idx = np.asarray(idx)
+    inner = (d < d[:, -1:]) & (idx >= 0)
+    listed = np.where(inner, deg[np.where(idx >= 0, idx, 0)], 0).sum(axis=1)
+    return deg[: idx.shape[0]] + listed, 1 + inner.sum(axis=1).astype(np.int64)
+
+
+def frontier_alg_bytes(entries, rows, k):
+    """Algorithmic bytes of one frontier-engine launch (partial form, one warp
+    per source): per expanded row its two row_ptr words and its adjacency
+    (4 bytes per entry), per source the k ids and distances written (6 k)."""
+    return int(8 * int(rows.sum()) + 4 * int(entries.sum()) + 6 * k * len(rows))
+
+
+def sort_alg_bytes(n, k):
+    """Algorithmic bytes of one COO sort (gumap_knn_run with union weights):
+    2 n k (key, value) pairs of 12 bytes; one read of the keys for the digit
+    counts of every pass, then per 8-bit pass one read and one write of the
+    pairs. The key has 2 ceil(log2 n) bits."""
+    bits = max(1, (max(n, 2) - 1).bit_length())
+    passes = (2 * bits + 7) // 8
+    return 2 * n * k * (8 + 24 * passes)
 
 
 def cpu_cores():
@@ -478,6 +512,161 @@ def run_batch_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def run_partial_workload(args):
+    """Partial form (SL-GUMAP, Algorithm 4) on the two 1,000,000-vertex
+    graphs at k = 15 and k = 50: one step runs gumap_knn_run (kNN lists,
+    weights, union, sorted COO, all sources) for each (graph, k). Work per
+    source: the adjacency entries of the vertices it expands (closer than
+    the distance of its k-th neighbour) / 2, counted from the lists.
+    Prints its own JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_2509_19703_gb300 import graphgen as gg
+    from paper_2509_19703_gb300 import gumap
+
+    torch.cuda.set_device(0)
+    graphs = [gg.config_ba1m(), gg.config_grid1m()]
+    runs = [(g, k) for g in graphs for k in (15, 50)]
+    kgs = [gumap.KnnGraph.from_graph(g, k, mode=gumap.PARTIAL) for g, k in runs]
+    tuned = [kg.autotune() for kg in kgs]
+    for kg in kgs:
+        kg.set_option(gumap.OPT_PROFILE, 1)
+    outs = [kg.alloc_outputs(g.n) for kg, (g, _) in zip(kgs, runs)]
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for kg, o in zip(kgs, outs):
+            kg.run(out=o)
+    for kg in kgs:
+        kg.check()
+        kg.reset_stats()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for s in range(args.steps):
+        flush.fill_(s & 0xFF)
+        torch.cuda.nvtx.range_push("timed_step")
+        ev[s][0].record(stream)
+        for kg, o in zip(kgs, outs):
+            kg.run(out=o)
+        ev[s][1].record(stream)
+        torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    for kg in kgs:
+        kg.check()
+    stats = [kg.stats() for kg in kgs]
+
+    # work and algorithmic bytes from the lists (identical every step)
+    per_run = []
+    for (g, k), o, st in zip(runs, outs, stats):
+        entries, rows = partial_work(g, o["idx"].cpu().numpy(), gumap.dist_u16(o["dist"]))
+        engine_bytes = (frontier_alg_bytes(entries, rows, k) if st["engine"] == gumap.ENGINE_FRONTIER
+                        else msbfs_alg_bytes(g, st["block_bits"], st["bfs_level_sum"] // args.steps,
+                                             st["bfs_launches"] // args.steps))
+        per_run.append({"graph": g.name, "n": g.n, "m": g.m, "k": k, "engine": st["engine"],
+                        "work_edges": int(entries.sum()) // 2, "entries": entries, "rows": rows,
+                        "engine_alg_bytes": engine_bytes, "sort_alg_bytes": sort_alg_bytes(g.n, k),
+                        "engine_ms": st["bfs_ms"] / args.steps, "weights_ms": st["weights_ms"] / args.steps,
+                        "sort_ms": st["sort_ms"] / args.steps,
+                        "engine_launches": st["bfs_launches"] // args.steps,
+                        "sort_launches": st["sort_launches"] // args.steps})
+    work_per_step = sum(r["work_edges"] for r in per_run)
+    value = work_per_step / (ms * 1e-3) / 1e9
+    stage_ms = {key: sum(r[key] for r in per_run) for key in ("engine_ms", "weights_ms", "sort_ms")}
+
+    # roofline of the kernel that takes the largest share of the step
+    peak, peak_kind = measured_peak_gbs()
+    if stage_ms["sort_ms"] > stage_ms["engine_ms"]:
+        kernel, t_ms = "COO sort (hist_all_kernel + onesweep_kernel)", stage_ms["sort_ms"]
+        alg = sum(r["sort_alg_bytes"] for r in per_run)
+        launches = sum(r["sort_launches"] for r in per_run)
+    else:
+        kernel, t_ms = "BFS engine (frontier_kernel)", stage_ms["engine_ms"]
+        alg = sum(r["engine_alg_bytes"] for r in per_run)
+        launches = sum(r["engine_launches"] for r in per_run)
+    achieved = alg / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if peak else None, "traffic": None, "peak_source": peak_kind,
+                "kernel": kernel, "launches_per_step": launches, "alg_bytes_per_step": alg,
+                "kernel_share_of_step": t_ms / ms if ms else None,
+                "stage_ms_per_step": stage_ms}
+    gpu_launches = sum(st["kernel_launches"] for st in stats)
+
+    e2e = None
+    if args.e2e_steps > 0:
+        pinned = {}
+        for g in graphs:
+            pinned[g.name] = (torch.from_numpy(g.row_ptr).pin_memory(), torch.from_numpy(g.col).pin_memory())
+        host_out = [dict(idx=torch.empty((g.n, k), dtype=torch.int32).pin_memory(),
+                         dist=torch.empty((g.n, k), dtype=torch.int16).pin_memory(),
+                         w=torch.empty((g.n, k), dtype=torch.float32).pin_memory()) for g, k in runs]
+        h2d = sum(pinned[g.name][0].numel() * 4 + pinned[g.name][1].numel() * 4 for g, _ in runs)
+        d2h = sum(o[key].numel() * o[key].element_size() for o in host_out for key in o)
+        times = []
+        for s in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for (g, k), ho, o in zip(runs, host_out, outs):
+                rp, col = pinned[g.name]
+                drp = rp.to("cuda", non_blocking=True)
+                dcol = col.to("cuda", non_blocking=True)
+                h = gumap.gumap_knn_create(drp, dcol, g.n, g.nnz, k, gumap.PARTIAL, gumap.CSR_ON_DEVICE)
+                gumap.gumap_knn_run(h, None, g.n, o["idx"], o["dist"], o["w"])
+                for key in ("idx", "dist", "w"):
+                    ho[key].copy_(o[key], non_blocking=True)
+                torch.cuda.synchronize()
+                gumap.gumap_knn_destroy(h)
+            if s > 0:
+                times.append(time.perf_counter() - t0)
+        e2e_t = statistics.median(times)
+        e2e = {"value": work_per_step / e2e_t / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t * 1e3, "timing": "wall clock, median"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        total_work, total_t, parts = 0, 0.0, []
+        for r, (g, k) in zip(per_run, runs):
+            order = np.random.default_rng(1234).permutation(g.n).astype(np.int32)
+            done, t0 = 0, time.perf_counter()
+            while done < g.n and time.perf_counter() - t0 < args.cpu_seconds / len(runs):
+                src = order[done:done + 4096]
+                _, dist, work = oracle.knn_partial(g, k, sources=src, return_work=True)
+                oracle.smooth_knn(dist)
+                if not np.array_equal(work, r["entries"][src]):
+                    raise RuntimeError(f"{g.name} k={k}: work counted from the lists differs from the oracle's")
+                total_work += int(work.sum())
+                done += len(src)
+            total_t += time.perf_counter() - t0
+            parts.append(f"{done} of {g.n} sources of {g.name} at k={k}")
+        cpu = {"value": total_work / 2 / total_t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": "; ".join(parts) + " (seeded random order, partial BFS + FP64 weights, 1 thread)"}
+
+    for r in per_run:
+        r.pop("entries")
+        r.pop("rows")
+    line = {"metric": "BFS-kNN GTEPS (partial form, k=15 and 50) and % of HBM peak", "value": value,
+            "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32 ids / u16 distances / f32 weights", "data": "synthetic",
+            "config": {"workload": "partial-BFS SL-GUMAP kNN + UMAP weights + fuzzy union + sorted COO, all "
+                                   "sources, k=15 and k=50, on BA n=1000000 m0=4 seed 3 and the 1000x1000 grid",
+                       "work_edges_per_step": work_per_step, "runs": per_run,
+                       "l2": "flushed (512 MB write) before each timed step",
+                       "autotuned": [{key: t[key] for key in ("engine", "state_bytes", "best_ms", "default_ms")}
+                                     for t in tuned]},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    for kg in kgs:
+        kg.close()
+
+
 def serve_requests(count, seed, n_cap):
     """Config 5 request stream: n lognormal (median 5000, sigma_ln 1.0) clamped
     to [64, n_cap]; BA (4 edges per vertex) / grid / G(n, p) (mean degree 10)
@@ -589,6 +778,8 @@ def main():
     args = parse_args()
     if args.workload == "serve":
         run_serve_workload(args)
+    elif args.workload == "partial":
+        run_partial_workload(args)
     elif args.workload == "batch":
         run_batch_workload(args)
     elif args.impl == "reference":

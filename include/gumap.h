@@ -83,7 +83,7 @@ extern "C" {
 /* --------------------------------------------------------------- options */
 #define GUMAP_OPT_ENGINE      1 /* value: GUMAP_ENGINE_*                                 */
 #define GUMAP_OPT_BLOCK_BITS  2 /* value: sources per MS-BFS block (multiple of 128), 0 = auto */
-#define GUMAP_OPT_PROFILE     3 /* value: 1 = time each BFS launch with CUDA events       */
+#define GUMAP_OPT_PROFILE     3 /* value: 1 = time each BFS launch, the weights and the COO sort with CUDA events */
 #define GUMAP_OPT_STATE_BYTES 4 /* value: device bytes allowed for MS-BFS bitsets, 0 = auto */
 #define GUMAP_OPT_HEAVY_DEGREE 5 /* value: MS-BFS vertices of larger degree are processed by a whole warp
                                     (default max(64, 4 x mean degree)); setting it synchronises the device */
@@ -252,6 +252,9 @@ typedef struct {
     double  bfs_push_ms;     /* MS-BFS device time in push levels (queue preparation + push) */
     int64_t bfs_push_levels; /* MS-BFS levels run as a push since the last reset */
     int64_t bfs_staged_launches; /* MS-BFS launches whose rows were staged in shared memory */
+    double  weights_ms;      /* device time of rho/sigma, weights, union and COO keys (GUMAP_OPT_PROFILE on), ms */
+    double  sort_ms;         /* device time of the COO sort: clearing, digit counts, passes (GUMAP_OPT_PROFILE on), ms */
+    int64_t sort_launches;   /* COO sort kernel launches since the last reset */
 } gumap_knn_stats;
 
 typedef struct {

@@ -229,8 +229,12 @@ struct gumap_knn {
     int64_t bfs_launches = 0;
     int64_t kernel_launches = 0;
     std::vector<cudaEvent_t> ev_pool;  // pairs
+    std::vector<int> ev_stage;         // per pair: what it brackets (kStage*)
     size_t ev_used = 0;
     double bfs_ms_done = 0.0;
+    double weights_ms_done = 0.0;
+    double sort_ms_done = 0.0;
+    int64_t sort_launches = 0;
 };
 
 namespace {
@@ -292,16 +296,23 @@ int pick_engine(const gumap_knn* h) {
     return h->mode == GUMAP_PARTIAL ? GUMAP_ENGINE_FRONTIER : GUMAP_ENGINE_MSBFS;
 }
 
-int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b) {
+// What a profiling event pair brackets (GUMAP_OPT_PROFILE).
+constexpr int kStageBfs = 0;      // one BFS engine launch
+constexpr int kStageWeights = 1;  // rho/sigma and weights, union and COO keys
+constexpr int kStageSort = 2;     // the COO sort (clearing, digit counts, passes)
+
+int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b, int stage = kStageBfs) {
     if (h->ev_used + 2 > h->ev_pool.size()) {
         for (int i = 0; i < 2; ++i) {
             cudaEvent_t e;
             CK(cudaEventCreate(&e), "cudaEventCreate");
             h->ev_pool.push_back(e);
         }
+        h->ev_stage.push_back(kStageBfs);
     }
     *a = h->ev_pool[h->ev_used];
     *b = h->ev_pool[h->ev_used + 1];
+    h->ev_stage[h->ev_used / 2] = stage;
     h->ev_used += 2;
     return GUMAP_OK;
 }
@@ -849,6 +860,11 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
 
     const float T = (float)std::log2((double)k);
     float* a_dst = want_union ? static_cast<float*>(h->a.p) : out_w;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->opt_profile) {
+        if ((rc = next_event_pair(h, &e0, &e1, kStageWeights))) return rc;
+        CK(cudaEventRecord(e0, st), "cudaEventRecord");
+    }
     CK(launch_smooth_knn(out_dist, n_src, k, T, static_cast<float*>(h->rho.p), static_cast<float*>(h->sigma.p), a_dst, st),
        "smooth_knn");
     h->kernel_launches++;
@@ -864,6 +880,11 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
                         static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), h->d_ctr, st),
            "union");
         h->kernel_launches++;
+        if (h->opt_profile) {
+            CK(cudaEventRecord(e1, st), "cudaEventRecord");
+            if ((rc = next_event_pair(h, &e0, &e1, kStageSort))) return rc;
+            CK(cudaEventRecord(e0, st), "cudaEventRecord");
+        }
         int launches = 0;
         CK(radix_sort_pairs(static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
                             static_cast<unsigned long long*>(h->keys_tmp.p), static_cast<float*>(h->vals_tmp.p), cnt,
@@ -871,9 +892,11 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
                             &h->coo_vals, &launches),
            "radix sort");
         h->kernel_launches += launches;
+        h->sort_launches += launches;
         h->coo_key_bits = B;
         h->last_union = true;
     }
+    if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
     return GUMAP_OK;
 }
 
@@ -1035,7 +1058,9 @@ int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
     CK(cudaMemcpy(&c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
     for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
         float ms = 0.0f;
-        if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) == cudaSuccess) h->bfs_ms_done += ms;
+        if (cudaEventElapsedTime(&ms, h->ev_pool[i], h->ev_pool[i + 1]) != cudaSuccess) continue;
+        const int stage = h->ev_stage[i / 2];
+        (stage == kStageSort ? h->sort_ms_done : stage == kStageWeights ? h->weights_ms_done : h->bfs_ms_done) += ms;
     }
     h->ev_used = 0;
     memset(out, 0, sizeof(*out));
@@ -1054,6 +1079,9 @@ int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
     out->bfs_push_ms = (double)c.t_push_ns * 1e-6;
     out->bfs_push_levels = c.push_levels;
     out->bfs_staged_launches = h->staged_launches;
+    out->weights_ms = h->weights_ms_done;
+    out->sort_ms = h->sort_ms_done;
+    out->sort_launches = h->sort_launches;
     return GUMAP_OK;
 }
 
@@ -1065,6 +1093,9 @@ int gumap_knn_reset_stats(gumap_knn* h) {
     h->kernel_launches = 0;
     h->staged_launches = 0;
     h->bfs_ms_done = 0.0;
+    h->weights_ms_done = 0.0;
+    h->sort_ms_done = 0.0;
+    h->sort_launches = 0;
     h->ev_used = 0;
     DeviceCounters c;
     CK(cudaMemcpy(&c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");

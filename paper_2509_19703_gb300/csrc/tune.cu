@@ -204,12 +204,18 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
         Setting f;
         f.engine = GUMAP_ENGINE_FRONTIER;
         cands.push_back(f);
-        for (long long budget : {96ll << 20, 256ll << 20}) {
-            Setting s;
-            s.engine = GUMAP_ENGINE_MSBFS;
-            s.state_bytes = budget;
-            cands.push_back(s);
-        }
+        // The MS-BFS engine sweeps the bitsets of all n vertices at every
+        // level of every source block: at least 3 n^2 / 8 bytes per level
+        // over all blocks. Beyond 64 GB of that (n above about 400,000) one
+        // timing run would take seconds against the frontier engine's
+        // milliseconds, so it is not a candidate there.
+        if (3.0 * (double)in.n * (double)in.n / 8.0 <= 64e9)
+            for (long long budget : {96ll << 20, 256ll << 20}) {
+                Setting s;
+                s.engine = GUMAP_ENGINE_MSBFS;
+                s.state_bytes = budget;
+                cands.push_back(s);
+            }
     }
     double default_ms = 0.0;
     if ((rc = time_run(&default_ms))) {

@@ -50,7 +50,8 @@ class _Stats(ctypes.Structure):
                 ("device_bytes", ctypes.c_int64), ("bfs_init_ms", ctypes.c_double),
                 ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double),
                 ("bfs_push_ms", ctypes.c_double), ("bfs_push_levels", ctypes.c_int64),
-                ("bfs_staged_launches", ctypes.c_int64)]
+                ("bfs_staged_launches", ctypes.c_int64), ("weights_ms", ctypes.c_double),
+                ("sort_ms", ctypes.c_double), ("sort_launches", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
