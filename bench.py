@@ -235,14 +235,13 @@ def frontier_alg_bytes(entries, rows, k):
     return int(8 * int(rows.sum()) + 4 * int(entries.sum()) + 6 * k * len(rows))
 
 
-def sort_alg_bytes(n, k):
-    """Algorithmic bytes of one COO sort (gumap_knn_run with union weights):
-    2 n k (key, value) pairs of 12 bytes; one read of the keys for the digit
-    counts of every pass, then per 8-bit pass one read and one write of the
-    pairs. The key has 2 ceil(log2 n) bits."""
-    bits = max(1, (max(n, 2) - 1).bit_length())
-    passes = (2 * bits + 7) // 8
-    return 2 * n * k * (8 + 24 * passes)
+def coo_alg_bytes(n, k, nnz):
+    """Algorithmic bytes of one COO build (gumap_knn_run with union weights),
+    after the union kernel: the row scan reads the per-row counts and writes
+    the row offsets (16 n); the scatter reads each slot's id, weight and
+    mirror place (12 n k) and writes every entry's column and weight
+    (8 nnz); the row sorts read those and write the sorted rows (16 nnz)."""
+    return 16 * n + 12 * n * k + 24 * nnz
 
 
 def cpu_cores():
@@ -563,28 +562,29 @@ def run_partial_workload(args):
 
     # work and algorithmic bytes from the lists (identical every step)
     per_run = []
-    for (g, k), o, st in zip(runs, outs, stats):
+    for (g, k), o, st, kg in zip(runs, outs, stats, kgs):
         entries, rows = partial_work(g, o["idx"].cpu().numpy(), gumap.dist_u16(o["dist"]))
+        nnz = int(kg.coo()[0].numel())
         engine_bytes = (frontier_alg_bytes(entries, rows, k) if st["engine"] == gumap.ENGINE_FRONTIER
                         else msbfs_alg_bytes(g, st["block_bits"], st["bfs_level_sum"] // args.steps,
                                              st["bfs_launches"] // args.steps))
         per_run.append({"graph": g.name, "n": g.n, "m": g.m, "k": k, "engine": st["engine"],
                         "work_edges": int(entries.sum()) // 2, "entries": entries, "rows": rows,
-                        "engine_alg_bytes": engine_bytes, "sort_alg_bytes": sort_alg_bytes(g.n, k),
+                        "coo_nnz": nnz, "engine_alg_bytes": engine_bytes, "coo_alg_bytes": coo_alg_bytes(g.n, k, nnz),
                         "engine_ms": st["bfs_ms"] / args.steps, "weights_ms": st["weights_ms"] / args.steps,
-                        "sort_ms": st["sort_ms"] / args.steps,
+                        "coo_ms": st["sort_ms"] / args.steps,
                         "engine_launches": st["bfs_launches"] // args.steps,
-                        "sort_launches": st["sort_launches"] // args.steps})
+                        "coo_launches": st["sort_launches"] // args.steps})
     work_per_step = sum(r["work_edges"] for r in per_run)
     value = work_per_step / (ms * 1e-3) / 1e9
-    stage_ms = {key: sum(r[key] for r in per_run) for key in ("engine_ms", "weights_ms", "sort_ms")}
+    stage_ms = {key: sum(r[key] for r in per_run) for key in ("engine_ms", "weights_ms", "coo_ms")}
 
     # roofline of the kernel that takes the largest share of the step
     peak, peak_kind = measured_peak_gbs()
-    if stage_ms["sort_ms"] > stage_ms["engine_ms"]:
-        kernel, t_ms = "COO sort (hist_all_kernel + onesweep_kernel)", stage_ms["sort_ms"]
-        alg = sum(r["sort_alg_bytes"] for r in per_run)
-        launches = sum(r["sort_launches"] for r in per_run)
+    if stage_ms["coo_ms"] > stage_ms["engine_ms"]:
+        kernel, t_ms = "COO build (row_scan + scatter + row sorts)", stage_ms["coo_ms"]
+        alg = sum(r["coo_alg_bytes"] for r in per_run)
+        launches = sum(r["coo_launches"] for r in per_run)
     else:
         kernel, t_ms = "BFS engine (frontier_kernel)", stage_ms["engine_ms"]
         alg = sum(r["engine_alg_bytes"] for r in per_run)

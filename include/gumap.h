@@ -83,7 +83,7 @@ extern "C" {
 /* --------------------------------------------------------------- options */
 #define GUMAP_OPT_ENGINE      1 /* value: GUMAP_ENGINE_*                                 */
 #define GUMAP_OPT_BLOCK_BITS  2 /* value: sources per MS-BFS block (multiple of 128), 0 = auto */
-#define GUMAP_OPT_PROFILE     3 /* value: 1 = time each BFS launch, the weights and the COO sort with CUDA events */
+#define GUMAP_OPT_PROFILE     3 /* value: 1 = time each BFS launch, the weights and the COO build with CUDA events */
 #define GUMAP_OPT_STATE_BYTES 4 /* value: device bytes allowed for MS-BFS bitsets, 0 = auto */
 #define GUMAP_OPT_HEAVY_DEGREE 5 /* value: MS-BFS vertices of larger degree are processed by a whole warp
                                     (default max(64, 4 x mean degree)); setting it synchronises the device */
@@ -95,6 +95,10 @@ extern "C" {
                                    for: 3 (default, up to 80 registers a thread) or 4 (64)        */
 #define GUMAP_OPT_BATCH_WIDTH 11 /* value: batch handles: widest unit in 32-bit words (32 sources each),
                                    1..64, 0 = 64 (default); re-plans the batch, synchronises      */
+#define GUMAP_OPT_COO_BUILD  12 /* value: how gumap_knn_run builds the union COO: 0 = automatic (default:
+                                   1 below 2^21 slots n x k, 2 from there on), 1 = LSD radix sort of
+                                   2 n k (row, col) keys, 2 = row by row (row counts, one scan,
+                                   scatter, each row ranked by column); same COO either way      */
 #define GUMAP_OPT_STAGE      10 /* value: 1 (default) = each MS-BFS CTA bulk-copies its slice of the
                                    ordinary-degree rows into shared memory once per launch when
                                    every slice fits; 0 = neighbour ids always read from the CSR;
@@ -252,9 +256,9 @@ typedef struct {
     double  bfs_push_ms;     /* MS-BFS device time in push levels (queue preparation + push) */
     int64_t bfs_push_levels; /* MS-BFS levels run as a push since the last reset */
     int64_t bfs_staged_launches; /* MS-BFS launches whose rows were staged in shared memory */
-    double  weights_ms;      /* device time of rho/sigma, weights, union and COO keys (GUMAP_OPT_PROFILE on), ms */
-    double  sort_ms;         /* device time of the COO sort: clearing, digit counts, passes (GUMAP_OPT_PROFILE on), ms */
-    int64_t sort_launches;   /* COO sort kernel launches since the last reset */
+    double  weights_ms;      /* device time of rho/sigma, weights and union (GUMAP_OPT_PROFILE on), ms */
+    double  sort_ms;         /* device time of the COO build, radix sort or rows (GUMAP_OPT_PROFILE on), ms */
+    int64_t sort_launches;   /* COO build kernel launches since the last reset */
 } gumap_knn_stats;
 
 typedef struct {

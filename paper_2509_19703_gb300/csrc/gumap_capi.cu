@@ -7,7 +7,9 @@
 //          writing the (distance, id)-ordered kNN rows into the caller's
 //          out_idx/out_dist;
 //   W      rho/sigma/a_ij (weights.cu) and, for union weights, the fuzzy
-//          union and the symmetric COO sorted by an LSD radix sort (sort.cu).
+//          union and the symmetric COO sorted by (row, col): an LSD radix sort
+//          of (row, col) keys (sort.cu) below 2^21 slots, built row by row
+//          (coo.cu) from there on.
 #include "gumap.h"
 #include "gumap_internal.cuh"
 
@@ -200,11 +202,14 @@ struct gumap_knn {
 
     // per-run scratch
     DevBuf rho, sigma, a;
-    DevBuf keys, vals, keys_tmp, vals_tmp, sort_temp;
+    DevBuf keys, vals, keys_tmp, vals_tmp, sort_temp;  // COO as radix-sorted (key, value) pairs
+    DevBuf coo_scr, coo_kval, coo_mpos, coo_rowoff, coo_large, coo_tcol, coo_tw, coo_col, coo_w;  // COO by rows
 
     // last run
     int32_t last_n_src = -1;
     bool last_union = false;
+    bool coo_rows = false;  // the last run's COO was built by rows (coo), else radix-sorted pairs
+    CooArgs coo{};
     unsigned long long* coo_keys = nullptr;
     float* coo_vals = nullptr;
     int coo_key_bits = 0;
@@ -224,6 +229,7 @@ struct gumap_knn {
     std::vector<int32_t> batch_offsets, batch_modes;  // the batch's graphs, kept to re-plan
     std::vector<int64_t> batch_edges;
     int32_t batch_width = 0;  // GUMAP_OPT_BATCH_WIDTH in force
+    int opt_coo_build = 0;    // GUMAP_OPT_COO_BUILD
 
     // stats
     int64_t bfs_launches = 0;
@@ -266,7 +272,9 @@ size_t held_bytes(const gumap_knn* h) {
     size_t t = (size_t)(h->n + 1) * 4 + (size_t)h->nnz * 4 + (size_t)h->n * 4 + sizeof(DeviceCounters);
     for (const auto& c : h->cuts) t += (size_t)(c.grid + 1) * 4 + c.meta_bytes + c.ocol_bytes;
     const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
-                          &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
+                          &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
+                          &h->coo_scr, &h->coo_kval, &h->coo_mpos, &h->coo_rowoff, &h->coo_large,
+                          &h->coo_tcol, &h->coo_tw, &h->coo_col, &h->coo_w};
     for (const DevBuf* b : bs) t += b->bytes;
     return t;
 }
@@ -298,8 +306,8 @@ int pick_engine(const gumap_knn* h) {
 
 // What a profiling event pair brackets (GUMAP_OPT_PROFILE).
 constexpr int kStageBfs = 0;      // one BFS engine launch
-constexpr int kStageWeights = 1;  // rho/sigma and weights, union and COO keys
-constexpr int kStageSort = 2;     // the COO sort (clearing, digit counts, passes)
+constexpr int kStageWeights = 1;  // rho/sigma and weights, union (with the COO row counts)
+constexpr int kStageSort = 2;     // the COO build: radix sort of the pairs, or row scan, scatter, row sorts
 
 int next_event_pair(gumap_knn* h, cudaEvent_t* a, cudaEvent_t* b, int stage = kStageBfs) {
     if (h->ev_used + 2 > h->ev_pool.size()) {
@@ -628,7 +636,9 @@ int gumap_knn_destroy(gumap_knn* h) {
     release(h->vslab);
     pool_free(h->d_ctr, sizeof(DeviceCounters));
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
-                    &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp};
+                    &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
+                    &h->coo_scr, &h->coo_kval, &h->coo_mpos, &h->coo_rowoff, &h->coo_large,
+                    &h->coo_tcol, &h->coo_tw, &h->coo_col, &h->coo_w};
     for (DevBuf* b : bs) release(*b);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -868,7 +878,9 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
     CK(launch_smooth_knn(out_dist, n_src, k, T, static_cast<float*>(h->rho.p), static_cast<float*>(h->sigma.p), a_dst, st),
        "smooth_knn");
     h->kernel_launches++;
-    if (want_union) {
+    const bool coo_by_rows =
+        h->opt_coo_build == 2 || (h->opt_coo_build == 0 && (long long)slots >= kCooRowsMinSlots);
+    if (want_union && !coo_by_rows) {
         const long long cnt = 2ll * n_src * k;
         const int B = key_bits_for(h->n);
         if ((rc = ensure(h->keys, cnt * 8, "coo keys")) || (rc = ensure(h->vals, cnt * 4, "coo vals")) ||
@@ -876,8 +888,9 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
             (rc = ensure(h->sort_temp, radix_sort_temp_bytes(cnt, 2 * B), "sort temp")))
             return rc;
         CK(cudaMemsetAsync(&h->d_ctr->coo_nnz, 0, sizeof(unsigned long long), st), "memset nnz");
-        CK(launch_union(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, B,
-                        static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), h->d_ctr, st),
+        CK(launch_union_pairs(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, B,
+                              static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), h->d_ctr,
+                              st),
            "union");
         h->kernel_launches++;
         if (h->opt_profile) {
@@ -894,6 +907,54 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
         h->kernel_launches += launches;
         h->sort_launches += launches;
         h->coo_key_bits = B;
+        h->coo_rows = false;
+        h->last_union = true;
+    } else if (want_union) {
+        const size_t slots2 = 2 * slots;
+        if ((rc = ensure(h->coo_scr, coo_scratch_bytes(n_src), "coo scratch")) ||
+            (rc = ensure(h->coo_kval, (size_t)n_src * 4, "coo kval")) ||
+            (rc = ensure(h->coo_mpos, slots * 4, "coo mpos")) ||
+            (rc = ensure(h->coo_rowoff, ((size_t)n_src + 1) * 8, "coo rowoff")) ||
+            (rc = ensure(h->coo_large, (size_t)n_src * 4, "coo long rows")) ||
+            (rc = ensure(h->coo_tcol, slots2 * 4, "coo scattered cols")) ||
+            (rc = ensure(h->coo_tw, slots2 * 4, "coo scattered weights")) ||
+            (rc = ensure(h->coo_col, slots2 * 4, "coo cols")) || (rc = ensure(h->coo_w, slots2 * 4, "coo weights")))
+            return rc;
+        LaunchLimits lim;
+        if ((rc = launch_limits(h->device, lim))) return rc;
+        CooArgs c{};
+        uint32_t* mcnt = nullptr;
+        coo_scratch_split(h->coo_scr.p, n_src, &mcnt, &c.ctr, &c.pub);
+        c.idx = out_idx;
+        c.w = out_w;
+        c.mpos = static_cast<uint32_t*>(h->coo_mpos.p);
+        c.kval = static_cast<int32_t*>(h->coo_kval.p);
+        c.mcnt = mcnt;
+        c.n = n_src;
+        c.k = k;
+        c.rowoff = static_cast<unsigned long long*>(h->coo_rowoff.p);
+        c.large = static_cast<int32_t*>(h->coo_large.p);
+        c.tcol = static_cast<int32_t*>(h->coo_tcol.p);
+        c.tw = static_cast<float*>(h->coo_tw.p);
+        c.ccol = static_cast<int32_t*>(h->coo_col.p);
+        c.cw = static_cast<float*>(h->coo_w.p);
+        c.status = &h->d_ctr->status;
+        CK(cudaMemsetAsync(h->coo_scr.p, 0, coo_scratch_bytes(n_src), st), "memset coo scratch");
+        CK(launch_union(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, mcnt,
+                        static_cast<uint32_t*>(h->coo_mpos.p), static_cast<int32_t*>(h->coo_kval.p), st),
+           "union");
+        h->kernel_launches++;
+        if (h->opt_profile) {
+            CK(cudaEventRecord(e1, st), "cudaEventRecord");
+            if ((rc = next_event_pair(h, &e0, &e1, kStageSort))) return rc;
+            CK(cudaEventRecord(e0, st), "cudaEventRecord");
+        }
+        int launches = 0;
+        CK(launch_coo_build(c, lim.sms, st, &launches), "coo build");
+        h->kernel_launches += launches;
+        h->sort_launches += launches;
+        h->coo = c;
+        h->coo_rows = true;
         h->last_union = true;
     }
     if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
@@ -953,9 +1014,13 @@ int gumap_knn_coo(gumap_knn* h, int32_t* row, int32_t* col, float* w, int64_t* n
     if (!h || !h->last_union) return fail(GUMAP_ERR_INVALID_ARG, "last run built no union COO");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     const long long cap = 2ll * h->last_n_src * h->k;
-    CK(launch_coo_unpack(h->coo_keys, h->coo_vals, h->coo_key_bits, h->d_ctr, cap, row, col, w, nnz,
-                         static_cast<cudaStream_t>(stream)),
-       "coo unpack");
+    if (h->coo_rows) {
+        CK(launch_coo_unpack(h->coo, cap, row, col, w, nnz, static_cast<cudaStream_t>(stream)), "coo unpack");
+    } else {
+        CK(launch_pairs_unpack(h->coo_keys, h->coo_vals, h->coo_key_bits, h->d_ctr, cap, row, col, w, nnz,
+                               static_cast<cudaStream_t>(stream)),
+           "coo unpack");
+    }
     h->kernel_launches++;
     return GUMAP_OK;
 }
@@ -1010,6 +1075,10 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             CK(cudaSetDevice(h->device), "cudaSetDevice");
             CK(cudaDeviceSynchronize(), "sync");
             return apply_batch_plan(h, value == 0 ? kMaxBatchW : (int32_t)value);
+        case GUMAP_OPT_COO_BUILD:
+            if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "COO build must be 0, 1 or 2");
+            h->opt_coo_build = (int)value;
+            return GUMAP_OK;
         case GUMAP_OPT_STAGE:
             if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "stage must be 0, 1 or 2");
             h->opt_stage = (int)value;

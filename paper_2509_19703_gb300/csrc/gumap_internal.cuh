@@ -45,7 +45,7 @@ struct DeviceCounters {
     int32_t levels_max;        // max over launches since the last host reset
     int32_t aux_count;         // scratch counter of the set-up kernels
     long long level_sum;       // sum of levels over launches since the last host reset
-    unsigned long long coo_nnz;
+    unsigned long long coo_nnz;  // valid (key, value) pairs of the radix-sorted COO
     // device time of the MS-BFS phases (globaltimer ns, block 0's view at the
     // grid barriers), summed over launches since the last host reset
     unsigned long long t_init_ns;
@@ -212,13 +212,24 @@ cudaError_t launch_frontier(const FrontierArgs& a, cudaStream_t s);
 // ---- weights.cu
 cudaError_t launch_smooth_knn(const uint16_t* dist, int32_t n_rows, int32_t k, float T, float* rho,
                               float* sigma, float* a, cudaStream_t s);
-// Union weights into w; when keys != NULL also the 2 * n * k COO (key, value)
-// pairs, counting the valid keys into ctr->coo_nnz.
+// Union weights into w; when mcnt != NULL also the per-slot mirror ranks
+// (mpos) and per-row counts (kval, mcnt) of the row-by-row COO build; mcnt
+// must be zero on entry.
 cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k, float* w,
-                         int key_bits, unsigned long long* keys, float* vals, DeviceCounters* ctr, cudaStream_t s);
-cudaError_t launch_coo_unpack(const unsigned long long* keys, const float* vals, int key_bits,
-                              const DeviceCounters* ctr, long long cap, int32_t* row, int32_t* col, float* w,
-                              int64_t* nnz_out, cudaStream_t s);
+                         uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s);
+
+// Below kCooRowsMinSlots slots the COO is 2 n k (key, value) pairs sorted by
+// the radix sort; the row-by-row build's long-row tails cost more there than
+// the passes it saves.
+constexpr long long kCooRowsMinSlots = 2ll << 20;
+// Union weights into w and the 2 * n * k COO (key, value) pairs (padding
+// pairs all ones), counting the valid pairs into ctr->coo_nnz.
+cudaError_t launch_union_pairs(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k,
+                               float* w, int key_bits, unsigned long long* keys, float* vals, DeviceCounters* ctr,
+                               cudaStream_t s);
+cudaError_t launch_pairs_unpack(const unsigned long long* keys, const float* vals, int key_bits,
+                                const DeviceCounters* ctr, long long cap, int32_t* row, int32_t* col, float* w,
+                                int64_t* nnz_out, cudaStream_t s);
 
 // ---- sort.cu: LSD radix sort of (u64 key, float value) on the low `bits` key bits
 // (bits <= 64). A look-back wait that gives up writes kStatusTimeout to *status.
@@ -227,6 +238,40 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned lon
                              float* vals_tmp, long long count, int bits, void* temp, size_t temp_bytes,
                              int32_t* status, cudaStream_t s, unsigned long long** keys_out, float** vals_out,
                              int* launches);
+
+// ---- coo.cu: the fuzzy union as a COO sorted by (row, col), built by rows
+constexpr uint32_t kNoMirror = 0xFFFFFFFFu;  // mpos of a slot that emits no mirror
+constexpr int kCooCtrTile = 0;               // tile counter of the row scan
+constexpr int kCooCtrLarge = 1;              // rows on the long-row list
+constexpr int kCooCtrNextLarge = 2;          // next long row to sort
+constexpr int kCooCtrWords = 4;
+
+struct CooArgs {
+    const int32_t* idx;          // kNN lists [n][k], valid slots first
+    const float* w;              // union weight per slot [n][k]
+    const uint32_t* mpos;        // per slot: place of its mirror among the target row's mirrors, or kNoMirror
+    const int32_t* kval;         // per row: valid slots (own entries)
+    const uint32_t* mcnt;        // per row: mirrors received
+    int32_t n;
+    int32_t k;
+    unsigned long long* rowoff;  // [n + 1] first entry of each row; rowoff[n] = nnz
+    unsigned long long* pub;     // look-back words of the row scan [tiles], zeroed
+    uint32_t* ctr;               // [kCooCtrWords], zeroed
+    int32_t* large;              // [n] rows too long for one warp
+    int32_t* tcol;               // scattered rows [2 n k] (columns, unordered in a row)
+    float* tw;
+    int32_t* ccol;               // sorted rows [2 n k]
+    float* cw;
+    int32_t* status;             // kStatusTimeout if a look-back wait gives up
+};
+// One zeroed block per run: mcnt [n] (16-byte padded), ctr, pub.
+size_t coo_scratch_bytes(int32_t n);
+void coo_scratch_split(void* scratch, int32_t n, uint32_t** mcnt, uint32_t** ctr, unsigned long long** pub);
+// Row scan, scatter, warp-row sort, long-row sort (4 launches) after launch_union.
+cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* launches);
+// Rows, columns and weights of the sorted COO (up to cap entries) and nnz.
+cudaError_t launch_coo_unpack(const CooArgs& a, long long cap, int32_t* row, int32_t* col, float* w,
+                              int64_t* nnz_out, cudaStream_t s);
 
 // ---- validate.cu
 // Device-side CSR validation; writes 0 to *bad if the graph is valid.

@@ -418,7 +418,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
     float* rho = reinterpret_cast<float*>(dptr(o_rho));
     float* sigma = reinterpret_cast<float*>(dptr(o_sigma));
     ck(launch_smooth_knn(L->dist, (int32_t)N, k, T, rho, sigma, want_union ? d_a : L->w, st));
-    if (want_union) ck(launch_union(L->idx, L->dist, d_a, (int32_t)N, k, L->w, 0, nullptr, nullptr, nullptr, st));
+    if (want_union) ck(launch_union(L->idx, L->dist, d_a, (int32_t)N, k, L->w, nullptr, nullptr, nullptr, st));
     if (ng > 1) {
         long long grid = (N + 255) / 256;
         if (grid > 4096) grid = 4096;

@@ -140,10 +140,50 @@ __device__ __forceinline__ int find_in_row(const int32_t* __restrict__ idx, cons
     return (lo < k && rd[lo] == dij && ri[lo] == i) ? lo : -1;
 }
 
+// One thread per slot (i, t): union weight into w. With mcnt given, also
+// what the row-by-row COO build needs (coo.cu): a slot whose target j does
+// not list i is a mirror in row j and takes the next place among j's
+// mirrors (mpos; kNoMirror otherwise), and the row's own entries are its
+// valid slots, which come first (kval).
+__global__ void __launch_bounds__(256) union_kernel(const int32_t* __restrict__ idx,
+                                                    const uint16_t* __restrict__ dist,
+                                                    const float* __restrict__ a, int n, int k,
+                                                    float* __restrict__ w, uint32_t* __restrict__ mcnt,
+                                                    uint32_t* __restrict__ mpos, int32_t* __restrict__ kval) {
+    const long long total = (long long)n * k;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < total;
+         s += (long long)gridDim.x * blockDim.x) {
+        const long long i = s / k;
+        const int t = (int)(s - i * k);
+        const int j = idx[s];
+        float wv = 0.0f;
+        bool mutual = false;
+        if (j >= 0) {
+            const float aij = a[s];
+            const int p = find_in_row(idx, dist, k, j, (int)i, dist[s]);
+            const float aji = p >= 0 ? a[(size_t)j * k + p] : 0.0f;
+            mutual = p >= 0;
+            wv = aij + aji - aij * aji;
+        }
+        w[s] = wv;
+        if (mcnt) {
+            if (j >= 0) {
+                mpos[s] = mutual ? kNoMirror : atomicAdd(&mcnt[j], 1u);
+                if (t == k - 1 || idx[s + 1] < 0) kval[i] = t + 1;
+            } else {
+                mpos[s] = kNoMirror;
+                if (t == 0) kval[i] = 0;
+            }
+        }
+    }
+}
+
+// The COO as (row << key_bits | col, weight) pairs for the radix sort
+// (sort.cu), used below a size where the row-by-row build (coo.cu) pays.
 // One thread per slot (i, t): union weight into w, and the COO pairs:
 // (i, j) always, (j, i) too when i is absent from j's list (otherwise j's own
 // slot emits it). Padding slots emit all-ones keys, which sort last.
-__global__ void __launch_bounds__(256) union_kernel(const int32_t* __restrict__ idx,
+__global__ void __launch_bounds__(256) union_pairs_kernel(const int32_t* __restrict__ idx,
                                                     const uint16_t* __restrict__ dist,
                                                     const float* __restrict__ a, int n, int k,
                                                     float* __restrict__ w, int key_bits,
@@ -199,7 +239,7 @@ __global__ void __launch_bounds__(256) union_kernel(const int32_t* __restrict__ 
     }
 }
 
-__global__ void coo_unpack_kernel(const unsigned long long* __restrict__ keys, const float* __restrict__ vals,
+__global__ void pairs_unpack_kernel(const unsigned long long* __restrict__ keys, const float* __restrict__ vals,
                                   int key_bits, const unsigned long long* __restrict__ nnz_dev, long long cap,
                                   int32_t* __restrict__ row, int32_t* __restrict__ col, float* __restrict__ w,
                                   int64_t* __restrict__ nnz_out) {
@@ -234,18 +274,27 @@ cudaError_t launch_smooth_knn(const uint16_t* dist, int32_t n_rows, int32_t k, f
 }
 
 cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k, float* w,
-                         int key_bits, unsigned long long* keys, float* vals, DeviceCounters* ctr, cudaStream_t s) {
+                         uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int grid = grid_for((long long)n * k, 256, 152 * 16);
-    union_kernel<<<grid, 256, 0, s>>>(idx, dist, a, n, k, w, key_bits, keys, vals, ctr ? &ctr->coo_nnz : nullptr);
+    union_kernel<<<grid, 256, 0, s>>>(idx, dist, a, n, k, w, mcnt, mpos, kval);
     return cudaGetLastError();
 }
 
-cudaError_t launch_coo_unpack(const unsigned long long* keys, const float* vals, int key_bits,
-                              const DeviceCounters* ctr, long long cap, int32_t* row, int32_t* col, float* w,
-                              int64_t* nnz_out, cudaStream_t s) {
+cudaError_t launch_union_pairs(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k,
+                               float* w, int key_bits, unsigned long long* keys, float* vals, DeviceCounters* ctr,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int grid = grid_for((long long)n * k, 256, 152 * 16);
+    union_pairs_kernel<<<grid, 256, 0, s>>>(idx, dist, a, n, k, w, key_bits, keys, vals, ctr ? &ctr->coo_nnz : nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs_unpack(const unsigned long long* keys, const float* vals, int key_bits,
+                                const DeviceCounters* ctr, long long cap, int32_t* row, int32_t* col, float* w,
+                                int64_t* nnz_out, cudaStream_t s) {
     const int grid = grid_for(cap > 0 ? cap : 1, 256, 152 * 16);
-    coo_unpack_kernel<<<grid, 256, 0, s>>>(keys, vals, key_bits, &ctr->coo_nnz, cap, row, col, w, nnz_out);
+    pairs_unpack_kernel<<<grid, 256, 0, s>>>(keys, vals, key_bits, &ctr->coo_nnz, cap, row, col, w, nnz_out);
     return cudaGetLastError();
 }
 

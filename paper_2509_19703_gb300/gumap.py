@@ -25,6 +25,8 @@ ENGINE_AUTO, ENGINE_MSBFS, ENGINE_MSBFS_SM, ENGINE_FRONTIER, ENGINE_BATCH = 0, 1
 OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 2, 3, 4, 5
 OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH, OPT_CTAS_PER_SM, OPT_STAGE = 6, 7, 8, 9, 10
 OPT_BATCH_WIDTH = 11
+OPT_COO_BUILD = 12
+COO_AUTO, COO_RADIX, COO_ROWS = 0, 1, 2
 DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
 MAX_K = 256
 DIST_INF = 0xFFFF

@@ -123,3 +123,20 @@ def test_no_cpu_fallback_when_library_missing(monkeypatch, tmp_path):
     monkeypatch.setattr(gumap._build, "LIB", str(tmp_path / "absent.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         gumap.load()
+
+
+def test_binding_constants_match_the_header():
+    """Every GUMAP_* integer constant of the header that the binding also
+    defines (without the prefix) has the same value there."""
+    import re
+
+    from paper_2509_19703_gb300 import gumap
+    text = open(os.path.join(ROOT, "include", "gumap.h")).read()
+    pairs = re.findall(r"^#define\s+GUMAP_(\w+)\s+(0x[0-9A-Fa-f]+|-?\d+)\b", text, flags=re.M)
+    assert len(pairs) > 20
+    checked = 0
+    for name, val in pairs:
+        if hasattr(gumap, name):
+            assert getattr(gumap, name) == int(val, 0), name
+            checked += 1
+    assert checked >= 20

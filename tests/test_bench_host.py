@@ -56,11 +56,9 @@ def test_partial_work_accepts_int16_distances():
     assert np.array_equal(entries, work)
 
 
-def test_frontier_and_sort_byte_models():
+def test_frontier_and_coo_byte_models():
     entries = np.array([4, 12, 0], dtype=np.int64)
     rows = np.array([1, 3, 1], dtype=np.int64)
     assert bench.frontier_alg_bytes(entries, rows, 15) == 8 * 5 + 4 * 16 + 6 * 15 * 3
-    # n = 1,000,000: 20-bit ids, 40-bit keys, 5 passes
-    assert bench.sort_alg_bytes(1_000_000, 15) == 2 * 1_000_000 * 15 * (8 + 24 * 5)
-    # n = 1024: 10-bit ids (0..1023), 20-bit keys, 3 passes
-    assert bench.sort_alg_bytes(1024, 15) == 2 * 1024 * 15 * (8 + 24 * 3)
+    # row scan 16 n, scatter 12 n k + 8 nnz, row sorts 16 nnz
+    assert bench.coo_alg_bytes(1000, 15, 24000) == 16 * 1000 + 12 * 15000 + 24 * 24000

@@ -65,6 +65,24 @@ def test_zoo_forced_direction(g, k, direction):
                       f"{g.name} {mode} k={k} direction={direction}")
 
 
+@pytest.mark.parametrize("build", [gumap.COO_RADIX, gumap.COO_ROWS], ids=["radix", "rows"])
+@pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
+def test_zoo_coo_builds(g, k, build):
+    """Both builds of the union COO (radix-sorted (row, col) keys; rows
+    counted, scanned, scattered and ranked by column) give the oracle's COO."""
+    for mode in ("full", "partial"):
+        ref = oracle_ref(g, k, mode)
+        assert_parity(run_gpu(g, k, mode, coo_build=build), ref, f"{g.name} {mode} k={k} coo build {build}")
+
+
+@pytest.mark.parametrize("g", [gg.star(3000), gg.barabasi_albert(20000, 5, 1)], ids=lambda g: g.name)
+def test_long_rows_of_the_row_build(g):
+    """Rows longer than one warp sorts (the star's centre: 2999 entries; the
+    scale-free hubs) go through the shared-memory bitmap ranking."""
+    ref = oracle_ref(g, 15, "partial")
+    assert_parity(run_gpu(g, 15, "partial", coo_build=gumap.COO_ROWS), ref, f"{g.name} rows")
+
+
 @pytest.mark.parametrize("width,ctas,stage", [(2, 3, 1), (4, 4, 1), (2, 4, 0), (4, 3, 0), (4, 3, 2)])
 @pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
 def test_zoo_kernel_builds(g, k, width, ctas, stage):
@@ -240,7 +258,7 @@ def test_bad_option_values_are_rejected():
     g = gg.grid(5, 5)
     with gumap.KnnGraph.from_graph(g, 3) as kg:
         for opt, val in ((gumap.OPT_CTAS_PER_SM, 5), (gumap.OPT_PULL_WIDTH, 3), (gumap.OPT_DIRECTION, 7),
-                         (gumap.OPT_STAGE, 3)):
+                         (gumap.OPT_STAGE, 3), (gumap.OPT_COO_BUILD, 3)):
             with pytest.raises(gumap.GumapError) as e:
                 kg.set_option(opt, val)
             assert e.value.status == gumap.ERR_INVALID_ARG
