@@ -689,7 +689,7 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
     cudaError_t e;
 
     const cudaMemcpyKind kind = (flags & GUMAP_CSR_ON_DEVICE) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    // row_ptr plus one slot for the device validation's verdict
+    // row_ptr plus one slot for the device validation's result
     if ((e = pool_alloc((void**)&h->d_rp, sizeof(int32_t) * ((size_t)n + 2))) != cudaSuccess ||
         (e = pool_alloc((void**)&h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(nnz, 1))) != cudaSuccess ||
         (e = pool_alloc((void**)&h->d_identity, sizeof(int32_t) * (size_t)n)) != cudaSuccess ||
@@ -709,7 +709,7 @@ int gumap_knn_create(gumap_knn** out, const int32_t* row_ptr, const int32_t* col
         return cuda_fail(e, "cudaMalloc");
     }
     {
-        // A CSR on the device is validated there; the verdict lands in the slot
+        // A CSR on the device is validated there; the result lands in the slot
         // after row_ptr, so one readback brings back both (the host needs
         // row_ptr for the degrees).
         std::vector<int32_t> rp_dev;
