@@ -62,3 +62,15 @@ def test_frontier_and_coo_byte_models():
     assert bench.frontier_alg_bytes(entries, rows, 15) == 8 * 5 + 4 * 16 + 6 * 15 * 3
     # row scan 16 n, scatter 12 n k + 8 nnz, row sorts 16 nnz
     assert bench.coo_alg_bytes(1000, 15, 24000) == 16 * 1000 + 12 * 15000 + 24 * 24000
+
+
+def test_all_core_oracle_sample_covers_each_source_once():
+    """The all-core CPU baseline splits one seeded source order over spawned
+    processes in disjoint strides; with a budget large enough to finish, the
+    processes together do every source of every graph."""
+    graphs = [gg.grid(12, 12), gg.disjoint_union([gg.path(30), gg.star(9)], "pathstar")]
+    works = [bench.component_work(g) for g in graphs]
+    v, desc = bench.oracle_sample_all_cores(graphs, works, 60.0, 2)
+    assert v > 0
+    assert desc.startswith(f"{graphs[0].n} of {graphs[0].n} sources") and "2 processes" in desc
+    assert f"{graphs[1].n} of {graphs[1].n} sources" in desc
