@@ -459,7 +459,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc = oracle_sample(graphs, works, args.cpu_seconds)
         cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc}
-        procs = cpu_cores()
+        procs = min(cpu_cores(), 64)
         if procs > 1:
             try:
                 v, desc = oracle_sample_all_cores(graphs, works, args.cpu_seconds / 2, procs)
