@@ -156,6 +156,32 @@ def check_partial_work(orc):
     for k, want in ((15, 52), (50, 164)):
         _, _, work = orc.knn_partial(g, k, sources=np.array([v]), return_work=True)
         assert int(work[0]) == want, (k, int(work[0]))
+    # closed forms: path interior at k = 15 stops at D = 8 after 1 + 14
+    # vertices of degree 2 (30), at k = 1 after the source alone (2); a star's
+    # centre after itself (n - 1); a leaf after itself at k = 1 (1), after
+    # itself and the centre at k >= 2 (1 + n - 1); K_n after the source
+    # (n - 1); a component of fewer than k + 1 vertices is exhausted (2 m).
+    cases = [(gg.path(100), 50, 15, 30), (gg.path(100), 50, 1, 2), (gg.star(40), 0, 15, 39),
+             (gg.star(40), 7, 1, 1), (gg.star(40), 7, 15, 40), (gg.complete(20), 3, 15, 19),
+             (gg.disjoint_union([gg.path(5), gg.complete(30)], "p5k30"), 2, 15, 8)]
+    for g, v, k, want in cases:
+        _, _, work = orc.knn_partial(g, k, sources=np.array([v]), return_work=True)
+        assert int(work[0]) == want, (g.name, v, k, int(work[0]))
+    # brute force from Floyd-Warshall distances: D_s is the k-th smallest
+    # distance to another reachable vertex (infinite if fewer than k), and
+    # the work is the degree sum over the vertices closer than D_s
+    for g in tiny_graphs():
+        if g.n < 2:
+            continue
+        D = floyd_warshall(g)
+        deg = np.diff(g.row_ptr)
+        for k in sorted({1, 3, min(15, g.n - 1)}):
+            _, _, work = orc.knn_partial(g, k, return_work=True)
+            for s_ in range(g.n):
+                others = np.sort(D[s_][np.isfinite(D[s_]) & (np.arange(g.n) != s_)])
+                Ds = others[k - 1] if len(others) >= k else np.inf
+                want = int(deg[D[s_] < Ds].sum())
+                assert int(work[s_]) == want, (g.name, k, s_, int(work[s_]), want)
 
 
 # --------------------------------------------------------------------------
