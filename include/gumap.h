@@ -180,8 +180,9 @@ int gumap_batch_create(gumap_knn **h, int32_t n_graphs, const int32_t *vertex_of
  * n_src exceeds every earlier call. With union weights the symmetric COO is
  * also built and kept in the handle for gumap_knn_coo(): below 2^21 slots
  * (n k) by an LSD radix sort of 2 n k (row, col) keys, from there on row by
- * row (GUMAP_OPT_COO_BUILD overrides the choice); either build holds about
- * 32 n k bytes of scratch in the handle. Errors:
+ * row (GUMAP_OPT_COO_BUILD overrides the choice). The handle keeps that
+ * build's scratch: 48 n k bytes for the radix sort (keys and values, twice),
+ * 36 n k bytes for the row build. Errors:
  * INVALID_ARG (bad pointer/size, union with explicit sources), OOM, CUDA.
  * Device-side failures (a bounded wait that timed out) are reported by
  * gumap_knn_check().
