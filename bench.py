@@ -42,6 +42,9 @@ K_NEIGHBOURS = 15
 METRIC = "BFS-kNN GTEPS (full all-pairs form, k=15) and % of HBM peak"
 WORKLOAD = ("full-APSP GUMAP kNN + UMAP weights + fuzzy union + sorted COO, k=15, all sources, on "
             "BA n=20000 m0=5 seed 1 and G(n=5000, p=0.1) seed 2")
+PARTIAL_METRIC = "BFS-kNN GTEPS (partial form, k=15 and 50) and % of HBM peak"
+PARTIAL_WORKLOAD = ("partial-BFS SL-GUMAP kNN + UMAP weights + fuzzy union + sorted COO, all sources, k=15 and "
+                    "k=50, on BA n=1000000 m0=4 seed 3 and the 1000x1000 grid")
 FLUSH_BYTES = 512 << 20
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "msbfs_kernel_traffic.json")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_2509_19703_gb300", "csrc", "msbfs.cu")]
@@ -343,6 +346,50 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def partial_runs():
+    from paper_2509_19703_gb300 import graphgen as gg
+    graphs = [gg.config_ba1m(), gg.config_grid1m()]
+    return [(g, k) for g in graphs for k in (15, 50)]
+
+
+def run_reference_partial(args):
+    """The reference arm of the partial workload: the oracle's partial BFS
+    (with its own scan count as the work) and FP64 weights on a seeded
+    source sample of each (graph, k), one thread."""
+    import numpy as np
+
+    import oracle
+    rank, _, _ = dist_info()
+    if rank != 0:
+        return
+    runs = partial_runs()
+    budget = max(0.2, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals, parts = [], []
+    for i in range(args.warmup + args.steps):
+        work, busy, parts = 0, 0.0, []
+        for g, k in runs:
+            order = np.random.default_rng(1234).permutation(g.n).astype(np.int32)
+            done, t0 = 0, time.perf_counter()
+            while done < g.n and time.perf_counter() - t0 < budget / len(runs):
+                _, dist, w = oracle.knn_partial(g, k, sources=order[done:done + 1024], return_work=True)
+                oracle.smooth_knn(dist)
+                work += int(w.sum())
+                done += len(w)
+            busy += time.perf_counter() - t0
+            parts.append(f"{done} of {g.n} sources of {g.name} at k={k}")
+        if i >= args.warmup:
+            vals.append(work / 2 / busy / 1e9)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": PARTIAL_METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": budget * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32/f64", "data": "synthetic",
+            "config": {"workload": PARTIAL_WORKLOAD},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: {'; '.join(parts)}, about {budget:.0f} s"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -568,12 +615,14 @@ def run_partial_workload(args):
     import numpy as np
     import torch
 
-    from paper_2509_19703_gb300 import graphgen as gg
     from paper_2509_19703_gb300 import gumap
 
     torch.cuda.set_device(0)
-    graphs = [gg.config_ba1m(), gg.config_grid1m()]
-    runs = [(g, k) for g in graphs for k in (15, 50)]
+    runs = partial_runs()
+    graphs = []
+    for g, _ in runs:
+        if not any(g is h for h in graphs):
+            graphs.append(g)
     kgs = [gumap.KnnGraph.from_graph(g, k, mode=gumap.PARTIAL) for g, k in runs]
     tuned = [kg.autotune() for kg in kgs]
     for kg in kgs:
@@ -697,12 +746,11 @@ def run_partial_workload(args):
     for r in per_run:
         r.pop("entries")
         r.pop("rows")
-    line = {"metric": "BFS-kNN GTEPS (partial form, k=15 and 50) and % of HBM peak", "value": value,
+    line = {"metric": PARTIAL_METRIC, "value": value,
             "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32 ids / u16 distances / f32 weights", "data": "synthetic",
-            "config": {"workload": "partial-BFS SL-GUMAP kNN + UMAP weights + fuzzy union + sorted COO, all "
-                                   "sources, k=15 and k=50, on BA n=1000000 m0=4 seed 3 and the 1000x1000 grid",
+            "config": {"workload": PARTIAL_WORKLOAD,
                        "work_edges_per_step": work_per_step, "runs": per_run,
                        "l2": "flushed (512 MB write) before each timed step",
                        "autotuned": [{key: t[key] for key in ("engine", "state_bytes", "best_ms", "default_ms")}
@@ -823,7 +871,13 @@ def run_serve_workload(args):
 
 def main():
     args = parse_args()
-    if args.workload == "serve":
+    if args.impl == "reference" and args.workload in ("batch", "serve"):
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle arm covers the full-form and partial-form "
+                                                              "workloads; batch and serve compare against one launch "
+                                                              "per graph on the GPU instead"}), flush=True)
+    elif args.impl == "reference" and args.workload == "partial":
+        run_reference_partial(args)
+    elif args.workload == "serve":
         run_serve_workload(args)
     elif args.workload == "partial":
         run_partial_workload(args)
