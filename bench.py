@@ -301,18 +301,47 @@ def _oracle_worker(job):
     return work, busy, done_per
 
 
+def _oracle_worker_to_queue(job, q):
+    try:
+        q.put(("ok", _oracle_worker(job)))
+    except Exception as e:  # reported to the parent instead of a result
+        q.put(("error", f"{type(e).__name__}: {e}"))
+
+
 def oracle_sample_all_cores(graphs, works, budget_s, procs):
     """The oracle sample of oracle_sample spread over `procs` processes
     (spawned, so no CUDA state is inherited): process p takes every procs-th
     source of the same seeded order. GTEPS = all processes' work / the
-    longest busy time."""
+    longest busy time. Raises if a process fails or does not report within
+    a generous deadline; every process is ended before returning."""
     import multiprocessing as mp
+    import queue
 
     import numpy as np
     orders = [np.random.default_rng(1234).permutation(g.n).astype(np.int32) for g in graphs]
     jobs = [(graphs, works, [o[p::procs] for o in orders], budget_s / len(graphs)) for p in range(procs)]
-    with mp.get_context("spawn").Pool(procs) as pool:
-        res = pool.map(_oracle_worker, jobs)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    workers = [ctx.Process(target=_oracle_worker_to_queue, args=(job, q), daemon=True) for job in jobs]
+    res = []
+    try:
+        for w in workers:
+            w.start()
+        deadline = time.monotonic() + 2 * budget_s + 120.0
+        for _ in workers:
+            try:
+                status, r = q.get(timeout=max(0.1, deadline - time.monotonic()))
+            except queue.Empty:
+                raise TimeoutError("an oracle process did not report in time") from None
+            if status != "ok":
+                raise RuntimeError(r)
+            res.append(r)
+    finally:
+        for w in workers:
+            w.join(timeout=5)
+            if w.is_alive():
+                w.terminate()
+                w.join(timeout=5)
     work = sum(r[0] for r in res)
     busy = max(r[1] for r in res)
     done = [sum(r[2][i] for r in res) for i in range(len(graphs))]
