@@ -176,8 +176,11 @@ int gumap_batch_create(gumap_knn **h, int32_t n_graphs, const int32_t *vertex_of
  *            (GUMAP_WEIGHTS_DIRECTED); 0 for padded slots.
  *
  * All three outputs are owned by the caller and must not overlap. The call
- * may grow library-owned scratch (which may synchronise the device) when
- * n_src exceeds every earlier call. With union weights the symmetric COO is
+ * grows library-owned scratch when n_src exceeds every earlier call, without
+ * synchronising: a replaced block returns to the library's pool once the
+ * work queued before it has finished. A handle's calls must be ordered on
+ * the device (one stream, or streams the caller orders), since they share
+ * the handle's scratch. With union weights the symmetric COO is
  * also built and kept in the handle for gumap_knn_coo(): below 2^21 slots
  * (n k) by an LSD radix sort of 2 n k (row, col) keys, from there on row by
  * row (GUMAP_OPT_COO_BUILD overrides the choice). The handle keeps that

@@ -341,7 +341,7 @@ cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* lau
 
 cudaError_t launch_coo_unpack(const CooArgs& a, long long cap, int32_t* row, int32_t* col, float* w,
                               int64_t* nnz_out, cudaStream_t s) {
-    const int grid = grid_for((long long)(a.n > 0 ? a.n : 1) * 32, 256, 152 * 16);
+    const int grid = grid_for((long long)(a.n > 0 ? a.n : 1) * 32, 256, device_sm_count() * 16);
     coo_unpack_kernel<<<grid, 256, 0, s>>>(a, cap, row, col, w, nnz_out);
     return cudaGetLastError();
 }

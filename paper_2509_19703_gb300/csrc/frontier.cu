@@ -113,7 +113,7 @@ template <int LPL>
 cudaError_t launch_lpl(const FrontierArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)kWarpsPerBlock * (a.k + 1) * sizeof(int32_t);
     long long g = ((long long)a.n_src + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (g > 152 * 64) g = 152 * 64;
+    if (g > device_sm_count() * 64ll) g = device_sm_count() * 64ll;
     if (g < 1) g = 1;
     frontier_kernel<LPL><<<(unsigned)g, kThreads, smem, s>>>(a);
     return cudaGetLastError();

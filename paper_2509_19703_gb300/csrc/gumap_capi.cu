@@ -201,7 +201,7 @@ struct gumap_knn {
     DevBuf act, need, cnt;
 
     // per-run scratch
-    DevBuf rho, sigma, a;
+    DevBuf rho, sigma, wrow;  // wrow: the smoothing step's per-row records (union weights)
     DevBuf keys, vals, keys_tmp, vals_tmp, sort_temp;  // COO as radix-sorted (key, value) pairs
     DevBuf coo_scr, coo_kval, coo_mpos, coo_rowoff, coo_large, coo_tcol, coo_tw, coo_col, coo_w;  // COO by rows
 
@@ -231,6 +231,17 @@ struct gumap_knn {
     int32_t batch_width = 0;  // GUMAP_OPT_BATCH_WIDTH in force
     int opt_coo_build = 0;    // GUMAP_OPT_COO_BUILD
 
+    // Blocks replaced by a larger one while work queued before may still use
+    // them: each goes back to the pool once an event recorded on the stream of
+    // that work has completed (no device-wide synchronisation).
+    struct Deferred {
+        void* p;
+        size_t bytes;
+        cudaEvent_t ev;
+    };
+    std::vector<Deferred> deferred;
+    cudaStream_t last_stream = nullptr;  // stream of the handle's latest enqueued work
+
     // stats
     int64_t bfs_launches = 0;
     int64_t kernel_launches = 0;
@@ -245,13 +256,37 @@ struct gumap_knn {
 
 namespace {
 
-// Buffers come from the library's pool (pool.cu). Growing one waits for the
-// device first: queued work may still use the old block.
-int ensure(DevBuf& b, size_t bytes, const char* what) {
+// Hands the deferred blocks whose work has finished back to the pool (all of
+// them when `all`: the caller has synchronised the device).
+void reap(gumap_knn* h, bool all) {
+    size_t keep = 0;
+    for (size_t i = 0; i < h->deferred.size(); ++i) {
+        const gumap_knn::Deferred d = h->deferred[i];
+        if (all || cudaEventQuery(d.ev) == cudaSuccess) {
+            pool_free(d.p, d.bytes);
+            cudaEventDestroy(d.ev);
+        } else {
+            h->deferred[keep++] = d;
+        }
+    }
+    h->deferred.resize(keep);
+}
+
+// Buffers come from the library's pool (pool.cu). A buffer that grows hands
+// its old block back only once the work the handle queued before (on
+// last_stream; a handle's calls are ordered on its streams by contract) has
+// finished.
+int ensure(gumap_knn* h, DevBuf& b, size_t bytes, const char* what) {
     if (b.bytes >= bytes && b.p) return GUMAP_OK;
     if (b.p) {
-        CK(cudaDeviceSynchronize(), "sync before growing a buffer");
-        pool_free(b.p, b.bytes);
+        cudaEvent_t ev = nullptr;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event for a replaced buffer");
+        cudaError_t e = cudaEventRecord(ev, h->last_stream);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(ev);
+            return cuda_fail(e, "event for a replaced buffer");
+        }
+        h->deferred.push_back({b.p, b.bytes, ev});
         b.p = nullptr;
         b.bytes = 0;
     }
@@ -271,7 +306,7 @@ void release(DevBuf& b) {
 size_t held_bytes(const gumap_knn* h) {
     size_t t = (size_t)(h->n + 1) * 4 + (size_t)h->nnz * 4 + (size_t)h->n * 4 + sizeof(DeviceCounters);
     for (const auto& c : h->cuts) t += (size_t)(c.grid + 1) * 4 + c.meta_bytes + c.ocol_bytes;
-    const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
+    const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                           &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
                           &h->coo_scr, &h->coo_kval, &h->coo_mpos, &h->coo_rowoff, &h->coo_large,
                           &h->coo_tcol, &h->coo_tw, &h->coo_col, &h->coo_w};
@@ -468,10 +503,10 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
     // pull items' saturation states (n x W/2 bytes: enough for either item width), 16-byte aligned
     const size_t sat_off = (words * 3 * sizeof(uint32_t) + 5 * (size_t)h->n * sizeof(int32_t) + 15) & ~(size_t)15;
     const size_t sat_bytes = ((size_t)h->n * (size_t)(W / 2) + 15) & ~(size_t)15;
-    if ((rc = ensure(h->bits, sat_off + sat_bytes, "bitsets"))) return rc;
-    if ((rc = ensure(h->act, (size_t)W * 4, "act"))) return rc;
-    if ((rc = ensure(h->need, (size_t)W * 4, "need"))) return rc;
-    if ((rc = ensure(h->cnt, (size_t)S * 4, "cnt"))) return rc;
+    if ((rc = ensure(h, h->bits, sat_off + sat_bytes, "bitsets"))) return rc;
+    if ((rc = ensure(h, h->act, (size_t)W * 4, "act"))) return rc;
+    if ((rc = ensure(h, h->need, (size_t)W * 4, "need"))) return rc;
+    if ((rc = ensure(h, h->cnt, (size_t)S * 4, "cnt"))) return rc;
     uint32_t* base = static_cast<uint32_t*>(h->bits.p);
     const int nblocks = (int)(((long long)n_src + S - 1) / S);
     for (int b = 0; b < nblocks; ++b) {
@@ -603,6 +638,130 @@ int run_frontier(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_i
 
 }  // namespace
 
+namespace {
+
+int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_idx, uint16_t* out_dist, float* out_w,
+             cudaStream_t st) {
+    const bool want_union = !(h->flags & GUMAP_WEIGHTS_DIRECTED);
+    const int32_t* src = sources ? sources : h->d_identity;
+    const int32_t k = h->k;
+    int rc;
+    const size_t slots = (size_t)n_src * k;
+    if ((rc = ensure(h, h->rho, (size_t)n_src * 4, "rho")) || (rc = ensure(h, h->sigma, (size_t)n_src * 4, "sigma")))
+        return rc;
+    if (want_union && (rc = ensure(h, h->wrow, (size_t)n_src * sizeof(WeightRow), "row records"))) return rc;
+
+    const int engine = pick_engine(h);
+    h->last_engine = engine;
+    if (engine == GUMAP_ENGINE_MSBFS) {
+        rc = run_msbfs(h, src, sources == nullptr, n_src, out_idx, out_dist, st);
+    } else if (engine == GUMAP_ENGINE_FRONTIER) {
+        if (h->mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
+        rc = run_frontier(h, src, n_src, out_idx, out_dist, st);
+    } else if (engine == GUMAP_ENGINE_BATCH) {
+        if (!h->batch || sources) return fail(GUMAP_ERR_INVALID_ARG, "the batched engine needs a batch handle and sources == NULL");
+        rc = run_batch(h, out_idx, out_dist, st);
+    } else {
+        return fail(GUMAP_ERR_INVALID_ARG, "engine %d not available", engine);
+    }
+    if (rc) return rc;
+
+    const float T = (float)std::log2((double)k);
+    WeightRow* wrow = want_union ? static_cast<WeightRow*>(h->wrow.p) : nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->opt_profile) {
+        if ((rc = next_event_pair(h, &e0, &e1, kStageWeights))) return rc;
+        CK(cudaEventRecord(e0, st), "cudaEventRecord");
+    }
+    CK(launch_smooth_knn(out_idx, out_dist, n_src, k, T, static_cast<float*>(h->rho.p), static_cast<float*>(h->sigma.p),
+                         wrow, want_union ? nullptr : out_w, st),
+       "smooth_knn");
+    h->kernel_launches++;
+    const bool coo_by_rows =
+        h->opt_coo_build == 2 || (h->opt_coo_build == 0 && (long long)slots >= kCooRowsMinSlots);
+    if (want_union && !coo_by_rows) {
+        const long long cnt = 2ll * n_src * k;
+        const int B = key_bits_for(h->n);
+        if ((rc = ensure(h, h->keys, cnt * 8, "coo keys")) || (rc = ensure(h, h->vals, cnt * 4, "coo vals")) ||
+            (rc = ensure(h, h->keys_tmp, cnt * 8, "coo keys tmp")) || (rc = ensure(h, h->vals_tmp, cnt * 4, "coo vals tmp")) ||
+            (rc = ensure(h, h->sort_temp, radix_sort_temp_bytes(cnt, 2 * B), "sort temp")))
+            return rc;
+        CK(cudaMemsetAsync(&h->d_ctr->coo_nnz, 0, sizeof(unsigned long long), st), "memset nnz");
+        CK(launch_union_pairs(out_idx, out_dist, wrow, n_src, k, out_w, B,
+                              static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), h->d_ctr,
+                              st),
+           "union");
+        h->kernel_launches++;
+        if (h->opt_profile) {
+            CK(cudaEventRecord(e1, st), "cudaEventRecord");
+            if ((rc = next_event_pair(h, &e0, &e1, kStageSort))) return rc;
+            CK(cudaEventRecord(e0, st), "cudaEventRecord");
+        }
+        int launches = 0;
+        CK(radix_sort_pairs(static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
+                            static_cast<unsigned long long*>(h->keys_tmp.p), static_cast<float*>(h->vals_tmp.p), cnt,
+                            2 * B, h->sort_temp.p, h->sort_temp.bytes, &h->d_ctr->status, st, &h->coo_keys,
+                            &h->coo_vals, &launches),
+           "radix sort");
+        h->kernel_launches += launches;
+        h->sort_launches += launches;
+        h->coo_key_bits = B;
+        h->coo_rows = false;
+        h->last_union = true;
+    } else if (want_union) {
+        const size_t slots2 = 2 * slots;
+        if ((rc = ensure(h, h->coo_scr, coo_scratch_bytes(n_src), "coo scratch")) ||
+            (rc = ensure(h, h->coo_kval, (size_t)n_src * 4, "coo kval")) ||
+            (rc = ensure(h, h->coo_mpos, slots * 4, "coo mpos")) ||
+            (rc = ensure(h, h->coo_rowoff, ((size_t)n_src + 1) * 8, "coo rowoff")) ||
+            (rc = ensure(h, h->coo_large, (size_t)n_src * 4, "coo long rows")) ||
+            (rc = ensure(h, h->coo_tcol, slots2 * 4, "coo scattered cols")) ||
+            (rc = ensure(h, h->coo_tw, slots2 * 4, "coo scattered weights")) ||
+            (rc = ensure(h, h->coo_col, slots2 * 4, "coo cols")) || (rc = ensure(h, h->coo_w, slots2 * 4, "coo weights")))
+            return rc;
+        LaunchLimits lim;
+        if ((rc = launch_limits(h->device, lim))) return rc;
+        CooArgs c{};
+        uint32_t* mcnt = nullptr;
+        coo_scratch_split(h->coo_scr.p, n_src, &mcnt, &c.ctr, &c.pub);
+        c.idx = out_idx;
+        c.w = out_w;
+        c.mpos = static_cast<uint32_t*>(h->coo_mpos.p);
+        c.kval = static_cast<int32_t*>(h->coo_kval.p);
+        c.mcnt = mcnt;
+        c.n = n_src;
+        c.k = k;
+        c.rowoff = static_cast<unsigned long long*>(h->coo_rowoff.p);
+        c.large = static_cast<int32_t*>(h->coo_large.p);
+        c.tcol = static_cast<int32_t*>(h->coo_tcol.p);
+        c.tw = static_cast<float*>(h->coo_tw.p);
+        c.ccol = static_cast<int32_t*>(h->coo_col.p);
+        c.cw = static_cast<float*>(h->coo_w.p);
+        c.status = &h->d_ctr->status;
+        CK(cudaMemsetAsync(h->coo_scr.p, 0, coo_scratch_bytes(n_src), st), "memset coo scratch");
+        CK(launch_union(out_idx, out_dist, wrow, n_src, k, out_w, mcnt,
+                        static_cast<uint32_t*>(h->coo_mpos.p), static_cast<int32_t*>(h->coo_kval.p), st),
+           "union");
+        h->kernel_launches++;
+        if (h->opt_profile) {
+            CK(cudaEventRecord(e1, st), "cudaEventRecord");
+            if ((rc = next_event_pair(h, &e0, &e1, kStageSort))) return rc;
+            CK(cudaEventRecord(e0, st), "cudaEventRecord");
+        }
+        int launches = 0;
+        CK(launch_coo_build(c, lim.sms, st, &launches), "coo build");
+        h->kernel_launches += launches;
+        h->sort_launches += launches;
+        h->coo = c;
+        h->coo_rows = true;
+        h->last_union = true;
+    }
+    if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
+    return GUMAP_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* gumap_status_string(int s) {
@@ -627,6 +786,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     if (!h) return GUMAP_OK;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();  // nothing queued may still use the buffers handed back below
+    reap(h, true);
     pool_free(h->d_rp, sizeof(int32_t) * ((size_t)h->n + 2));
     pool_free(h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz, 1));
     pool_free(h->d_identity, sizeof(int32_t) * (size_t)h->n);
@@ -635,7 +795,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     pool_free(h->d_units, sizeof(BatchUnit) * (size_t)std::max<int32_t>(h->n_units, 1));
     release(h->vslab);
     pool_free(h->d_ctr, sizeof(DeviceCounters));
-    DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->a,
+    DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
                     &h->coo_scr, &h->coo_kval, &h->coo_mpos, &h->coo_rowoff, &h->coo_large,
                     &h->coo_tcol, &h->coo_tw, &h->coo_col, &h->coo_w};
@@ -772,7 +932,7 @@ int apply_batch_plan(gumap_knn* h, int32_t max_w) {
     h->batch_smem = smem;
     h->vslab_words = slab;
     int rc;
-    if (slab > 0 && (rc = ensure(h->vslab, (size_t)slab * 4 * h->batch_grid, "batch slab"))) return rc;
+    if (slab > 0 && (rc = ensure(h, h->vslab, (size_t)slab * 4 * h->batch_grid, "batch slab"))) return rc;
     pool_free(h->d_units, sizeof(BatchUnit) * (size_t)std::max<int32_t>(h->n_units, 1));
     h->d_units = nullptr;
     h->n_units = (int32_t)sorted.size();  // sizes the block handed back by destroy
@@ -842,123 +1002,12 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
     if (n_src > 0 && (!out_idx || !out_dist || !out_w)) return fail(GUMAP_ERR_INVALID_ARG, "NULL output");
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    reap(h, false);
     h->last_n_src = n_src;
     h->last_union = false;
-    if (n_src == 0) return GUMAP_OK;
-    const int32_t* src = sources ? sources : h->d_identity;
-    const int32_t k = h->k;
-    int rc;
-    const size_t slots = (size_t)n_src * k;
-    if ((rc = ensure(h->rho, (size_t)n_src * 4, "rho")) || (rc = ensure(h->sigma, (size_t)n_src * 4, "sigma")))
-        return rc;
-    if (want_union && (rc = ensure(h->a, slots * 4, "a"))) return rc;
-
-    const int engine = pick_engine(h);
-    h->last_engine = engine;
-    if (engine == GUMAP_ENGINE_MSBFS) {
-        rc = run_msbfs(h, src, sources == nullptr, n_src, out_idx, out_dist, st);
-    } else if (engine == GUMAP_ENGINE_FRONTIER) {
-        if (h->mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
-        rc = run_frontier(h, src, n_src, out_idx, out_dist, st);
-    } else if (engine == GUMAP_ENGINE_BATCH) {
-        if (!h->batch || sources) return fail(GUMAP_ERR_INVALID_ARG, "the batched engine needs a batch handle and sources == NULL");
-        rc = run_batch(h, out_idx, out_dist, st);
-    } else {
-        return fail(GUMAP_ERR_INVALID_ARG, "engine %d not available", engine);
-    }
-    if (rc) return rc;
-
-    const float T = (float)std::log2((double)k);
-    float* a_dst = want_union ? static_cast<float*>(h->a.p) : out_w;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (h->opt_profile) {
-        if ((rc = next_event_pair(h, &e0, &e1, kStageWeights))) return rc;
-        CK(cudaEventRecord(e0, st), "cudaEventRecord");
-    }
-    CK(launch_smooth_knn(out_dist, n_src, k, T, static_cast<float*>(h->rho.p), static_cast<float*>(h->sigma.p), a_dst, st),
-       "smooth_knn");
-    h->kernel_launches++;
-    const bool coo_by_rows =
-        h->opt_coo_build == 2 || (h->opt_coo_build == 0 && (long long)slots >= kCooRowsMinSlots);
-    if (want_union && !coo_by_rows) {
-        const long long cnt = 2ll * n_src * k;
-        const int B = key_bits_for(h->n);
-        if ((rc = ensure(h->keys, cnt * 8, "coo keys")) || (rc = ensure(h->vals, cnt * 4, "coo vals")) ||
-            (rc = ensure(h->keys_tmp, cnt * 8, "coo keys tmp")) || (rc = ensure(h->vals_tmp, cnt * 4, "coo vals tmp")) ||
-            (rc = ensure(h->sort_temp, radix_sort_temp_bytes(cnt, 2 * B), "sort temp")))
-            return rc;
-        CK(cudaMemsetAsync(&h->d_ctr->coo_nnz, 0, sizeof(unsigned long long), st), "memset nnz");
-        CK(launch_union_pairs(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, B,
-                              static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), h->d_ctr,
-                              st),
-           "union");
-        h->kernel_launches++;
-        if (h->opt_profile) {
-            CK(cudaEventRecord(e1, st), "cudaEventRecord");
-            if ((rc = next_event_pair(h, &e0, &e1, kStageSort))) return rc;
-            CK(cudaEventRecord(e0, st), "cudaEventRecord");
-        }
-        int launches = 0;
-        CK(radix_sort_pairs(static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
-                            static_cast<unsigned long long*>(h->keys_tmp.p), static_cast<float*>(h->vals_tmp.p), cnt,
-                            2 * B, h->sort_temp.p, h->sort_temp.bytes, &h->d_ctr->status, st, &h->coo_keys,
-                            &h->coo_vals, &launches),
-           "radix sort");
-        h->kernel_launches += launches;
-        h->sort_launches += launches;
-        h->coo_key_bits = B;
-        h->coo_rows = false;
-        h->last_union = true;
-    } else if (want_union) {
-        const size_t slots2 = 2 * slots;
-        if ((rc = ensure(h->coo_scr, coo_scratch_bytes(n_src), "coo scratch")) ||
-            (rc = ensure(h->coo_kval, (size_t)n_src * 4, "coo kval")) ||
-            (rc = ensure(h->coo_mpos, slots * 4, "coo mpos")) ||
-            (rc = ensure(h->coo_rowoff, ((size_t)n_src + 1) * 8, "coo rowoff")) ||
-            (rc = ensure(h->coo_large, (size_t)n_src * 4, "coo long rows")) ||
-            (rc = ensure(h->coo_tcol, slots2 * 4, "coo scattered cols")) ||
-            (rc = ensure(h->coo_tw, slots2 * 4, "coo scattered weights")) ||
-            (rc = ensure(h->coo_col, slots2 * 4, "coo cols")) || (rc = ensure(h->coo_w, slots2 * 4, "coo weights")))
-            return rc;
-        LaunchLimits lim;
-        if ((rc = launch_limits(h->device, lim))) return rc;
-        CooArgs c{};
-        uint32_t* mcnt = nullptr;
-        coo_scratch_split(h->coo_scr.p, n_src, &mcnt, &c.ctr, &c.pub);
-        c.idx = out_idx;
-        c.w = out_w;
-        c.mpos = static_cast<uint32_t*>(h->coo_mpos.p);
-        c.kval = static_cast<int32_t*>(h->coo_kval.p);
-        c.mcnt = mcnt;
-        c.n = n_src;
-        c.k = k;
-        c.rowoff = static_cast<unsigned long long*>(h->coo_rowoff.p);
-        c.large = static_cast<int32_t*>(h->coo_large.p);
-        c.tcol = static_cast<int32_t*>(h->coo_tcol.p);
-        c.tw = static_cast<float*>(h->coo_tw.p);
-        c.ccol = static_cast<int32_t*>(h->coo_col.p);
-        c.cw = static_cast<float*>(h->coo_w.p);
-        c.status = &h->d_ctr->status;
-        CK(cudaMemsetAsync(h->coo_scr.p, 0, coo_scratch_bytes(n_src), st), "memset coo scratch");
-        CK(launch_union(out_idx, out_dist, static_cast<float*>(h->a.p), n_src, k, out_w, mcnt,
-                        static_cast<uint32_t*>(h->coo_mpos.p), static_cast<int32_t*>(h->coo_kval.p), st),
-           "union");
-        h->kernel_launches++;
-        if (h->opt_profile) {
-            CK(cudaEventRecord(e1, st), "cudaEventRecord");
-            if ((rc = next_event_pair(h, &e0, &e1, kStageSort))) return rc;
-            CK(cudaEventRecord(e0, st), "cudaEventRecord");
-        }
-        int launches = 0;
-        CK(launch_coo_build(c, lim.sms, st, &launches), "coo build");
-        h->kernel_launches += launches;
-        h->sort_launches += launches;
-        h->coo = c;
-        h->coo_rows = true;
-        h->last_union = true;
-    }
-    if (h->opt_profile) CK(cudaEventRecord(e1, st), "cudaEventRecord");
-    return GUMAP_OK;
+    const int rc = run_path(h, sources, n_src, out_idx, out_dist, out_w, st);
+    h->last_stream = st;
+    return rc;
 }
 
 int gumap_knn_apsp(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
@@ -977,7 +1026,11 @@ int gumap_knn_apsp(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t*
     h->last_n_src = -1;  // no weights: rho_sigma and coo refer to no run
     h->last_union = false;
     h->last_engine = GUMAP_ENGINE_MSBFS;
-    return run_msbfs(h, sources ? sources : h->d_identity, sources == nullptr, n_src, out_idx, out_dist, st, out_apsp);
+    reap(h, false);
+    const int rc = run_msbfs(h, sources ? sources : h->d_identity, sources == nullptr, n_src, out_idx, out_dist, st,
+                             out_apsp);
+    h->last_stream = st;
+    return rc;
 }
 
 int gumap_selftest_wait_timeout(int device, double limit_s) {
@@ -1007,6 +1060,7 @@ int gumap_knn_rho_sigma(gumap_knn* h, float* rho, float* sigma, void* stream) {
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     if (rho) CK(cudaMemcpyAsync(rho, h->rho.p, (size_t)h->last_n_src * 4, cudaMemcpyDeviceToDevice, st), "copy rho");
     if (sigma) CK(cudaMemcpyAsync(sigma, h->sigma.p, (size_t)h->last_n_src * 4, cudaMemcpyDeviceToDevice, st), "copy sigma");
+    h->last_stream = st;
     return GUMAP_OK;
 }
 
@@ -1021,6 +1075,7 @@ int gumap_knn_coo(gumap_knn* h, int32_t* row, int32_t* col, float* w, int64_t* n
                                static_cast<cudaStream_t>(stream)),
            "coo unpack");
     }
+    h->last_stream = static_cast<cudaStream_t>(stream);
     h->kernel_launches++;
     return GUMAP_OK;
 }

@@ -178,7 +178,9 @@ bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, 
 int32_t plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int64_t* graph_edges, const int32_t* modes,
                    std::vector<BatchUnit>& units, size_t& smem, long long& slab, int32_t max_w = kMaxBatchW);
 
-// ---- pool.cu: the handles' device-memory pool
+// ---- pool.cu: the handles' device-memory pool, and the SM count of the current device
+// (queried once per device; grid caps are multiples of it)
+int device_sm_count();
 cudaError_t pool_alloc(void** p, size_t bytes);
 void pool_free(void* p, size_t bytes);  // the device must be done with p
 void pool_trim(int device);             // device < 0: every device
@@ -210,13 +212,29 @@ cudaError_t launch_barrier_selftest(GridBarrier* bar, int32_t* status, unsigned 
 cudaError_t launch_frontier(const FrontierArgs& a, cudaStream_t s);
 
 // ---- weights.cu
-cudaError_t launch_smooth_knn(const uint16_t* dist, int32_t n_rows, int32_t k, float T, float* rho,
-                              float* sigma, float* a, cudaStream_t s);
-// Union weights into w; when mcnt != NULL also the per-slot mirror ranks
-// (mpos) and per-row counts (kval, mcnt) of the row-by-row COO build; mcnt
-// must be zero on entry.
-cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k, float* w,
-                         uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s);
+// Per-row record of the smoothing step (16 bytes, one aligned load): the key
+// of the row's last list slot (its id and distance; last_dist = kDistInf and
+// last_id = -1 when the list is padded, i.e. holds every vertex the row's
+// vertex reaches), and the row's rho and sigma. The union reads it to decide
+// whether a row lists a given vertex and to recompute that slot's weight.
+struct __align__(16) WeightRow {
+    int32_t last_id;
+    int32_t last_dist;
+    int32_t rho;
+    float sigma;
+};
+// Dynamic shared memory of one smoothing launch for k slots per row.
+size_t smooth_knn_smem_bytes(int32_t k);
+// rho, sigma [n_rows]; rec (NULL: not written; needs idx) [n_rows]; a (NULL:
+// not written) the directed weights [n_rows][k]. Rows: distances ascending,
+// padding 0xFFFF last, as every engine writes them.
+cudaError_t launch_smooth_knn(const int32_t* idx, const uint16_t* dist, int32_t n_rows, int32_t k, float T,
+                              float* rho, float* sigma, WeightRow* rec, float* a, cudaStream_t s);
+// Union weights into w from the lists and the records; when mcnt != NULL also
+// the per-slot mirror ranks (mpos) and per-row counts (kval, mcnt) of the
+// row-by-row COO build; mcnt must be zero on entry.
+cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
+                         float* w, uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s);
 
 // Below kCooRowsMinSlots slots the COO is 2 n k (key, value) pairs sorted by
 // the radix sort; the row-by-row build's long-row tails cost more there than
@@ -224,7 +242,7 @@ cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const float* 
 constexpr long long kCooRowsMinSlots = 2ll << 20;
 // Union weights into w and the 2 * n * k COO (key, value) pairs (padding
 // pairs all ones), counting the valid pairs into ctr->coo_nnz.
-cudaError_t launch_union_pairs(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k,
+cudaError_t launch_union_pairs(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
                                float* w, int key_bits, unsigned long long* keys, float* vals, DeviceCounters* ctr,
                                cudaStream_t s);
 cudaError_t launch_pairs_unpack(const unsigned long long* keys, const float* vals, int key_bits,

@@ -1050,7 +1050,7 @@ cudaError_t launch_gather_rows(const int32_t* row_ptr, const int32_t* col, const
                                int32_t* ocol, cudaStream_t s) {
     if (n_pos <= 0) return cudaSuccess;
     long long g = ((long long)n_pos * 32 + 255) / 256;
-    if (g > 152 * 16) g = 152 * 16;
+    if (g > device_sm_count() * 16ll) g = device_sm_count() * 16ll;
     gather_rows_kernel<<<(unsigned)g, 256, 0, s>>>(row_ptr, col, meta, n_pos, ocol);
     return cudaGetLastError();
 }

@@ -15,6 +15,7 @@
 #include <map>
 #include <mutex>
 #include <utility>
+#include <vector>
 
 namespace gumap {
 
@@ -44,6 +45,21 @@ size_t cap_bytes() {
 }
 
 }  // namespace
+
+int device_sm_count() {
+    static std::mutex mu;
+    static std::vector<int> cache;  // per device ordinal; 0 = not queried yet
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    if ((size_t)dev >= cache.size()) cache.resize((size_t)dev + 1, 0);
+    if (cache[(size_t)dev] <= 0) {
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 1;
+        cache[(size_t)dev] = sms;
+    }
+    return cache[(size_t)dev];
+}
 
 cudaError_t pool_alloc(void** p, size_t bytes) {
     int dev = 0;

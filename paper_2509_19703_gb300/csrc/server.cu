@@ -8,7 +8,7 @@
 // large for it alone (frontier.cu for the partial form, msbfs.cu for the full
 // form) -- and keeps up to n_streams launches in flight on separate streams.
 // Each launch runs the whole path of gumap_knn_run without the COO: BFS kNN
-// lists, rho/sigma/a (weights.cu), the fuzzy union, then ids made local to
+// lists, rho/sigma and the weights (weights.cu), the fuzzy union, then ids made local to
 // each request's graph. A host callback enqueued after the launch stamps its
 // completion. Requests that arrive meanwhile wait only for a free stream and
 // memory, so launches overlap on the device.
@@ -269,7 +269,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
     const size_t o_idx = c.take<int32_t>((size_t)N * k);
     const size_t o_dist = c.take<uint16_t>((size_t)N * k);
     const size_t o_w = c.take<float>((size_t)N * k);
-    const size_t o_a = c.take<float>((size_t)N * k);
+    const size_t o_rec = c.take<WeightRow>((size_t)N);
     const size_t o_rho = c.take<float>((size_t)N);
     const size_t o_sigma = c.take<float>((size_t)N);
     size_t o_slab = 0, o_bits = 0, o_act = 0, o_need = 0, o_cnt = 0, o_order = 0, o_queue = 0;
@@ -335,7 +335,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
     int32_t* d_rp = reinterpret_cast<int32_t*>(dptr(o_rp));
     int32_t* d_col = reinterpret_cast<int32_t*>(dptr(o_col));
     int32_t* d_offs = reinterpret_cast<int32_t*>(dptr(o_offs));
-    float* d_a = reinterpret_cast<float*>(dptr(o_a));
+    WeightRow* d_rec = reinterpret_cast<WeightRow*>(dptr(o_rec));
 
     bool ok = true;
     auto ck = [&](cudaError_t e) {
@@ -417,8 +417,9 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
     const float T = (float)std::log2((double)k);
     float* rho = reinterpret_cast<float*>(dptr(o_rho));
     float* sigma = reinterpret_cast<float*>(dptr(o_sigma));
-    ck(launch_smooth_knn(L->dist, (int32_t)N, k, T, rho, sigma, want_union ? d_a : L->w, st));
-    if (want_union) ck(launch_union(L->idx, L->dist, d_a, (int32_t)N, k, L->w, nullptr, nullptr, nullptr, st));
+    ck(launch_smooth_knn(L->idx, L->dist, (int32_t)N, k, T, rho, sigma, want_union ? d_rec : nullptr,
+                         want_union ? nullptr : L->w, st));
+    if (want_union) ck(launch_union(L->idx, L->dist, d_rec, (int32_t)N, k, L->w, nullptr, nullptr, nullptr, st));
     if (ng > 1) {
         long long grid = (N + 255) / 256;
         if (grid > 4096) grid = 4096;

@@ -200,7 +200,7 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned lon
     cudaError_t e = cudaMemsetAsync(temp, 0, need, s);
     if (e != cudaSuccess) return e;
     long long hgrid = (count + kThreads * 16 - 1) / (kThreads * 16);
-    if (hgrid > 152 * 8) hgrid = 152 * 8;
+    if (hgrid > device_sm_count() * 8) hgrid = device_sm_count() * 8;
     hist_all_kernel<<<(unsigned)hgrid, kThreads, 0, s>>>(keys, count, P, hist);
     if (launches) *launches += 1;
     unsigned long long *ka = keys, *kb = keys_tmp;

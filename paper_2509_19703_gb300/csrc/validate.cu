@@ -57,7 +57,7 @@ cudaError_t launch_validate_csr(const int32_t* row_ptr, const int32_t* col, int3
     if (e != cudaSuccess || n <= 0) return e;
     const long long work = nnz > n ? nnz : (long long)n;
     long long g = (work + 255) / 256;
-    if (g > 152 * 32) g = 152 * 32;
+    if (g > device_sm_count() * 32ll) g = device_sm_count() * 32ll;
     validate_kernel<<<(unsigned)g, 256, 0, s>>>(row_ptr, col, n, nnz, bad);
     return cudaGetLastError();
 }

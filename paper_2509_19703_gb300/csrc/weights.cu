@@ -2,23 +2,38 @@
 // union (the symmetrisation of the UMAP implementation the paper builds on,
 // Section 4.1.1).
 //
-// smooth_knn: one warp per row. rho_i is the smallest valid distance of the
-// row; sigma_i solves f(sigma) = sum_j exp(-max(0, d_ij - rho_i)/sigma) = T
-// with T = log2 k, by FP32 bisection on a bracket [0, hi] whose hi doubles
-// until f(hi) >= T. f rises strictly from c_eq = #{j : d_ij = rho_i} (sigma
-// -> 0) to kv = #valid (sigma -> inf), so a root exists iff c_eq < T < kv:
+// smooth_knn: one lane per row, 32 rows per warp. The warp stages its rows'
+// distances in shared memory (row stride an odd number of words, so the 32
+// lanes reading one slot each of their own rows hit 32 different banks);
+// then each lane finds rho_i = the smallest valid distance of its row and
+// sigma_i solving
+//     f(sigma) = sum_j exp(-max(0, d_ij - rho_i)/sigma) = T,  T = log2 k,
+// by FP32 bisection on a bracket [0, hi] whose hi doubles until f(hi) >= T.
+// Hop distances are integers, so with y = exp(-1/sigma) the sum is the
+// polynomial f = sum_L c_L y^(L - rho) over the row's levels L (c_L slots at
+// level L); it is evaluated by Horner's rule over the sorted row, one exp
+// per bisection step instead of one per slot. f rises strictly from
+// c_eq = #{j : d_ij = rho_i} (sigma -> 0) to kv = #valid (sigma -> inf), so
+// a root exists iff c_eq < T < kv:
 //   kv <= T   -> no root, sigma = +inf, every weight 1;
 //   c_eq >= T -> no root, sigma -> 0+, lifted by the floor;
 // and sigma = max(sigma*, 1e-3 * mean_j d_ij). Both decisions compare exact
 // integers with T, and log2 k is at least 0.0056 away from any integer for a
 // k that is not a power of two, so FP32 and FP64 take the same branch.
+// Besides rho and sigma each row gets a 16-byte record (WeightRow): rho,
+// sigma and the (distance, id) key of its list's last slot.
 //
 // union: w_ij = a_ij + a_ji - a_ij a_ji with a_ji = 0 when i is not in j's
 // list. Hop distances are symmetric, so i can sit in j's list only at
-// distance d_ij; the lookup binary-searches the run of row j with that
-// distance (rows are sorted by (distance, id)).
+// distance d_ij; and j's list holds the k smallest (distance, id) keys of
+// its reachable vertices, so i is in it exactly when the list is not full
+// (it then holds every vertex j reaches, i among them) or (d_ij, i) is at
+// most the key of its last slot. Both weights are recomputed from the two
+// rows' records with the same expression the directed weights use, so the
+// union needs one 16-byte record per neighbour and no search of its row.
 #include "gumap_internal.cuh"
 
+#include <climits>
 #include <math_constants.h>
 
 namespace gumap {
@@ -26,153 +41,184 @@ namespace gumap {
 namespace {
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr int kSkThreads = 128;  // 4 warps, 32 rows each
+constexpr int kSkWarps = kSkThreads / 32;
 
-__device__ __forceinline__ float warp_sum(float x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
-    return x;
+// a_ij = exp(-max(0, d - rho) / sigma) of one valid slot (d >= rho): the one
+// expression every kernel evaluates, so that weights of the same slot agree
+// bit for bit wherever they are computed.
+__device__ __forceinline__ float umap_a(int d, int rho, float sigma) {
+    return isinf(sigma) ? 1.0f : expf(-(float)(d - rho) / sigma);
 }
 
-// f(sigma) for the lane's slots, summed over the warp (every lane gets the
-// bitwise-identical total, so all lanes take the same bisection branch).
-__device__ __forceinline__ float f_sigma(const int (&dl)[kMaxK / 32], int rho, float sigma) {
+// 32-bit words per staged row: enough for k uint16 values, odd.
+__host__ __device__ __forceinline__ int sk_stride(int k) { return ((k + 1) / 2) | 1; }
+
+// f(sigma) of one row by Horner's rule over its valid slots d[0 .. kv - 1]
+// (ascending distances, d[0] = rho): going down the row, the accumulated
+// sum is multiplied by y^(gap) whenever the level drops, then the slot adds
+// 1. BFS levels are contiguous, so every gap is 1 (y itself); a wider gap
+// costs one more exp.
+__device__ __forceinline__ float f_poly(const uint16_t* __restrict__ d, int kv, int rho, float sigma) {
+    const float y = expf(-1.0f / sigma);
     float acc = 0.0f;
-#pragma unroll
-    for (int q = 0; q < kMaxK / 32; ++q) {
-        if (dl[q] >= 0) acc += expf(-(float)(dl[q] - rho) / sigma);
+    int prev = d[kv - 1];
+    for (int t = kv - 1; t >= 0; --t) {
+        const int x = d[t];
+        if (x != prev) {
+            const int gap = prev - x;
+            acc *= gap == 1 ? y : expf(-(float)gap / sigma);
+            prev = x;
+        }
+        acc += 1.0f;
     }
-    return warp_sum(acc);
+    if (prev != rho) acc *= expf(-(float)(prev - rho) / sigma);
+    return acc;
 }
 
-__global__ void __launch_bounds__(256) smooth_knn_kernel(const uint16_t* __restrict__ dist, int n_rows, int k,
-                                                         float T, float* __restrict__ rho_out,
-                                                         float* __restrict__ sigma_out, float* __restrict__ a_out) {
+// a: NULL, or [n_rows][k] directed weights (padding 0). rec: NULL, or the
+// per-row records for the union (idx then gives the last slot's id).
+__global__ void __launch_bounds__(kSkThreads) smooth_knn_kernel(const int32_t* __restrict__ idx,
+                                                                const uint16_t* __restrict__ dist, int n_rows,
+                                                                int k, float T, float* __restrict__ rho_out,
+                                                                float* __restrict__ sigma_out,
+                                                                WeightRow* __restrict__ rec, float* __restrict__ a_out) {
+    extern __shared__ uint32_t sk_smem[];
     const int lane = threadIdx.x & 31;
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    const int nloc = (k + 31) >> 5;  // slots per lane (<= 8)
-    for (long long i = warp; i < n_rows; i += nwarps) {
-        const uint16_t* d = dist + (size_t)i * k;
-        int dl[kMaxK / 32];
-        int kv = 0, dmin = 0x7FFFFFFF;
-        long long sum = 0;
-#pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) {
-            dl[q] = -1;
-            const int t = lane + 32 * q;
-            if (q < nloc && t < k) {
-                const int x = d[t];
-                if (x != kDistInf) {
-                    dl[q] = x;
-                    kv++;
-                    sum += x;
-                    dmin = min(dmin, x);
+    const int wib = threadIdx.x >> 5;
+    const int stride = sk_stride(k);
+    uint32_t* buf = sk_smem + (size_t)wib * 32 * stride;
+    const long long chunks = ((long long)n_rows + 31) / 32;
+    for (long long ch = (long long)blockIdx.x * kSkWarps + wib; ch < chunks; ch += (long long)gridDim.x * kSkWarps) {
+        const long long r0 = ch * 32;
+        const int nr = (int)min(32ll, (long long)n_rows - r0);
+        // stage the chunk's rows: slot e of the chunk is row e / k, slot e % k
+        const uint16_t* src = dist + r0 * k;
+        const int total = nr * k;
+        for (int e = lane; e < total; e += 32) {
+            const int r = e / k;
+            reinterpret_cast<uint16_t*>(buf + r * stride)[e - r * k] = src[e];
+        }
+        __syncwarp();
+        const uint16_t* my = reinterpret_cast<const uint16_t*>(buf + lane * stride);
+        int kv = 0, rho = 0;
+        float sigma = 0.0f;
+        if (lane < nr) {
+            while (kv < k && my[kv] != kDistInf) ++kv;
+            if (kv > 0) {
+                rho = my[0];
+                int sum = 0;  // at most 256 values below 2^16
+                for (int t = 0; t < kv; ++t) {
+                    rho = min(rho, (int)my[t]);
+                    sum += my[t];
                 }
+                int ceq = 0;
+                for (int t = 0; t < kv; ++t) ceq += my[t] == rho ? 1 : 0;
+                const float mean = (float)sum / (float)kv;
+                if ((float)kv <= T) {
+                    sigma = CUDART_INF_F;
+                } else if ((float)ceq >= T) {
+                    sigma = 0.0f;
+                } else {
+                    float lo = 0.0f, hi = 1.0f;
+                    for (int it = 0; it < 128 && f_poly(my, kv, rho, hi) < T; ++it) hi *= 2.0f;
+                    for (int it = 0; it < 200; ++it) {
+                        const float mid = 0.5f * (lo + hi);
+                        if (!(mid > lo && mid < hi)) break;
+                        if (f_poly(my, kv, rho, mid) > T) hi = mid;
+                        else lo = mid;
+                    }
+                    sigma = 0.5f * (lo + hi);
+                }
+                sigma = fmaxf(sigma, 1e-3f * mean);
             }
-        }
-        kv = __reduce_add_sync(kFull, kv);
-        float* arow = a_out + (size_t)i * k;
-        if (kv == 0) {
-            for (int t = lane; t < k; t += 32) arow[t] = 0.0f;
-            if (lane == 0) {
-                rho_out[i] = 0.0f;
-                sigma_out[i] = 0.0f;
-            }
-            continue;
-        }
-        const int rho = __reduce_min_sync(kFull, dmin);
-        int ceq = 0;
-#pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) ceq += (dl[q] == rho) ? 1 : 0;
-        ceq = __reduce_add_sync(kFull, ceq);
-        // sum of at most 256 uint16 values fits in int32
-        const int isum = __reduce_add_sync(kFull, (int)sum);
-        const float mean = (float)isum / (float)kv;
-        float sigma;
-        if ((float)kv <= T) {
-            sigma = CUDART_INF_F;
-        } else if ((float)ceq >= T) {
-            sigma = 0.0f;
-        } else {
-            float lo = 0.0f, hi = 1.0f;
-            for (int it = 0; it < 128 && f_sigma(dl, rho, hi) < T; ++it) hi *= 2.0f;
-            for (int it = 0; it < 200; ++it) {
-                const float mid = 0.5f * (lo + hi);
-                if (!(mid > lo && mid < hi)) break;
-                if (f_sigma(dl, rho, mid) > T) hi = mid;
-                else lo = mid;
-            }
-            sigma = 0.5f * (lo + hi);
-        }
-        sigma = fmaxf(sigma, 1e-3f * mean);
-#pragma unroll
-        for (int q = 0; q < kMaxK / 32; ++q) {
-            const int t = lane + 32 * q;
-            if (q < nloc && t < k) {
-                float v = 0.0f;
-                if (dl[q] >= 0) v = isinf(sigma) ? 1.0f : expf(-(float)(dl[q] - rho) / sigma);
-                arow[t] = v;
-            }
-        }
-        if (lane == 0) {
+            const long long i = r0 + lane;
             rho_out[i] = (float)rho;
             sigma_out[i] = sigma;
+            if (rec) {
+                WeightRow wr;
+                wr.last_dist = my[k - 1];
+                wr.last_id = wr.last_dist == kDistInf ? -1 : __ldg(idx + i * k + (k - 1));
+                wr.rho = rho;
+                wr.sigma = sigma;
+                rec[i] = wr;
+            }
         }
+        if (a_out) {  // directed weights, one row at a time, coalesced
+            for (int r = 0; r < nr; ++r) {
+                const int kv_r = __shfl_sync(kFull, kv, r);
+                const int rho_r = __shfl_sync(kFull, rho, r);
+                const float sg_r = __shfl_sync(kFull, sigma, r);
+                const uint16_t* dr = reinterpret_cast<const uint16_t*>(buf + r * stride);
+                float* ar = a_out + (r0 + r) * k;
+                for (int t = lane; t < k; t += 32) ar[t] = t < kv_r ? umap_a(dr[t], rho_r, sg_r) : 0.0f;
+            }
+        }
+        __syncwarp();
     }
 }
 
-// Position of i in row j of the lists, or -1. The row is sorted by
-// (distance, id); i can only appear at distance dij.
-__device__ __forceinline__ int find_in_row(const int32_t* __restrict__ idx, const uint16_t* __restrict__ dist,
-                                           int k, int j, int i, int dij) {
-    const int32_t* ri = idx + (size_t)j * k;
-    const uint16_t* rd = dist + (size_t)j * k;
-    // lower bound of (dij, i) in the (distance, id) order; padding sorts last
-    int lo = 0, hi = k;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        const int dm = rd[mid];
-        const int im = ri[mid];
-        const bool less = (dm < dij) || (dm == dij && im < i);
-        if (less && dm != kDistInf) lo = mid + 1;
-        else hi = mid;
-    }
-    return (lo < k && rd[lo] == dij && ri[lo] == i) ? lo : -1;
+// Is row i at distance d in row j's list, whose record is rj?
+__device__ __forceinline__ bool in_list(const WeightRow& rj, int i, int d) {
+    return rj.last_dist == (int)kDistInf || d < rj.last_dist || (d == rj.last_dist && i <= rj.last_id);
 }
 
 // One thread per slot (i, t): union weight into w. With mcnt given, also
 // what the row-by-row COO build needs (coo.cu): a slot whose target j does
 // not list i is a mirror in row j and takes the next place among j's
 // mirrors (mpos; kNoMirror otherwise), and the row's own entries are its
-// valid slots, which come first (kval).
+// valid slots, which come first (kval). Lanes of a warp that add a mirror to
+// the same row take their places with one atomic.
 __global__ void __launch_bounds__(256) union_kernel(const int32_t* __restrict__ idx,
                                                     const uint16_t* __restrict__ dist,
-                                                    const float* __restrict__ a, int n, int k,
+                                                    const WeightRow* __restrict__ rec, int n, int k,
                                                     float* __restrict__ w, uint32_t* __restrict__ mcnt,
                                                     uint32_t* __restrict__ mpos, int32_t* __restrict__ kval) {
     const long long total = (long long)n * k;
-    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < total;
-         s += (long long)gridDim.x * blockDim.x) {
-        const long long i = s / k;
-        const int t = (int)(s - i * k);
-        const int j = idx[s];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    // whole warps iterate together (the mirror places use warp collectives)
+    for (long long s0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); s0 < total; s0 += stride) {
+        const long long s = s0 + lane;
+        const bool live = s < total;
+        int j = -1, t = 0;
+        long long i = 0;
         float wv = 0.0f;
-        bool mutual = false;
-        if (j >= 0) {
-            const float aij = a[s];
-            const int p = find_in_row(idx, dist, k, j, (int)i, dist[s]);
-            const float aji = p >= 0 ? a[(size_t)j * k + p] : 0.0f;
-            mutual = p >= 0;
-            wv = aij + aji - aij * aji;
-        }
-        w[s] = wv;
-        if (mcnt) {
+        bool mirror = false;
+        if (live) {
+            i = s / k;
+            t = (int)(s - i * k);
+            j = idx[s];
             if (j >= 0) {
-                mpos[s] = mutual ? kNoMirror : atomicAdd(&mcnt[j], 1u);
-                if (t == k - 1 || idx[s + 1] < 0) kval[i] = t + 1;
-            } else {
-                mpos[s] = kNoMirror;
-                if (t == 0) kval[i] = 0;
+                const int d = dist[s];
+                const WeightRow ri = rec[i];
+                const WeightRow rj = rec[j];
+                const float aij = umap_a(d, ri.rho, ri.sigma);
+                const bool mutual = in_list(rj, (int)i, d);
+                const float aji = mutual ? umap_a(d, rj.rho, rj.sigma) : 0.0f;
+                mirror = !mutual;
+                wv = aij + aji - aij * aji;
+            }
+            w[s] = wv;
+        }
+        if (mcnt) {
+            const unsigned want = __ballot_sync(kFull, mirror);
+            uint32_t place = kNoMirror;
+            if (mirror) {
+                const unsigned peers = __match_any_sync(want, j);
+                const int leader = __ffs(peers) - 1;
+                uint32_t base = 0;
+                if (lane == leader) base = atomicAdd(&mcnt[j], (uint32_t)__popc(peers));
+                base = __shfl_sync(peers, base, leader);
+                place = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+            }
+            if (live) {
+                mpos[s] = place;
+                if (j >= 0) {
+                    if (t == k - 1 || idx[s + 1] < 0) kval[i] = t + 1;
+                } else if (t == 0) {
+                    kval[i] = 0;
+                }
             }
         }
     }
@@ -184,11 +230,11 @@ __global__ void __launch_bounds__(256) union_kernel(const int32_t* __restrict__ 
 // (i, j) always, (j, i) too when i is absent from j's list (otherwise j's own
 // slot emits it). Padding slots emit all-ones keys, which sort last.
 __global__ void __launch_bounds__(256) union_pairs_kernel(const int32_t* __restrict__ idx,
-                                                    const uint16_t* __restrict__ dist,
-                                                    const float* __restrict__ a, int n, int k,
-                                                    float* __restrict__ w, int key_bits,
-                                                    unsigned long long* __restrict__ keys,
-                                                    float* __restrict__ vals, unsigned long long* nnz) {
+                                                          const uint16_t* __restrict__ dist,
+                                                          const WeightRow* __restrict__ rec, int n, int k,
+                                                          float* __restrict__ w, int key_bits,
+                                                          unsigned long long* __restrict__ keys,
+                                                          float* __restrict__ vals, unsigned long long* nnz) {
     const long long total = (long long)n * k;
     unsigned long long local = 0;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < total;
@@ -198,10 +244,12 @@ __global__ void __launch_bounds__(256) union_pairs_kernel(const int32_t* __restr
         float wv = 0.0f;
         bool mutual = false;
         if (j >= 0) {
-            const float aij = a[s];
-            const int p = find_in_row(idx, dist, k, j, i, dist[s]);
-            const float aji = p >= 0 ? a[(size_t)j * k + p] : 0.0f;
-            mutual = p >= 0;
+            const int d = dist[s];
+            const WeightRow ri = rec[i];
+            const WeightRow rj = rec[j];
+            const float aij = umap_a(d, ri.rho, ri.sigma);
+            mutual = in_list(rj, i, d);
+            const float aji = mutual ? umap_a(d, rj.rho, rj.sigma) : 0.0f;
             wv = aij + aji - aij * aji;
         }
         w[s] = wv;
@@ -240,9 +288,9 @@ __global__ void __launch_bounds__(256) union_pairs_kernel(const int32_t* __restr
 }
 
 __global__ void pairs_unpack_kernel(const unsigned long long* __restrict__ keys, const float* __restrict__ vals,
-                                  int key_bits, const unsigned long long* __restrict__ nnz_dev, long long cap,
-                                  int32_t* __restrict__ row, int32_t* __restrict__ col, float* __restrict__ w,
-                                  int64_t* __restrict__ nnz_out) {
+                                    int key_bits, const unsigned long long* __restrict__ nnz_dev, long long cap,
+                                    int32_t* __restrict__ row, int32_t* __restrict__ col, float* __restrict__ w,
+                                    int64_t* __restrict__ nnz_out) {
     const long long nnz = (long long)*nnz_dev;
     const unsigned long long mask = (1ull << key_bits) - 1ull;
     const long long lim = nnz < cap ? nnz : cap;
@@ -265,35 +313,45 @@ int grid_for(long long work, int threads, int cap) {
 
 }  // namespace
 
-cudaError_t launch_smooth_knn(const uint16_t* dist, int32_t n_rows, int32_t k, float T, float* rho, float* sigma,
-                              float* a, cudaStream_t s) {
+size_t smooth_knn_smem_bytes(int32_t k) { return (size_t)kSkWarps * 32 * sk_stride(k) * sizeof(uint32_t); }
+
+cudaError_t launch_smooth_knn(const int32_t* idx, const uint16_t* dist, int32_t n_rows, int32_t k, float T,
+                              float* rho, float* sigma, WeightRow* rec, float* a, cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
-    const int grid = grid_for((long long)n_rows * 32, 256, 152 * 16);
-    smooth_knn_kernel<<<grid, 256, 0, s>>>(dist, n_rows, k, T, rho, sigma, a);
+    const size_t smem = smooth_knn_smem_bytes(k);
+    if (smem > 48 * 1024) {
+        static_assert(kSkWarps * 32 * 129 * 4 <= 227 * 1024, "staged rows of k = 256 fit a CTA");
+        cudaError_t e = cudaFuncSetAttribute(smooth_knn_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const long long chunks = ((long long)n_rows + 31) / 32;
+    const int grid = grid_for(chunks * 32, kSkThreads, device_sm_count() * 16);
+    smooth_knn_kernel<<<grid, kSkThreads, smem, s>>>(idx, dist, n_rows, k, T, rho, sigma, rec, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k, float* w,
-                         uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s) {
+cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
+                         float* w, uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int grid = grid_for((long long)n * k, 256, 152 * 16);
-    union_kernel<<<grid, 256, 0, s>>>(idx, dist, a, n, k, w, mcnt, mpos, kval);
+    const int grid = grid_for((long long)n * k, 256, device_sm_count() * 16);
+    union_kernel<<<grid, 256, 0, s>>>(idx, dist, rec, n, k, w, mcnt, mpos, kval);
     return cudaGetLastError();
 }
 
-cudaError_t launch_union_pairs(const int32_t* idx, const uint16_t* dist, const float* a, int32_t n, int32_t k,
+cudaError_t launch_union_pairs(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
                                float* w, int key_bits, unsigned long long* keys, float* vals, DeviceCounters* ctr,
                                cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int grid = grid_for((long long)n * k, 256, 152 * 16);
-    union_pairs_kernel<<<grid, 256, 0, s>>>(idx, dist, a, n, k, w, key_bits, keys, vals, ctr ? &ctr->coo_nnz : nullptr);
+    const int grid = grid_for((long long)n * k, 256, device_sm_count() * 16);
+    union_pairs_kernel<<<grid, 256, 0, s>>>(idx, dist, rec, n, k, w, key_bits, keys, vals,
+                                            ctr ? &ctr->coo_nnz : nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pairs_unpack(const unsigned long long* keys, const float* vals, int key_bits,
                                 const DeviceCounters* ctr, long long cap, int32_t* row, int32_t* col, float* w,
                                 int64_t* nnz_out, cudaStream_t s) {
-    const int grid = grid_for(cap > 0 ? cap : 1, 256, 152 * 16);
+    const int grid = grid_for(cap > 0 ? cap : 1, 256, device_sm_count() * 16);
     pairs_unpack_kernel<<<grid, 256, 0, s>>>(keys, vals, key_bits, &ctr->coo_nnz, cap, row, col, w, nnz_out);
     return cudaGetLastError();
 }
