@@ -13,6 +13,9 @@ Functions (see the C file for the passage each one follows):
   slot_union(idx, a)           per-slot fuzzy union a + b - ab
   coo_union(idx, a)            symmetric COO of the union, sorted (row, col)
   apsp(g)                      n x n hop-distance matrix (uint16, 0xFFFF = inf)
+  np_metric(g, X, r)           neighbourhood preservation of a drawing (Section 4.1.3)
+  stress(g, X)                 aggregated stress of a drawing (Section 4.1.3)
+  spectral_layout(...)         Laplacian eigenvectors for the initial layout (oracle/spectral.py)
 
 Parity pins: the ``-m "not gpu"`` tests check these against Floyd-Warshall,
 closed forms on grids/paths/cycles/stars/complete graphs and polynomial
@@ -39,7 +42,9 @@ def compile_source(src: str, out: str) -> str:
     """gcc-compile an oracle source file into a shared library at ``out``."""
     os.makedirs(os.path.dirname(out), exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
+    # -ffp-contract=off: every float operation rounds on its own (no fused
+    # multiply-add), so the FP32 squared distances are the IEEE single steps
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, src, "-lm"])
     os.replace(tmp, out)
     return out
 
@@ -67,6 +72,10 @@ def _bind(lib):
     lib.oracle_slot_union.restype = None
     lib.oracle_coo_union.argtypes = [vp, vp, i32, i32, vp, vp, vp]
     lib.oracle_coo_union.restype = i64
+    lib.oracle_np.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp]
+    lib.oracle_np.restype = ctypes.c_double
+    lib.oracle_stress.argtypes = [vp, vp, i32, vp, i32, vp]
+    lib.oracle_stress.restype = ctypes.c_double
     return lib
 
 
@@ -167,6 +176,32 @@ class Oracle:
             raise MemoryError
         return row[:nnz], col[:nnz], w[:nnz]
 
+    def np_metric(self, g, X, r: int = 2):
+        """(c int32 [n], inter int32 [n], total float): |N_G(v, r)|, |N_G ∩ N_D|
+        and the sum over v of |∩| / |∪| for the drawing X (float32 [n, dim])."""
+        rp, col = _csr(g)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        assert X.ndim == 2 and X.shape[0] == g.n
+        c = np.empty(max(g.n, 1), dtype=np.int32)
+        inter = np.empty(max(g.n, 1), dtype=np.int32)
+        total = self.lib.oracle_np(rp.ctypes.data, col.ctypes.data, g.n, X.ctypes.data, X.shape[1], int(r),
+                                   c.ctypes.data, inter.ctypes.data)
+        if total < 0:
+            raise ValueError("oracle_np failed")
+        return c[:g.n], inter[:g.n], float(total)
+
+    def stress(self, g, X):
+        """(stress, per-row sums float64 [n]) of the drawing X (float32 [n, dim])."""
+        rp, col = _csr(g)
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        assert X.ndim == 2 and X.shape[0] == g.n
+        rows = np.empty(max(g.n, 1), dtype=np.float64)
+        total = self.lib.oracle_stress(rp.ctypes.data, col.ctypes.data, g.n, X.ctypes.data, X.shape[1],
+                                       rows.ctypes.data)
+        if total < 0:
+            raise ValueError("oracle_stress failed")
+        return float(total), rows[:g.n]
+
     def knn_pipeline(self, g, k: int, mode: str = "full"):
         """The whole path for all vertices: idx, dist, rho, sigma, a, w, coo."""
         idx, dist = self.knn_full(g, k) if mode == "full" else self.knn_partial(g, k)
@@ -217,3 +252,11 @@ def coo_union(idx, a):
 
 def knn_pipeline(g, k, mode="full"):
     return default().knn_pipeline(g, k, mode)
+
+
+def np_metric(g, X, r=2):
+    return default().np_metric(g, X, r)
+
+
+def stress(g, X):
+    return default().stress(g, X)

@@ -17,8 +17,13 @@
  *       h_ij = exp(-(d_ij - rho_i) / sigma_i)   (Section 2.1)
  *     with sigma_i solving sum_j exp(-max(0, d_ij - rho_i)/sigma_i) = log2 k;
  *   - the fuzzy union w_ij = a_ij + a_ji - a_ij * a_ji (the symmetrisation of
- *     the UMAP implementation the paper builds on, Section 4.1.1).
- * Floating point is FP64 throughout.
+ *     the UMAP implementation the paper builds on, Section 4.1.1);
+ *   - the quality metrics of a drawing X (Section 4.1.3): neighbourhood
+ *     preservation with radius r and the aggregated stress.
+ * Floating point is FP64 throughout, except the drawing's squared distances
+ * that order N_D(v, r): those are FP32 (the layout's own precision), each
+ * step rounded to float; the file is compiled with -ffp-contract=off so no
+ * a*b+c is fused into one rounding.
  *
  * Readings taken where the paper is silent or garbled:
  *   - the source itself is not in its own list and has distance 0; the list
@@ -31,7 +36,13 @@
  *   - no root of the sigma equation: if the row has at most log2 k valid
  *     entries, sigma = +inf (all weights 1); if at least log2 k entries sit at
  *     distance rho, sigma -> 0+ and is lifted to the floor below;
- *   - sigma floor: sigma = max(sigma*, 1e-3 * mean valid distance).
+ *   - sigma floor: sigma = max(sigma*, 1e-3 * mean valid distance);
+ *   - neighbourhood preservation: N_G(v, r) excludes v; N_D(v, r) is ordered
+ *     by (FP32 squared distance, id), the squared distance being a monotone
+ *     function of the distance; a vertex with an empty N_G(v, r) counts 1
+ *     (two empty sets are identical); the printed sum over v is returned;
+ *   - stress: a pair with no connecting path contributes 1, the limit of its
+ *     term as d_ij grows without bound ("infinite" distance, Section 3.2).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -335,4 +346,110 @@ int64_t oracle_coo_union(const int32_t *idx, const double *a, int32_t n, int32_t
     }
     free(e);
     return nnz;
+}
+
+/* ------------------------------------------------------------------ */
+/* Quality metrics of a drawing (Section 4.1.3).                       */
+/* X is the drawing, float[n][dim] row-major.                          */
+/* ------------------------------------------------------------------ */
+
+/* Squared Euclidean distance of rows u and v in FP32: per coordinate the
+ * difference, its square, then the running sum in coordinate order, every
+ * step rounded to float. */
+static float sqdist32(const float *X, int32_t dim, int32_t u, int32_t v) {
+    float acc = 0.0f;
+    for (int32_t c = 0; c < dim; ++c) {
+        float dx = X[(size_t)u * dim + c] - X[(size_t)v * dim + c];
+        float sq = dx * dx;
+        acc = acc + sq;
+    }
+    return acc;
+}
+
+/* (squared distance, id): the order of the geometric neighbourhood. */
+typedef struct { float d2; int32_t v; } gd_pair;
+
+static int cmp_gd(const void *a, const void *b) {
+    const gd_pair *x = (const gd_pair *)a, *y = (const gd_pair *)b;
+    if (x->d2 < y->d2) return -1;
+    if (x->d2 > y->d2) return 1;
+    return x->v < y->v ? -1 : (x->v > y->v);
+}
+
+/*
+ * Neighbourhood preservation (Section 4.1.3). For each vertex v:
+ *   N_G(v, r) = the other vertices at hop distance at most r (BFS);
+ *   N_D(v, r) = the |N_G(v, r)| other vertices closest to v in the drawing,
+ *               by (FP32 squared distance, id);
+ * out_c[v] = |N_G(v, r)|, out_inter[v] = |N_G(v, r) ∩ N_D(v, r)|. Returns the
+ * printed sum over v of |∩| / |∪|, where |∪| = 2 |N_G| - |∩| because both
+ * sets have |N_G| elements; a vertex with an empty N_G(v, r) adds 1.
+ * Returns -1 on failure.
+ */
+double oracle_np(const int32_t *row_ptr, const int32_t *col, int32_t n, const float *X, int32_t dim, int32_t r,
+                 int32_t *out_c, int32_t *out_inter) {
+    if (n < 1 || dim < 1 || r < 1) return -1.0;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    gd_pair *geo = (gd_pair *)malloc(sizeof(gd_pair) * (size_t)n);
+    if (!dist || !queue || !geo) { free(dist); free(queue); free(geo); return -1.0; }
+    double total = 0.0;
+    for (int32_t v = 0; v < n; ++v) {
+        oracle_bfs(row_ptr, col, n, v, dist, queue);
+        int32_t c = 0;
+        for (int32_t u = 0; u < n; ++u)
+            if (u != v && dist[u] >= 0 && dist[u] <= r) c++;
+        int32_t m = 0;
+        for (int32_t u = 0; u < n; ++u)
+            if (u != v) { geo[m].d2 = sqdist32(X, dim, u, v); geo[m].v = u; m++; }
+        qsort(geo, (size_t)m, sizeof(gd_pair), cmp_gd);
+        int32_t inter = 0;
+        for (int32_t t = 0; t < c; ++t) {
+            int32_t u = geo[t].v;
+            if (dist[u] >= 0 && dist[u] <= r) inter++;
+        }
+        out_c[v] = c;
+        out_inter[v] = inter;
+        total += c == 0 ? 1.0 : (double)inter / (double)(2 * c - inter);
+    }
+    free(dist);
+    free(queue);
+    free(geo);
+    return total;
+}
+
+/*
+ * Aggregated stress (Section 4.1.3):
+ *   1/(n^2 - n) * sum over ordered pairs i != j of ((d_ij - ||X_i - X_j||) / d_ij)^2
+ * with d_ij the hop distance (BFS) and ||.|| the Euclidean distance in FP64.
+ * A pair with no connecting path adds 1. row_out (optional) receives each
+ * row's sum over j. Returns -1 on failure.
+ */
+double oracle_stress(const int32_t *row_ptr, const int32_t *col, int32_t n, const float *X, int32_t dim,
+                     double *row_out) {
+    if (n < 2 || dim < 1) return -1.0;
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    if (!dist || !queue) { free(dist); free(queue); return -1.0; }
+    double total = 0.0;
+    for (int32_t i = 0; i < n; ++i) {
+        oracle_bfs(row_ptr, col, n, i, dist, queue);
+        double row = 0.0;
+        for (int32_t j = 0; j < n; ++j) {
+            if (j == i) continue;
+            if (dist[j] < 0) { row += 1.0; continue; }
+            double sq = 0.0;
+            for (int32_t c = 0; c < dim; ++c) {
+                double dx = (double)X[(size_t)i * dim + c] - (double)X[(size_t)j * dim + c];
+                sq += dx * dx;
+            }
+            double t = ((double)dist[j] - sqrt(sq)) / (double)dist[j];
+            row += t * t;
+        }
+        if (row_out) row_out[i] = row;
+        total += row;
+    }
+    free(dist);
+    free(queue);
+    return total / ((double)n * (double)n - (double)n);
 }

@@ -13,7 +13,12 @@ Independent references used here:
   * the calibration equation sum_j exp(-(d_j - rho)/sigma) = log2 k written as
     a polynomial in x = exp(-1/sigma) and solved by numpy.roots (companion
     matrix eigenvalues), not by bisection;
-  * closed-form fuzzy-union weights on a star.
+  * closed-form fuzzy-union weights on a star;
+  * for the quality metrics of a drawing (Section 4.1.3): hand-derived
+    values (tests/golden/quality_closed_forms.json), a grid drawn on its own
+    integer coordinates (neighbourhood preservation 1 at every vertex), a path
+    on a unit line and a star on the unit circle (stress in closed form), and
+    brute force over the Floyd-Warshall matrix with numpy sorting.
 """
 from __future__ import annotations
 
@@ -26,6 +31,7 @@ import numpy as np
 from paper_2509_19703_gb300 import graphgen as gg
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "closed_forms.json")
+QUALITY_GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "quality_closed_forms.json")
 INF16 = 0xFFFF
 
 
@@ -339,7 +345,149 @@ def check_union_properties(orc):
                     assert r["w"][i, t] == 1.0
 
 
+# --------------------------------------------------------------------------
+# quality metrics of a drawing (Section 4.1.3)
+# --------------------------------------------------------------------------
+
+def _quality_graph(name, n):
+    if name == "path":
+        return gg.path(n)
+    if name == "star":
+        return gg.star(n)
+    if name == "complete":
+        return gg.complete(n)
+    if name == "two_k2":
+        return gg.disjoint_union([gg.path(2), gg.path(2)], "two_k2")
+    raise ValueError(name)
+
+
+def _closed_value(expr):
+    return {"(sqrt(2) - 1)^2 / 3": (math.sqrt(2.0) - 1.0) ** 2 / 3.0, "2/3": 2.0 / 3.0, "0": 0.0}[expr]
+
+
+def check_np_golden(orc):
+    with open(QUALITY_GOLDEN) as f:
+        cases = json.load(f)["np_cases"]
+    for case in cases:
+        g = _quality_graph(case["graph"], case["n"])
+        X = np.asarray(case["X"], dtype=np.float32)
+        c, inter, total = orc.np_metric(g, X, case["r"])
+        assert c.tolist() == case["c"], (case["why"], c.tolist())
+        assert inter.tolist() == case["inter"], (case["why"], inter.tolist())
+        assert abs(total - case["sum_num"] / case["sum_den"]) <= 1e-12, (case["why"], total)
+
+
+def check_np_grid_on_its_coordinates(orc):
+    """A grid drawn at its integer coordinates: the hop ball of radius r <= 2
+    is exactly the set of lattice points at squared distance <= r^2 (1, 2, 4
+    for r = 2; the next squared distance is 5), so N_D = N_G at every vertex."""
+    for W, H in ((7, 5), (3, 9), (12, 12), (1, 6)):
+        g = gg.grid(W, H)
+        X = np.array([[v % W, v // W] for v in range(g.n)], dtype=np.float32)
+        for r in (1, 2):
+            c, inter, total = orc.np_metric(g, X, r)
+            for v in range(g.n):
+                i, j = v // W, v % W
+                want = sum(1 for a in range(H) for b in range(W) if 0 < abs(a - i) + abs(b - j) <= r)
+                assert c[v] == want, (W, H, r, v, c[v], want)
+            assert np.array_equal(inter, c)
+            assert total == float(g.n)
+
+
+def _np_brute(g, X, r):
+    """Neighbourhood preservation from the Floyd-Warshall matrix and a numpy
+    lexicographic sort by (FP32 squared distance, id)."""
+    D = floyd_warshall(g)
+    X = np.asarray(X, dtype=np.float32)
+    n = g.n
+    cs, inters, total = [], [], 0.0
+    for v in range(n):
+        others = np.array([u for u in range(n) if u != v], dtype=np.int64)
+        ng = set(int(u) for u in others if D[v, u] <= r)
+        d2 = np.zeros(len(others), dtype=np.float32)
+        for c in range(X.shape[1]):
+            dx = (X[others, c] - X[v, c]).astype(np.float32)
+            d2 = (d2 + (dx * dx).astype(np.float32)).astype(np.float32)
+        order = others[np.lexsort((others, d2))]
+        nd = set(int(u) for u in order[:len(ng)])
+        inter = len(ng & nd)
+        cs.append(len(ng))
+        inters.append(inter)
+        total += 1.0 if not ng else inter / len(ng | nd)
+    return np.array(cs), np.array(inters), total
+
+
+def check_np_brute_force(orc):
+    rng = np.random.default_rng(77)
+    for g in tiny_graphs():
+        if g.n < 2:
+            continue
+        for layout in ("normal", "lattice"):
+            if layout == "normal":
+                X = rng.standard_normal((g.n, 2)).astype(np.float32)
+            else:  # small integer lattice: many equal distances, the tie rule decides
+                X = rng.integers(0, 4, size=(g.n, 2)).astype(np.float32)
+            for r in (1, 2, 3):
+                c, inter, total = orc.np_metric(g, X, r)
+                bc, bi, bt = _np_brute(g, X, r)
+                assert np.array_equal(c, bc) and np.array_equal(inter, bi), (g.name, layout, r)
+                assert abs(total - bt) <= 1e-12 * max(1.0, bt), (g.name, layout, r, total, bt)
+
+
+def check_stress_golden(orc):
+    with open(QUALITY_GOLDEN) as f:
+        cases = json.load(f)["stress_cases"]
+    for case in cases:
+        g = _quality_graph(case["graph"], case["n"])
+        total, rows = orc.stress(g, np.asarray(case["X"], dtype=np.float32))
+        assert abs(total - _closed_value(case["stress"])) <= 1e-14, (case["why"], total)
+        assert abs(rows.sum() / (g.n * g.n - g.n) - total) <= 1e-14
+
+
+def check_stress_star_circle(orc):
+    """Star with L leaves on the unit circle around its centre: centre-leaf
+    pairs have d = 1 = |X_i - X_j|; leaves a, b have d = 2 and chord length
+    2 sin(pi |a - b| / L), so their term is (1 - sin(pi |a - b| / L))^2."""
+    for L in (3, 5, 8):
+        g = gg.star(L + 1)
+        X = np.zeros((L + 1, 2), dtype=np.float32)
+        ang = 2.0 * math.pi * np.arange(L) / L
+        X[1:, 0] = np.cos(ang)
+        X[1:, 1] = np.sin(ang)
+        want = 0.0
+        for a in range(L):
+            for b in range(L):
+                if a != b:
+                    want += (1.0 - math.sin(math.pi * abs(a - b) / L)) ** 2
+        n = L + 1
+        want /= n * n - n
+        total, _ = orc.stress(g, X)
+        # the drawing is rounded to float32, the closed form is exact: 1e-6 covers the rounding
+        assert abs(total - want) <= 1e-6, (L, total, want)
+
+
+def check_stress_brute_force(orc):
+    rng = np.random.default_rng(78)
+    for g in tiny_graphs():
+        if g.n < 2:
+            continue
+        X = (3.0 * rng.standard_normal((g.n, 3))).astype(np.float32)
+        D = floyd_warshall(g)
+        Xd = X.astype(np.float64)
+        G = np.sqrt(((Xd[:, None, :] - Xd[None, :, :]) ** 2).sum(axis=2))
+        with np.errstate(divide="ignore", invalid="ignore"):
+            T = ((D - G) / D) ** 2
+        T[np.isinf(D)] = 1.0
+        np.fill_diagonal(T, 0.0)
+        want_rows = T.sum(axis=1)
+        want = want_rows.sum() / (g.n * g.n - g.n)
+        total, rows = orc.stress(g, X)
+        assert np.allclose(rows, want_rows, rtol=1e-12, atol=1e-12), g.name
+        assert abs(total - want) <= 1e-12 * max(1.0, want), (g.name, total, want)
+
+
 ALL_CHECKS = [check_apsp_floyd_warshall, check_knn_brute_force, check_closed_form_distances,
               check_golden_lists, check_full_equals_partial, check_partial_work,
               check_sigma_closed_forms, check_sigma_residual, check_union_star,
-              check_union_properties]
+              check_union_properties, check_np_golden, check_np_grid_on_its_coordinates,
+              check_np_brute_force, check_stress_golden, check_stress_star_circle, check_stress_brute_force]

@@ -35,6 +35,19 @@ MUTATIONS = [
     ("coo_no_transpose", "e[m].key = (int64_t)j * n + i; e[m].val = v; m++;",
      "e[m].key = (int64_t)i * n + j; e[m].val = v; m++;"),
     ("no_root_small_row", "if ((double)kv <= T) {", "if ((double)kv < 0.0) {"),
+    ("np_self_in_ball", "if (u != v && dist[u] >= 0 && dist[u] <= r) c++;", "if (dist[u] >= 0 && dist[u] <= r) c++;"),
+    ("np_radius_short", "if (u != v && dist[u] >= 0 && dist[u] <= r) c++;",
+     "if (u != v && dist[u] >= 0 && dist[u] < r) c++;"),
+    ("np_geo_tie_reversed", "return x->v < y->v ? -1 : (x->v > y->v);", "return x->v > y->v ? -1 : (x->v < y->v);"),
+    ("np_union_size", "(double)inter / (double)(2 * c - inter)", "(double)inter / (double)(2 * c)"),
+    ("np_unsquared", "float sq = dx * dx;", "float sq = dx;"),
+    ("np_empty_ball_zero", "total += c == 0 ? 1.0 :", "total += c == 0 ? 0.0 :"),
+    ("stress_normalisation", "return total / ((double)n * (double)n - (double)n);", "return total / ((double)n * (double)n);"),
+    ("stress_unreachable_zero", "if (dist[j] < 0) { row += 1.0; continue; }", "if (dist[j] < 0) { continue; }"),
+    ("stress_no_sqrt", "double t = ((double)dist[j] - sqrt(sq)) / (double)dist[j];",
+     "double t = ((double)dist[j] - sq) / (double)dist[j];"),
+    ("stress_not_relative", "double t = ((double)dist[j] - sqrt(sq)) / (double)dist[j];",
+     "double t = ((double)dist[j] - sqrt(sq));"),
 ]
 
 
