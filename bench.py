@@ -59,8 +59,13 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=15.0, help="bounded oracle sample budget")
-    p.add_argument("--only", choices=["ba20k", "er5k"], default=None,
-                   help="run one of the two graphs (for profiler captures; not a bench line)")
+    p.add_argument("--only", choices=["ba20k", "er5k", "ba1m-k15", "ba1m-k50", "grid1m-k15", "grid1m-k50"],
+                   default=None,
+                   help="run one graph of the workload (config2: ba20k, er5k; partial: ba1m-k15 ... grid1m-k50) "
+                        "for profiler captures; not a bench line")
+    p.add_argument("--frontier-build", choices=["tuned", "thread", "warp"], default="tuned",
+                   help="partial workload: the frontier engine's merge, autotuned (default) or forced "
+                        "(for profiler captures)")
     p.add_argument("--workload", choices=["config2", "partial", "batch", "serve"], default="config2",
                    help="config2: the headline line; partial: the partial form on the 1,000,000-vertex "
                         "graphs; batch: the 2000-graph batching comparison; serve: the request-stream "
@@ -375,8 +380,14 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def partial_runs():
+PARTIAL_RUN_NAMES = {"ba1m-k15": (0, 15), "ba1m-k50": (0, 50), "grid1m-k15": (1, 15), "grid1m-k50": (1, 50)}
+
+
+def partial_runs(only=None):
     from paper_2509_19703_gb300 import graphgen as gg
+    if only in PARTIAL_RUN_NAMES:
+        which, k = PARTIAL_RUN_NAMES[only]
+        return [((gg.config_ba1m, gg.config_grid1m)[which](), k)]
     graphs = [gg.config_ba1m(), gg.config_grid1m()]
     return [(g, k) for g in graphs for k in (15, 50)]
 
@@ -647,13 +658,21 @@ def run_partial_workload(args):
     from paper_2509_19703_gb300 import gumap
 
     torch.cuda.set_device(0)
-    runs = partial_runs()
+    runs = partial_runs(args.only)
     graphs = []
     for g, _ in runs:
         if not any(g is h for h in graphs):
             graphs.append(g)
     kgs = [gumap.KnnGraph.from_graph(g, k, mode=gumap.PARTIAL) for g, k in runs]
-    tuned = [kg.autotune() for kg in kgs]
+    if args.frontier_build == "tuned":
+        tuned = [kg.autotune() for kg in kgs]
+    else:  # a forced merge build, for profiler captures: no tuning runs
+        build = gumap.FRONTIER_THREAD if args.frontier_build == "thread" else gumap.FRONTIER_WARP
+        for kg in kgs:
+            kg.set_option(gumap.OPT_ENGINE, gumap.ENGINE_FRONTIER)
+            kg.set_option(gumap.OPT_FRONTIER_BUILD, build)
+        tuned = [{"engine": gumap.ENGINE_FRONTIER, "state_bytes": 0, "frontier_build": build, "best_ms": None,
+                  "default_ms": None} for _ in kgs]
     for kg in kgs:
         kg.set_option(gumap.OPT_PROFILE, 1)
     outs = [kg.alloc_outputs(g.n) for kg, (g, _) in zip(kgs, runs)]
@@ -782,7 +801,8 @@ def run_partial_workload(args):
             "config": {"workload": PARTIAL_WORKLOAD,
                        "work_edges_per_step": work_per_step, "runs": per_run,
                        "l2": "flushed (512 MB write) before each timed step",
-                       "autotuned": [{key: t[key] for key in ("engine", "state_bytes", "best_ms", "default_ms")}
+                       "autotuned": [{key: t[key] for key in ("engine", "state_bytes", "frontier_build", "best_ms",
+                                                               "default_ms")}
                                      for t in tuned]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clocks}

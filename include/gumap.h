@@ -99,6 +99,10 @@ extern "C" {
                                    1 below 2^21 slots n x k, 2 from there on), 1 = LSD radix sort of
                                    2 n k (row, col) keys, 2 = row by row (row counts, one scan,
                                    scatter, each row ranked by column); same COO either way      */
+#define GUMAP_OPT_FRONTIER_BUILD 13 /* value: the frontier engine's merge (partial form): 0 = automatic
+                                   (default: one thread per source for k <= 64, else one warp),
+                                   1 = one thread per source (k <= 64; larger k use a warp),
+                                   2 = one warp per source; same rows either way                 */
 #define GUMAP_OPT_STAGE      10 /* value: 1 (default) = each MS-BFS CTA bulk-copies its slice of the
                                    ordinary-degree rows into shared memory once per launch when
                                    every slice fits; 0 = neighbour ids always read from the CSR;
@@ -292,6 +296,7 @@ typedef struct {
     int32_t stage;
     int32_t push_div;        /* push threshold of the automatic direction (when direction == 0) */
     int32_t batch_width;     /* batch handles: widest unit in words */
+    int32_t frontier_build;  /* partial form, frontier engine: GUMAP_OPT_FRONTIER_BUILD value */
 } gumap_tune_result;
 
 /*
@@ -300,7 +305,8 @@ typedef struct {
  * sets the source-block width), pull item width, heavy-vertex degree
  * multiplier, CTAs per SM (the CTA shape: registers per thread against
  * resident warps), staging of rows in shared memory and level direction
- * with its push threshold for the full form; engine for the partial form;
+ * with its push threshold for the full form; engine and the frontier
+ * engine's merge build for the partial form;
  * the widest unit (source-block width) for batch handles (no cache). The best settings are applied to the handle and, if cache_path is
  * not NULL, appended to that JSON-lines file under a key of the graph's
  * shape class (form, k, log2 n, log2 mean degree, hub ratio); a later

@@ -1,21 +1,31 @@
-// Partial form (PartialBFS, Algorithm 4) with one warp per source.
+// Partial form (PartialBFS, Algorithm 4): one BFS per source, stopped after
+// the level at which k other vertices have been reached.
 //
 // The source's BFS proceeds level by level. The candidates of level d are
 // the neighbours of the level d-1 vertices; because every CSR row is sorted,
-// they can be enumerated in ascending id by merging those rows (one row per
-// lane, several per lane for k > 33): each round the warp takes the minimum
-// head, advances every row whose head equals it, and keeps the id if it is
-// new. A neighbour of a level d-1 vertex lies at level d-2, d-1 or d, so
-// "new" is a check against the levels d-2 and d-1 only (kept in shared
-// memory). The merge stops as soon as the list holds k entries; since ids
-// come out in ascending order, those are the k smallest by (distance, id),
-// and no adjacency beyond that point is read. A level that yields nothing
-// ends the search (the component is exhausted) and the rest of the row is
-// padding.
+// they can be enumerated in ascending id by merging those rows: each round
+// takes the minimum head, advances every row whose head equals it, and keeps
+// the id if it is new. A neighbour of a level d-1 vertex lies at level d-2,
+// d-1 or d, so "new" is a check against the levels d-2 and d-1 only; both
+// were emitted in ascending id, and the candidates of level d come out in
+// ascending id, so two pointers that only move forward decide membership.
+// The merge stops as soon as the list holds k entries; since ids come out in
+// ascending order, those are the k smallest by (distance, id), and no
+// adjacency beyond that point is read. A level that yields nothing ends the
+// search (the component is exhausted) and the rest of the row is padding.
 //
 // Every level before the last yields fewer than k new vertices, so the
-// frontier never holds more than k - 1 rows: k <= 256 means at most 8 rows
-// per lane.
+// frontier never holds more than k - 1 rows.
+//
+// Two builds of that merge:
+//   k <= 64: one THREAD per source. Its list, the frontier rows' cursors and
+//     heads live in shared memory (element q of thread t at q * T + t, so a
+//     warp reading the same element hits 32 banks); a round costs a pass over
+//     the frontier's heads in shared memory and one load when a row advances.
+//   k > 64: one WARP per source, one frontier row per lane (several per lane
+//     when the frontier exceeds 32 rows), the minimum taken by a warp
+//     reduction; the larger state of a big k would leave a thread-per-source
+//     build with too few threads per SM.
 #include "gumap_internal.cuh"
 
 #include <climits>
@@ -109,6 +119,94 @@ __global__ void __launch_bounds__(kThreads) frontier_kernel(FrontierArgs a) {
     }
 }
 
+constexpr int kThreadMaxK = 64;  // largest k of the thread-per-source build
+
+// One thread per source (k <= kThreadMaxK). Shared memory per thread, each
+// array strided by the block size T: lst[k + 1] (lst[0] the source, then the
+// vertices found, level by level, ascending within a level), and for each
+// frontier row (at most k - 1) its cursor, end and current head.
+__global__ void __launch_bounds__(128) frontier_thread_kernel(FrontierArgs a) {
+    extern __shared__ int32_t fsm[];
+    const int T = blockDim.x;
+    const int t = threadIdx.x;
+    const int k = a.k;
+    int32_t* lst = fsm + t;                  // lst[i * T]
+    int32_t* rpos = fsm + (k + 1) * T + t;   // rpos[q * T]
+    int32_t* rend = rpos + k * T;
+    int32_t* head = rend + k * T;
+    const long long stride = (long long)gridDim.x * T;
+    for (long long j = (long long)blockIdx.x * T + t; j < a.n_src; j += stride) {
+        const int s = a.src ? a.src[j] : (int)j;
+        int32_t* oi = a.out_idx + (size_t)j * k;
+        uint16_t* od = a.out_dist + (size_t)j * k;
+        int c = 0;  // vertices found so far
+        if (s < 0 || s >= a.n) {  // an invalid source is an empty row
+            atomicExch(a.status, kStatusBadSource);
+        } else {
+            lst[0] = s;
+            int fs = 0, fe = 1;  // frontier = lst[fs, fe) (level d-1)
+            int chk = 1;         // level d-2 = lst[chk, fs) (empty at d = 1)
+            for (int d = 1;; ++d) {
+                const int nf = fe - fs;
+                for (int q = 0; q < nf; ++q) {
+                    const int u = lst[(fs + q) * T];
+                    const int p0 = __ldg(a.row_ptr + u), p1 = __ldg(a.row_ptr + u + 1);
+                    rpos[q * T] = p0;
+                    rend[q * T] = p1;
+                    head[q * T] = p0 < p1 ? __ldg(a.col + p0) : INT_MAX;
+                }
+                const int lvl_start = 1 + c;
+                int pa = chk, pb = fs;  // forward pointers into levels d-2 and d-1
+                int found = 0;
+                while (c < k) {
+                    int m = INT_MAX;
+                    for (int q = 0; q < nf; ++q) m = min(m, head[q * T]);
+                    if (m == INT_MAX) break;
+                    for (int q = 0; q < nf; ++q) {
+                        if (head[q * T] == m) {
+                            const int p = rpos[q * T] + 1;
+                            rpos[q * T] = p;
+                            head[q * T] = p < rend[q * T] ? __ldg(a.col + p) : INT_MAX;
+                        }
+                    }
+                    while (pa < fs && lst[pa * T] < m) ++pa;
+                    while (pb < fe && lst[pb * T] < m) ++pb;
+                    if ((pa < fs && lst[pa * T] == m) || (pb < fe && lst[pb * T] == m)) continue;
+                    lst[(1 + c) * T] = m;
+                    oi[c] = m;
+                    od[c] = (uint16_t)d;
+                    ++c;
+                    ++found;
+                }
+                if (c >= k || found == 0) break;
+                chk = fs;  // level d-1 becomes level d-2 of the next round
+                fs = lvl_start;
+                fe = 1 + c;
+            }
+        }
+        for (int q = c; q < k; ++q) {
+            oi[q] = -1;
+            od[q] = kDistInf;
+        }
+    }
+}
+
+size_t thread_smem_bytes(int k, int threads) { return (size_t)(4 * k + 1) * threads * sizeof(int32_t); }
+
+cudaError_t launch_thread(const FrontierArgs& a, cudaStream_t s) {
+    // as many threads per CTA (a multiple of 32, at most 128) as keep the
+    // CTA's state within 48 KB
+    int threads = 128;
+    while (threads > 32 && thread_smem_bytes(a.k, threads) > 48 * 1024) threads -= 32;
+    const size_t smem = thread_smem_bytes(a.k, threads);
+    long long g = ((long long)a.n_src + threads - 1) / threads;
+    const long long cap = (long long)device_sm_count() * 64;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    frontier_thread_kernel<<<(unsigned)g, threads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int LPL>
 cudaError_t launch_lpl(const FrontierArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)kWarpsPerBlock * (a.k + 1) * sizeof(int32_t);
@@ -123,6 +221,7 @@ cudaError_t launch_lpl(const FrontierArgs& a, cudaStream_t s) {
 
 cudaError_t launch_frontier(const FrontierArgs& a, cudaStream_t s) {
     if (a.n_src <= 0) return cudaSuccess;
+    if (a.k <= kThreadMaxK && a.build != 2) return launch_thread(a, s);
     const int maxf = a.k - 1 > 0 ? a.k - 1 : 1;  // frontier rows at most k - 1 (level 1: the source)
     if (maxf <= 32) return launch_lpl<1>(a, s);
     if (maxf <= 64) return launch_lpl<2>(a, s);

@@ -230,6 +230,7 @@ struct gumap_knn {
     std::vector<int64_t> batch_edges;
     int32_t batch_width = 0;  // GUMAP_OPT_BATCH_WIDTH in force
     int opt_coo_build = 0;    // GUMAP_OPT_COO_BUILD
+    int opt_frontier_build = 0;  // GUMAP_OPT_FRONTIER_BUILD
 
     // Blocks replaced by a larger one while work queued before may still use
     // them: each goes back to the pool once an event recorded on the stream of
@@ -621,6 +622,7 @@ int run_frontier(gumap_knn* h, const int32_t* src, int32_t n_src, int32_t* out_i
     a.out_idx = out_idx;
     a.out_dist = out_dist;
     a.status = &h->d_ctr->status;
+    a.build = h->opt_frontier_build;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     int rc;
     if (h->opt_profile) {
@@ -1133,6 +1135,10 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
         case GUMAP_OPT_COO_BUILD:
             if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "COO build must be 0, 1 or 2");
             h->opt_coo_build = (int)value;
+            return GUMAP_OK;
+        case GUMAP_OPT_FRONTIER_BUILD:
+            if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "frontier build must be 0, 1 or 2");
+            h->opt_frontier_build = (int)value;
             return GUMAP_OK;
         case GUMAP_OPT_STAGE:
             if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "stage must be 0, 1 or 2");

@@ -138,6 +138,7 @@ struct FrontierArgs {
     int32_t* out_idx;
     uint16_t* out_dist;
     int32_t* status;         // set to kStatusBadSource for a source outside [0, n)
+    int32_t build;           // GUMAP_OPT_FRONTIER_BUILD: 0 automatic, 1 thread per source, 2 warp per source
 };
 
 // One unit of the batched engine: a block of sources of one graph of the

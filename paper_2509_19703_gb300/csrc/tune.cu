@@ -6,7 +6,8 @@
 // multiplier above which a vertex's items are warp-wide, then on the best of
 // those the CTAs per SM (the CTA shape), the staging of rows in shared
 // memory and the automatic level direction at three push thresholds; for the
-// partial form the engine; for batch handles the widest unit (the
+// partial form the engine and the frontier engine's merge (one thread or
+// one warp per source); for batch handles the widest unit (the
 // source-block width of the batched engine). Each candidate runs once to
 // warm up, then three times with the L2 flushed before each run; the median
 // device time decides. The winner is kept in a JSON-lines cache under a key
@@ -34,6 +35,7 @@ struct Setting {
     int stage = 1;
     int push_div = 8;
     int batch_width = 0;  // batch handles only
+    int frontier_build = 0;  // partial form, frontier engine
 };
 
 std::string shape_key(const gumap_knn_info& in) {
@@ -58,9 +60,9 @@ bool read_cache(const char* path, const std::string& key, Setting* s) {
         if (sscanf(line.c_str(),
                    "{\"key\": \"%199[^\"]\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, "
                    "\"direction\": %d, \"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, "
-                   "\"push_div\": %d, \"ms\": %lf}",
+                   "\"push_div\": %d, \"frontier_build\": %d, \"ms\": %lf}",
                    k, &t.engine, &t.pull_width, &t.heavy_mult, &t.direction, &t.state_bytes, &t.ctas_per_sm,
-                   &t.stage, &t.push_div, &ms) == 10 &&
+                   &t.stage, &t.push_div, &t.frontier_build, &ms) == 11 &&
             key == k) {
             *s = t;  // the last entry of a key wins
             found = true;
@@ -74,9 +76,10 @@ void append_cache(const char* path, const std::string& key, const Setting& s, do
     if (!f) return;
     fprintf(f,
             "{\"key\": \"%s\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, \"direction\": %d, "
-            "\"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"push_div\": %d, \"ms\": %.6f}\n",
+            "\"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"push_div\": %d, "
+            "\"frontier_build\": %d, \"ms\": %.6f}\n",
             key.c_str(), s.engine, s.pull_width, s.heavy_mult, s.direction, s.state_bytes, s.ctas_per_sm, s.stage,
-            s.push_div, ms);
+            s.push_div, s.frontier_build, ms);
     fclose(f);
 }
 
@@ -84,6 +87,9 @@ int apply(gumap_knn* h, const gumap_knn_info& in, const Setting& s) {
     int rc;
     if (in.batch) return gumap_knn_set_option(h, GUMAP_OPT_BATCH_WIDTH, s.batch_width);
     if ((rc = gumap_knn_set_option(h, GUMAP_OPT_ENGINE, s.engine))) return rc;
+    if (s.engine == GUMAP_ENGINE_FRONTIER &&
+        (rc = gumap_knn_set_option(h, GUMAP_OPT_FRONTIER_BUILD, s.frontier_build)))
+        return rc;
     if (s.engine == GUMAP_ENGINE_MSBFS || s.engine == GUMAP_ENGINE_AUTO) {
         const long long mean = in.n > 0 ? in.nnz / in.n : 0;
         if ((rc = gumap_knn_set_option(h, GUMAP_OPT_STATE_BYTES, s.state_bytes))) return rc;
@@ -132,6 +138,7 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
         res.ctas_per_sm = best.ctas_per_sm;
         res.stage = best.stage;
         res.push_div = best.push_div;
+        res.frontier_build = best.frontier_build;
         if (out) *out = res;
         return GUMAP_OK;
     }
@@ -201,9 +208,14 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
                     cands.push_back(s);
                 }
     } else {
-        Setting f;
-        f.engine = GUMAP_ENGINE_FRONTIER;
-        cands.push_back(f);
+        // the frontier engine's two merges (one thread or one warp per source)
+        for (int b : {1, 2}) {
+            if (b == 1 && in.k > 64) continue;  // the thread build covers k <= 64
+            Setting f;
+            f.engine = GUMAP_ENGINE_FRONTIER;
+            f.frontier_build = b;
+            cands.push_back(f);
+        }
         // The MS-BFS engine sweeps the bitsets of all n vertices at every
         // level of every source block: at least 3 n^2 / 8 bytes per level
         // over all blocks. Beyond 64 GB of that (n above about 400,000) one
@@ -272,6 +284,7 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
     res.stage = best.stage;
     res.push_div = best.push_div;
     res.batch_width = best.batch_width;
+    res.frontier_build = best.frontier_build;
     if (out) *out = res;
     return GUMAP_OK;
 }

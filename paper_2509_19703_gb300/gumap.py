@@ -26,7 +26,9 @@ OPT_ENGINE, OPT_BLOCK_BITS, OPT_PROFILE, OPT_STATE_BYTES, OPT_HEAVY_DEGREE = 1, 
 OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH, OPT_CTAS_PER_SM, OPT_STAGE = 6, 7, 8, 9, 10
 OPT_BATCH_WIDTH = 11
 OPT_COO_BUILD = 12
+OPT_FRONTIER_BUILD = 13
 COO_AUTO, COO_RADIX, COO_ROWS = 0, 1, 2
+FRONTIER_AUTO, FRONTIER_THREAD, FRONTIER_WARP = 0, 1, 2
 DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
 MAX_K = 256
 DIST_INF = 0xFFFF
@@ -66,7 +68,7 @@ class _Tune(ctypes.Structure):
                 ("default_ms", ctypes.c_double), ("engine", ctypes.c_int32), ("pull_width", ctypes.c_int32),
                 ("heavy_mult", ctypes.c_int32), ("direction", ctypes.c_int32), ("state_bytes", ctypes.c_int64),
                 ("ctas_per_sm", ctypes.c_int32), ("stage", ctypes.c_int32), ("push_div", ctypes.c_int32),
-                ("batch_width", ctypes.c_int32)]
+                ("batch_width", ctypes.c_int32), ("frontier_build", ctypes.c_int32)]
 
 
 class _ServerOpts(ctypes.Structure):

@@ -81,3 +81,46 @@ def test_mutation_is_caught(tmp_path, name, old, new):
     except subprocess.TimeoutExpired:
         return  # the planted mistake makes the oracle hang: caught
     assert proc.returncode != 0, f"planted mistake '{name}' passed every pin: {proc.stdout}"
+
+
+# Planted mistakes in the spectral-layout oracle (oracle/spectral.py). The
+# sign convention of each column has no mutant: the pins compare up to sign,
+# as the definition fixes eigenvectors only up to sign.
+SPECTRAL_SRC = os.path.join(os.path.dirname(oracle.__file__), "spectral.py")
+SPECTRAL_MUTATIONS = [
+    ("combinatorial_laplacian", "L_sym = np.eye(m) - (s[:, None] * Wl) * s[None, :]", "L_sym = np.diag(deg[live]) - Wl"),
+    ("no_degree_scaling", "Xl = Y * s[:, None]", "Xl = Y.copy()"),
+    ("skips_one_more", "Y = evecs[:, :take]", "Y = evecs[:, 1:take + 1]"),
+    ("trivial_kept", "Z = Z - np.outer(t, t @ Z)", "Z = Z + 0.0"),
+    ("unit_degrees", "deg = W.sum(axis=1)", "deg = (W > 0).sum(axis=1).astype(np.float64)"),
+    ("largest_instead", "evals, evecs = np.linalg.eigh(L_sym)", "evals, evecs = np.linalg.eigh(-L_sym); evals = -evals"),
+]
+
+SPECTRAL_RUNNER = """
+import importlib.util, sys
+sys.path[:0] = [{root!r}, {tests!r}]
+import spectral_pins as spins
+spec = importlib.util.spec_from_file_location("spectral_mutant", {path!r})
+mod = importlib.util.module_from_spec(spec)
+spec.loader.exec_module(mod)
+for check in spins.ALL_CHECKS:
+    try:
+        check(mod)
+    except Exception as e:
+        print("caught by", check.__name__, type(e).__name__)
+        sys.exit(3)
+print("not caught")
+"""
+
+
+@pytest.mark.parametrize("name,old,new", SPECTRAL_MUTATIONS, ids=[m[0] for m in SPECTRAL_MUTATIONS])
+def test_spectral_mutation_is_caught(tmp_path, name, old, new):
+    with open(SPECTRAL_SRC) as f:
+        text = f.read()
+    assert text.count(old) == 1, f"mutation anchor for {name} not unique"
+    mutated = tmp_path / f"spectral_{name}.py"
+    mutated.write_text(text.replace(old, new))
+    tests_dir = os.path.dirname(os.path.abspath(__file__))
+    code = SPECTRAL_RUNNER.format(root=os.path.dirname(tests_dir), tests=tests_dir, path=str(mutated))
+    proc = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=60)
+    assert proc.returncode != 0, f"planted mistake '{name}' passed every pin: {proc.stdout}"
