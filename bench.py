@@ -63,7 +63,7 @@ def parse_args():
                    default=None,
                    help="run one graph of the workload (config2: ba20k, er5k; partial: ba1m-k15 ... grid1m-k50) "
                         "for profiler captures; not a bench line")
-    p.add_argument("--frontier-build", choices=["tuned", "thread", "warp"], default="tuned",
+    p.add_argument("--frontier-build", choices=["tuned", "thread", "warp", "group"], default="tuned",
                    help="partial workload: the frontier engine's merge, autotuned (default) or forced "
                         "(for profiler captures)")
     p.add_argument("--workload", choices=["config2", "partial", "batch", "serve"], default="config2",
@@ -667,7 +667,8 @@ def run_partial_workload(args):
     if args.frontier_build == "tuned":
         tuned = [kg.autotune() for kg in kgs]
     else:  # a forced merge build, for profiler captures: no tuning runs
-        build = gumap.FRONTIER_THREAD if args.frontier_build == "thread" else gumap.FRONTIER_WARP
+        build = {"thread": gumap.FRONTIER_THREAD, "warp": gumap.FRONTIER_WARP,
+                 "group": gumap.FRONTIER_GROUP}[args.frontier_build]
         for kg in kgs:
             kg.set_option(gumap.OPT_ENGINE, gumap.ENGINE_FRONTIER)
             kg.set_option(gumap.OPT_FRONTIER_BUILD, build)

@@ -97,12 +97,14 @@ extern "C" {
                                    1..64, 0 = 64 (default); re-plans the batch, synchronises      */
 #define GUMAP_OPT_COO_BUILD  12 /* value: how gumap_knn_run builds the union COO: 0 = automatic (default:
                                    1 below 2^21 slots n x k, 2 from there on), 1 = LSD radix sort of
-                                   2 n k (row, col) keys, 2 = row by row (row counts, one scan,
-                                   scatter, each row ranked by column); same COO either way      */
+                                   2 n k (row, col) keys, 2 = row by row (the slots sorted stably by
+                                   target give each row's in-neighbours in id order; each row's own
+                                   entries ranked by column; one scan; every entry placed by
+                                   counting); same COO either way                                  */
 #define GUMAP_OPT_FRONTIER_BUILD 13 /* value: the frontier engine's merge (partial form): 0 = automatic
-                                   (default: one thread per source for k <= 64, else one warp),
-                                   1 = one thread per source (k <= 64; larger k use a warp),
-                                   2 = one warp per source; same rows either way                 */
+                                   (default: groups of lanes), 1 = one thread per source (k <= 64;
+                                   larger k use a warp), 2 = one warp per source, 3 = a group of
+                                   4 to 32 lanes per source (by k); same rows either way          */
 #define GUMAP_OPT_STAGE      10 /* value: 1 (default) = each MS-BFS CTA bulk-copies its slice of the
                                    ordinary-degree rows into shared memory once per launch when
                                    every slice fits; 0 = neighbour ids always read from the CSR;
@@ -188,8 +190,8 @@ int gumap_batch_create(gumap_knn **h, int32_t n_graphs, const int32_t *vertex_of
  * also built and kept in the handle for gumap_knn_coo(): below 2^21 slots
  * (n k) by an LSD radix sort of 2 n k (row, col) keys, from there on row by
  * row (GUMAP_OPT_COO_BUILD overrides the choice). The handle keeps that
- * build's scratch: 48 n k bytes for the radix sort (keys and values, twice),
- * 36 n k bytes for the row build. Errors:
+ * build's scratch: about 48 n k bytes for the radix sort (keys and values,
+ * twice), about 54 n k bytes for the row build. Errors:
  * INVALID_ARG (bad pointer/size, union with explicit sources), OOM, CUDA.
  * Device-side failures (a bounded wait that timed out) are reported by
  * gumap_knn_check().

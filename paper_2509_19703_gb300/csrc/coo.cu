@@ -3,26 +3,33 @@
 // Row i of the union holds (i, j) for every j in i's kNN list (its own
 // entries) and (i, j') for every j' whose list holds i while i's list does
 // not hold j' (mirrors). A column never appears twice in a row: an own
-// entry's column is in i's list, a mirror's is not. So every row is a set
-// of distinct columns and its order by column is unique.
+// entry's column is in i's list, a mirror's is not. The in-neighbours of i
+// (every j' whose list holds i) split into the mutual ones, which are own
+// entries of i too, and the mirrors; so the row is the merge of two sorted
+// lists, i's own entries by column and its in-neighbours by id, with the
+// mutual ones taken once.
 //
-//   union_kernel (weights.cu): the union weight of every slot; per row the
-//     number of own entries kval[i] and of mirrors mcnt[j] (an atomic whose
-//     old value is the mirror's rank mpos within its row).
-//   row_scan_kernel: rowoff = exclusive prefix of kval + mcnt over the rows
-//     in one pass (decoupled look-back of Merrill and Garland's single-pass
-//     scan); rows longer than kWarpRow go on a list.
-//   scatter_kernel: own entry (i, t) to rowoff[i] + t, mirror to rowoff[j] +
-//     kval[j] + mpos (column and weight; unordered within the row).
-//   row_sort_warp_kernel: rows of up to kWarpRow entries, one warp each; the
-//     place of an entry is the number of smaller columns in its row, counted
-//     against the row's columns in shared memory.
-//   row_sort_large_kernel: longer rows, one CTA each; a bitmap of the row's
-//     column range in shared memory (2^19 columns per chunk) whose popcount
-//     prefix is the place of each column.
-// Every write lands inside [0, 2 n k): row lengths are taken from kval +
-// mcnt, never from differences of rowoff, and rowoff never exceeds the true
-// prefix (a look-back that gives up leaves it short and reports TIMEOUT).
+//   union_kernel (weights.cu): the union weight of every slot, whether its
+//     target lists the row too (mut), and the slot as a transposed entry
+//     keyed (source << 32) | target.
+//   radix sort (sort.cu): a stable sort of those keys on the target's bits,
+//     so each target's in-neighbours come out together and in ascending id
+//     (the slots were in source order). No atomic counter is shared by the
+//     many rows that list a hub, and no row needs sorting afterwards.
+//   in_rows_kernel: each target's range [instart, inend) of sorted entries.
+//   own_sort_kernel: one warp per row ranks its own entries by column, and
+//     counts for each the mutual entries ranked before it (smp).
+//   row_scan_kernel: rowoff = exclusive prefix of the row lengths, own
+//     entries plus mirrors, in one pass (decoupled look-back of Merrill and
+//     Garland's single-pass scan).
+//   own_emit_kernel: an own entry of column c at rank r lands at
+//     rowoff + r + (in-neighbours below c) - (mutual own entries below c).
+//   mirror_emit_kernel: the q-th in-neighbour j' of row i, when not mutual,
+//     lands at rowoff + (q - mutual own entries below j') + (own entries
+//     below j').
+// Every write lands inside its row: row lengths come from the counts, never
+// from differences of rowoff, and rowoff never exceeds the true prefix (a
+// look-back that gives up leaves it short and reports TIMEOUT).
 #include "gumap_internal.cuh"
 
 #include <climits>
@@ -39,16 +46,7 @@ constexpr unsigned long long kFlagAggregate = 1ull << 62;  // this tile's sum on
 constexpr unsigned long long kFlagInclusive = 2ull << 62;  // sum of this tile and all before it
 constexpr unsigned long long kCountMask = (1ull << 62) - 1ull;
 constexpr unsigned long long kLookbackLimitNs = 1000ull * 1000ull * 1000ull;
-constexpr int kSortThreads = 256;
-constexpr int kWarpRow = 1024;                         // longest row sorted by one warp
-constexpr int kLargeThreads = 512;
-constexpr int kChunkWords = 16384;                     // bitmap words per chunk: 2^19 columns
-constexpr int kWordsPerWarp = kChunkWords / (kLargeThreads / 32);
-constexpr long long kChunkCols = 32ll * kChunkWords;
-constexpr size_t kLargeSmem = 2 * kChunkWords * sizeof(uint32_t);  // bitmap + word prefix: 128 KB
-
-static_assert(kWordsPerWarp % 32 == 0 && kWordsPerWarp * (kLargeThreads / 32) == kChunkWords, "chunk words per warp");
-static_assert(kWarpRow % 4 == 0, "shared rows hold whole int4 groups");
+constexpr int kOwnThreads = 256;                       // own_sort_kernel: one warp per row
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
@@ -58,6 +56,75 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 __device__ __forceinline__ long long row_len(const CooArgs& a, long long i) {
     return (long long)a.kval[i] + (long long)a.mcnt[i];
+}
+
+__device__ __forceinline__ unsigned target_of(unsigned long long key, unsigned mask) { return (unsigned)key & mask; }
+
+// Ranges of the sorted transposed entries per target: a run of equal targets
+// starts at instart and ends before inend. Padding keys (target bits all
+// ones, above every vertex) end the array.
+__global__ void __launch_bounds__(256) in_rows_kernel(CooArgs a, long long count) {
+    const unsigned mask = (1u << a.key_bits) - 1u;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        const unsigned t = target_of(a.tkey[p], mask);
+        if (t >= (unsigned)a.n) continue;
+        if (p == 0 || target_of(a.tkey[p - 1], mask) != t) a.instart[t] = (uint32_t)p;
+        if (p == count - 1 || target_of(a.tkey[p + 1], mask) != t) a.inend[t] = (uint32_t)(p + 1);
+    }
+}
+
+// One warp per row: the own entries (valid slots, distinct columns) ranked by
+// column into scol / sw, with smp = the mutual entries ranked before each;
+// the row's mutual count and its mirror count (in-degree minus mutual).
+__global__ void __launch_bounds__(kOwnThreads) own_sort_kernel(CooArgs a) {
+    __shared__ int32_t s_col[kOwnThreads / 32][kMaxK];
+    __shared__ uint8_t s_mut[kOwnThreads / 32][kMaxK];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    int32_t* sc = s_col[wib];
+    uint8_t* sm = s_mut[wib];
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const int k = a.k;
+    for (long long i = warp; i < a.n; i += nwarps) {
+        const int kv = a.kval[i];
+        const size_t base = (size_t)i * k;
+        for (int t = lane; t < kv; t += 32) sc[t] = a.idx[base + t];
+        __syncwarp();
+        int mutual = 0;
+        for (int t = lane; t < kv; t += 32) {
+            const int x = sc[t];
+            int r = 0;
+            for (int u = 0; u < kv; ++u) r += sc[u] < x ? 1 : 0;
+            const uint8_t m = a.mut[base + t];
+            a.scol[base + r] = x;
+            a.sw[base + r] = a.w[base + t];
+            sm[r] = m;
+            mutual += m;
+        }
+        __syncwarp();
+        // exclusive prefix of the mutual flags in column order, 32 ranks per step
+        int carry = 0;
+        for (int r0 = 0; r0 < kv; r0 += 32) {
+            const int r = r0 + lane;
+            const int m = r < kv ? sm[r] : 0;
+            int inc = m;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(kFull, inc, o);
+                if (lane >= o) inc += y;
+            }
+            if (r < kv) a.smp[base + r] = (uint16_t)(carry + inc - m);
+            carry += __shfl_sync(kFull, inc, 31);
+        }
+        mutual = __reduce_add_sync(kFull, mutual);
+        if (lane == 0) {
+            a.mtot[i] = mutual;
+            a.mcnt[i] = (a.inend[i] - a.instart[i]) - (uint32_t)mutual;
+        }
+        __syncwarp();  // s_col / s_mut are rewritten by the next row
+    }
 }
 
 __global__ void __launch_bounds__(kScanThreads) row_scan_kernel(CooArgs a) {
@@ -76,7 +143,6 @@ __global__ void __launch_bounds__(kScanThreads) row_scan_kernel(CooArgs a) {
         const long long r = r0 + e;
         c[e] = r < a.n ? (unsigned long long)row_len(a, r) : 0ull;
         mine += c[e];
-        if (r < a.n && c[e] > (unsigned long long)kWarpRow) a.large[atomicAdd(&a.ctr[kCooCtrLarge], 1u)] = (int32_t)r;
     }
     unsigned long long inc = mine;
 #pragma unroll
@@ -134,146 +200,59 @@ __global__ void __launch_bounds__(kScanThreads) row_scan_kernel(CooArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) scatter_kernel(CooArgs a) {
+
+// Number of in-neighbours of row i with an id below c: a binary search of the
+// row's sorted range of transposed entries (ids are the keys' high words).
+__device__ __forceinline__ uint32_t in_below(const CooArgs& a, long long i, int c) {
+    uint32_t lo = a.instart[i], hi = a.inend[i];
+    const uint32_t first = lo;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if ((int)(a.tkey[mid] >> 32) < c) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo - first;
+}
+
+// One thread per slot: own entry of rank r (column c) of row i.
+__global__ void __launch_bounds__(256) own_emit_kernel(CooArgs a) {
     const long long total = (long long)a.n * a.k;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < total;
          s += (long long)gridDim.x * blockDim.x) {
-        const int j = a.idx[s];
-        if (j < 0) continue;
         const long long i = s / a.k;
-        const long long t = s - i * a.k;
-        const float wv = a.w[s];
-        const unsigned long long po = a.rowoff[i] + (unsigned long long)t;
-        a.tcol[po] = j;
-        a.tw[po] = wv;
-        const uint32_t m = a.mpos[s];
-        if (m != kNoMirror) {
-            const unsigned long long pm = a.rowoff[j] + (unsigned long long)a.kval[j] + m;
-            a.tcol[pm] = (int32_t)i;
-            a.tw[pm] = wv;
-        }
+        const int r = (int)(s - i * a.k);
+        if (r >= a.kval[i]) continue;
+        const int c = a.scol[s];
+        const unsigned long long pos = a.rowoff[i] + (unsigned long long)r + in_below(a, i, c) - a.smp[s];
+        a.ccol[pos] = c;
+        a.cw[pos] = a.sw[s];
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) row_sort_warp_kernel(CooArgs a) {
-    __shared__ __align__(16) int32_t s_col[kSortThreads / 32][kWarpRow];
-    const int lane = threadIdx.x & 31;
-    int32_t* sc = s_col[threadIdx.x >> 5];
-    const int4* sv = reinterpret_cast<const int4*>(sc);
-    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long i = warp; i < a.n; i += nwarps) {
-        const int c = (int)min(row_len(a, i), (long long)kWarpRow + 1);
-        if (c == 0 || c > kWarpRow) continue;  // empty, or a long row (row_sort_large_kernel)
-        const unsigned long long base = a.rowoff[i];
-        const int c4 = (c + 3) & ~3;
-        for (int e = lane; e < c4; e += 32) sc[e] = e < c ? a.tcol[base + e] : INT_MAX;  // columns are < INT_MAX
-        __syncwarp();
-        for (int e0 = lane; e0 < c; e0 += 64) {
-            const int e1 = e0 + 32;
-            const int x0 = sc[e0];
-            const int x1 = e1 < c ? sc[e1] : INT_MAX;
-            int r0 = 0, r1 = 0;
-            for (int f = 0; f < (c4 >> 2); ++f) {
-                const int4 v = sv[f];
-                r0 += (v.x < x0) + (v.y < x0) + (v.z < x0) + (v.w < x0);
-                r1 += (v.x < x1) + (v.y < x1) + (v.z < x1) + (v.w < x1);
-            }
-            a.ccol[base + r0] = x0;
-            a.cw[base + r0] = a.tw[base + e0];
-            if (e1 < c) {
-                a.ccol[base + r1] = x1;
-                a.cw[base + r1] = a.tw[base + e1];
-            }
+// One thread per sorted transposed entry: the q-th in-neighbour j' of row i.
+// A mutual one is already an own entry of row i; the others are mirrors.
+__global__ void __launch_bounds__(256) mirror_emit_kernel(CooArgs a, long long count) {
+    const unsigned mask = (1u << a.key_bits) - 1u;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < count;
+         p += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long key = a.tkey[p];
+        const unsigned i = target_of(key, mask);
+        if (i >= (unsigned)a.n) continue;  // padding
+        const int src = (int)(key >> 32);
+        const size_t base = (size_t)i * a.k;
+        const int kv = a.kval[i];
+        int lo = 0, hi = kv;  // own entries of row i with a column below src
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (a.scol[base + mid] < src) lo = mid + 1;
+            else hi = mid;
         }
-        __syncwarp();
-    }
-}
-
-__global__ void __launch_bounds__(kLargeThreads) row_sort_large_kernel(CooArgs a) {
-    extern __shared__ uint32_t sm[];
-    uint32_t* bm = sm;                 // bitmap of the chunk's columns
-    uint32_t* pre = sm + kChunkWords;  // per word: set bits in the chunk's words before it
-    __shared__ int s_row, s_lo, s_hi;
-    __shared__ unsigned s_warp[kLargeThreads / 32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned nlarge = a.ctr[kCooCtrLarge];
-    for (;;) {
-        if (tid == 0) {
-            const unsigned r = atomicAdd(&a.ctr[kCooCtrNextLarge], 1u);
-            s_row = r < nlarge ? a.large[r] : -1;
-            s_lo = INT_MAX;
-            s_hi = -1;
-        }
-        __syncthreads();
-        const int i = s_row;
-        if (i < 0) break;
-        const long long c = row_len(a, i);
-        const unsigned long long base = a.rowoff[i];
-        int lo = INT_MAX, hi = -1;
-        for (long long e = tid; e < c; e += kLargeThreads) {
-            const int x = a.tcol[base + e];
-            lo = min(lo, x);
-            hi = max(hi, x);
-        }
-        lo = __reduce_min_sync(kFull, lo);
-        hi = __reduce_max_sync(kFull, hi);
-        if (lane == 0) {
-            atomicMin(&s_lo, lo);
-            atomicMax(&s_hi, hi);
-        }
-        __syncthreads();
-        const long long row_lo = s_lo, row_hi = s_hi;
-        unsigned long long run = 0;  // columns of the row in earlier chunks
-        for (long long cb = row_lo; cb <= row_hi; cb += kChunkCols) {
-            for (int wi = tid; wi < kChunkWords; wi += kLargeThreads) bm[wi] = 0u;
-            __syncthreads();
-            for (long long e = tid; e < c; e += kLargeThreads) {
-                const long long off = (long long)a.tcol[base + e] - cb;
-                if (off >= 0 && off < kChunkCols) atomicOr(&bm[off >> 5], 1u << (off & 31));
-            }
-            __syncthreads();
-            // exclusive prefix of the words' popcounts: warp w owns words
-            // [w * kWordsPerWarp, (w + 1) * kWordsPerWarp), read 32 at a time
-            // (one per lane, no bank conflict)
-            const int wb = warp * kWordsPerWarp;
-            unsigned mine = 0;
-            for (int q = 0; q < kWordsPerWarp / 32; ++q) mine += __popc(bm[wb + q * 32 + lane]);
-            mine = __reduce_add_sync(kFull, mine);
-            if (lane == 0) s_warp[warp] = mine;
-            __syncthreads();
-            unsigned carry = 0, chunk_total = 0;
-#pragma unroll
-            for (int w = 0; w < kLargeThreads / 32; ++w) {
-                if (w < warp) carry += s_warp[w];
-                chunk_total += s_warp[w];
-            }
-            for (int q = 0; q < kWordsPerWarp / 32; ++q) {
-                const unsigned pc = __popc(bm[wb + q * 32 + lane]);
-                unsigned inc = pc;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const unsigned y = __shfl_up_sync(kFull, inc, o);
-                    if (lane >= o) inc += y;
-                }
-                pre[wb + q * 32 + lane] = carry + inc - pc;
-                carry += __shfl_sync(kFull, inc, 31);
-            }
-            __syncthreads();
-            for (long long e = tid; e < c; e += kLargeThreads) {
-                const int x = a.tcol[base + e];
-                const long long off = (long long)x - cb;
-                if (off >= 0 && off < kChunkCols) {
-                    const int wi = (int)(off >> 5);
-                    const unsigned r = pre[wi] + __popc(bm[wi] & ((1u << (off & 31)) - 1u));
-                    const unsigned long long pos = base + run + r;
-                    a.ccol[pos] = x;
-                    a.cw[pos] = a.tw[base + e];
-                }
-            }
-            run += chunk_total;
-            __syncthreads();  // s_warp, bm and pre are rewritten by the next chunk
-        }
+        if (lo < kv && a.scol[base + lo] == src) continue;  // mutual: emitted as an own entry
+        const uint32_t mutual_below = lo < kv ? a.smp[base + lo] : (uint32_t)a.mtot[i];
+        const unsigned long long q = (unsigned long long)(p - a.instart[i]);
+        const unsigned long long pos = a.rowoff[i] + (q - mutual_below) + (unsigned long long)lo;
+        a.ccol[pos] = src;
+        a.cw[pos] = a.tval[p];
     }
 }
 
@@ -304,38 +283,43 @@ int grid_for(long long work, int threads, int cap) {
     return (int)g;
 }
 
+size_t pad16(size_t b) { return (b + 15) & ~(size_t)15; }
+
 }  // namespace
 
 size_t coo_scratch_bytes(int32_t n) {
-    const size_t tiles = (size_t)((n > 0 ? n : 1) + kScanTile - 1) / kScanTile;
-    const size_t mcnt = ((size_t)(n > 0 ? n : 1) * sizeof(uint32_t) + 15) & ~(size_t)15;
-    return mcnt + kCooCtrWords * sizeof(uint32_t) + tiles * sizeof(unsigned long long);
+    const size_t nn = (size_t)(n > 0 ? n : 1);
+    const size_t tiles = (nn + kScanTile - 1) / kScanTile;
+    return 2 * pad16(nn * sizeof(uint32_t)) + pad16(kCooCtrWords * sizeof(uint32_t)) +
+           tiles * sizeof(unsigned long long);
 }
 
-void coo_scratch_split(void* scratch, int32_t n, uint32_t** mcnt, uint32_t** ctr, unsigned long long** pub) {
-    const size_t m = ((size_t)(n > 0 ? n : 1) * sizeof(uint32_t) + 15) & ~(size_t)15;
+void coo_scratch_split(void* scratch, int32_t n, uint32_t** instart, uint32_t** inend, uint32_t** ctr,
+                       unsigned long long** pub) {
+    const size_t m = pad16((size_t)(n > 0 ? n : 1) * sizeof(uint32_t));
     char* p = static_cast<char*>(scratch);
-    *mcnt = reinterpret_cast<uint32_t*>(p);
-    *ctr = reinterpret_cast<uint32_t*>(p + m);
-    *pub = reinterpret_cast<unsigned long long*>(p + m + kCooCtrWords * sizeof(uint32_t));
+    *instart = reinterpret_cast<uint32_t*>(p);
+    *inend = reinterpret_cast<uint32_t*>(p + m);
+    *ctr = reinterpret_cast<uint32_t*>(p + 2 * m);
+    *pub = reinterpret_cast<unsigned long long*>(p + 2 * m + pad16(kCooCtrWords * sizeof(uint32_t)));
 }
 
 cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* launches) {
     if (a.n <= 0) return cudaSuccess;
-    const long long tiles = ((long long)a.n + kScanTile - 1) / kScanTile;
-    row_scan_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a);
+    const long long slots = (long long)a.n * a.k;
+    in_rows_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a, slots);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    scatter_kernel<<<grid_for((long long)a.n * a.k, 256, sms * 16), 256, 0, s>>>(a);
+    own_sort_kernel<<<grid_for((long long)a.n * 32, kOwnThreads, sms * 8), kOwnThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    row_sort_warp_kernel<<<grid_for((long long)a.n * 32, kSortThreads, sms * 8), kSortThreads, 0, s>>>(a);
+    const long long tiles = ((long long)a.n + kScanTile - 1) / kScanTile;
+    row_scan_kernel<<<(unsigned)tiles, kScanThreads, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(row_sort_large_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)kLargeSmem)) != cudaSuccess)
-        return e;
-    row_sort_large_kernel<<<sms, kLargeThreads, kLargeSmem, s>>>(a);
+    own_emit_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (launches) *launches += 4;
+    mirror_emit_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a, slots);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (launches) *launches += 5;
     return cudaSuccess;
 }
 

@@ -203,7 +203,8 @@ struct gumap_knn {
     // per-run scratch
     DevBuf rho, sigma, wrow;  // wrow: the smoothing step's per-row records (union weights)
     DevBuf keys, vals, keys_tmp, vals_tmp, sort_temp;  // COO as radix-sorted (key, value) pairs
-    DevBuf coo_scr, coo_kval, coo_mpos, coo_rowoff, coo_large, coo_tcol, coo_tw, coo_col, coo_w;  // COO by rows
+    // COO by rows (with the radix build's key and value buffers for the transposed entries)
+    DevBuf coo_scr, coo_kval, coo_mcnt, coo_mtot, coo_mut, coo_scol, coo_sw, coo_smp, coo_rowoff, coo_col, coo_w;
 
     // last run
     int32_t last_n_src = -1;
@@ -309,8 +310,8 @@ size_t held_bytes(const gumap_knn* h) {
     for (const auto& c : h->cuts) t += (size_t)(c.grid + 1) * 4 + c.meta_bytes + c.ocol_bytes;
     const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                           &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
-                          &h->coo_scr, &h->coo_kval, &h->coo_mpos, &h->coo_rowoff, &h->coo_large,
-                          &h->coo_tcol, &h->coo_tw, &h->coo_col, &h->coo_w};
+                          &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_mtot, &h->coo_mut,
+                          &h->coo_scol, &h->coo_sw, &h->coo_smp, &h->coo_rowoff, &h->coo_col, &h->coo_w};
     for (const DevBuf* b : bs) t += b->bytes;
     return t;
 }
@@ -712,37 +713,47 @@ int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_i
         h->last_union = true;
     } else if (want_union) {
         const size_t slots2 = 2 * slots;
+        const int TB = key_bits_for(n_src + 1);  // target bits of a transposed key: 2^TB > n
         if ((rc = ensure(h, h->coo_scr, coo_scratch_bytes(n_src), "coo scratch")) ||
             (rc = ensure(h, h->coo_kval, (size_t)n_src * 4, "coo kval")) ||
-            (rc = ensure(h, h->coo_mpos, slots * 4, "coo mpos")) ||
+            (rc = ensure(h, h->coo_mcnt, (size_t)n_src * 4, "coo mirror counts")) ||
+            (rc = ensure(h, h->coo_mtot, (size_t)n_src * 4, "coo mutual counts")) ||
+            (rc = ensure(h, h->coo_mut, slots, "coo mutual flags")) ||
+            (rc = ensure(h, h->keys, slots * 8, "coo transposed keys")) ||
+            (rc = ensure(h, h->vals, slots * 4, "coo transposed weights")) ||
+            (rc = ensure(h, h->keys_tmp, slots * 8, "coo keys tmp")) ||
+            (rc = ensure(h, h->vals_tmp, slots * 4, "coo vals tmp")) ||
+            (rc = ensure(h, h->sort_temp, radix_sort_temp_bytes((long long)slots, TB), "sort temp")) ||
+            (rc = ensure(h, h->coo_scol, slots * 4, "coo own columns")) ||
+            (rc = ensure(h, h->coo_sw, slots * 4, "coo own weights")) ||
+            (rc = ensure(h, h->coo_smp, slots * 2, "coo mutual prefix")) ||
             (rc = ensure(h, h->coo_rowoff, ((size_t)n_src + 1) * 8, "coo rowoff")) ||
-            (rc = ensure(h, h->coo_large, (size_t)n_src * 4, "coo long rows")) ||
-            (rc = ensure(h, h->coo_tcol, slots2 * 4, "coo scattered cols")) ||
-            (rc = ensure(h, h->coo_tw, slots2 * 4, "coo scattered weights")) ||
             (rc = ensure(h, h->coo_col, slots2 * 4, "coo cols")) || (rc = ensure(h, h->coo_w, slots2 * 4, "coo weights")))
             return rc;
         LaunchLimits lim;
         if ((rc = launch_limits(h->device, lim))) return rc;
         CooArgs c{};
-        uint32_t* mcnt = nullptr;
-        coo_scratch_split(h->coo_scr.p, n_src, &mcnt, &c.ctr, &c.pub);
+        coo_scratch_split(h->coo_scr.p, n_src, &c.instart, &c.inend, &c.ctr, &c.pub);
         c.idx = out_idx;
         c.w = out_w;
-        c.mpos = static_cast<uint32_t*>(h->coo_mpos.p);
+        c.mut = static_cast<uint8_t*>(h->coo_mut.p);
         c.kval = static_cast<int32_t*>(h->coo_kval.p);
-        c.mcnt = mcnt;
         c.n = n_src;
         c.k = k;
+        c.key_bits = TB;
+        c.mcnt = static_cast<uint32_t*>(h->coo_mcnt.p);
+        c.mtot = static_cast<int32_t*>(h->coo_mtot.p);
+        c.scol = static_cast<int32_t*>(h->coo_scol.p);
+        c.sw = static_cast<float*>(h->coo_sw.p);
+        c.smp = static_cast<uint16_t*>(h->coo_smp.p);
         c.rowoff = static_cast<unsigned long long*>(h->coo_rowoff.p);
-        c.large = static_cast<int32_t*>(h->coo_large.p);
-        c.tcol = static_cast<int32_t*>(h->coo_tcol.p);
-        c.tw = static_cast<float*>(h->coo_tw.p);
         c.ccol = static_cast<int32_t*>(h->coo_col.p);
         c.cw = static_cast<float*>(h->coo_w.p);
         c.status = &h->d_ctr->status;
         CK(cudaMemsetAsync(h->coo_scr.p, 0, coo_scratch_bytes(n_src), st), "memset coo scratch");
-        CK(launch_union(out_idx, out_dist, wrow, n_src, k, out_w, mcnt,
-                        static_cast<uint32_t*>(h->coo_mpos.p), static_cast<int32_t*>(h->coo_kval.p), st),
+        CK(launch_union(out_idx, out_dist, wrow, n_src, k, out_w, static_cast<uint8_t*>(h->coo_mut.p),
+                        static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
+                        static_cast<int32_t*>(h->coo_kval.p), st),
            "union");
         h->kernel_launches++;
         if (h->opt_profile) {
@@ -751,6 +762,15 @@ int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_i
             CK(cudaEventRecord(e0, st), "cudaEventRecord");
         }
         int launches = 0;
+        unsigned long long* tkey = nullptr;
+        float* tval = nullptr;
+        CK(radix_sort_pairs(static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
+                            static_cast<unsigned long long*>(h->keys_tmp.p), static_cast<float*>(h->vals_tmp.p),
+                            (long long)slots, TB, h->sort_temp.p, h->sort_temp.bytes, &h->d_ctr->status, st, &tkey,
+                            &tval, &launches),
+           "transpose sort");
+        c.tkey = tkey;
+        c.tval = tval;
         CK(launch_coo_build(c, lim.sms, st, &launches), "coo build");
         h->kernel_launches += launches;
         h->sort_launches += launches;
@@ -799,8 +819,8 @@ int gumap_knn_destroy(gumap_knn* h) {
     pool_free(h->d_ctr, sizeof(DeviceCounters));
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
-                    &h->coo_scr, &h->coo_kval, &h->coo_mpos, &h->coo_rowoff, &h->coo_large,
-                    &h->coo_tcol, &h->coo_tw, &h->coo_col, &h->coo_w};
+                    &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_mtot, &h->coo_mut,
+                    &h->coo_scol, &h->coo_sw, &h->coo_smp, &h->coo_rowoff, &h->coo_col, &h->coo_w};
     for (DevBuf* b : bs) release(*b);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -1137,7 +1157,7 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             h->opt_coo_build = (int)value;
             return GUMAP_OK;
         case GUMAP_OPT_FRONTIER_BUILD:
-            if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "frontier build must be 0, 1 or 2");
+            if (value < 0 || value > 3) return fail(GUMAP_ERR_INVALID_ARG, "frontier build must be 0, 1, 2 or 3");
             h->opt_frontier_build = (int)value;
             return GUMAP_OK;
         case GUMAP_OPT_STAGE:

@@ -138,7 +138,7 @@ struct FrontierArgs {
     int32_t* out_idx;
     uint16_t* out_dist;
     int32_t* status;         // set to kStatusBadSource for a source outside [0, n)
-    int32_t build;           // GUMAP_OPT_FRONTIER_BUILD: 0 automatic, 1 thread per source, 2 warp per source
+    int32_t build;           // GUMAP_OPT_FRONTIER_BUILD: 0 automatic (3), 1 thread, 2 warp, 3 group of lanes per source
 };
 
 // One unit of the batched engine: a block of sources of one graph of the
@@ -231,11 +231,13 @@ size_t smooth_knn_smem_bytes(int32_t k);
 // padding 0xFFFF last, as every engine writes them.
 cudaError_t launch_smooth_knn(const int32_t* idx, const uint16_t* dist, int32_t n_rows, int32_t k, float T,
                               float* rho, float* sigma, WeightRow* rec, float* a, cudaStream_t s);
-// Union weights into w from the lists and the records; when mcnt != NULL also
-// the per-slot mirror ranks (mpos) and per-row counts (kval, mcnt) of the
-// row-by-row COO build; mcnt must be zero on entry.
+// Union weights into w from the lists and the records; when tkey != NULL also
+// what the row-by-row COO build needs: per slot the mutual flag (mut) and the
+// transposed entry (key (i << 32) | j, value w; padding ~0), per row the
+// valid-slot count (kval).
 cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
-                         float* w, uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s);
+                         float* w, uint8_t* mut, unsigned long long* tkey, float* tval, int32_t* kval,
+                         cudaStream_t s);
 
 // Below kCooRowsMinSlots slots the COO is 2 n k (key, value) pairs sorted by
 // the radix sort; the row-by-row build's long-row tails cost more there than
@@ -259,34 +261,42 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned lon
                              int* launches);
 
 // ---- coo.cu: the fuzzy union as a COO sorted by (row, col), built by rows
-constexpr uint32_t kNoMirror = 0xFFFFFFFFu;  // mpos of a slot that emits no mirror
 constexpr int kCooCtrTile = 0;               // tile counter of the row scan
-constexpr int kCooCtrLarge = 1;              // rows on the long-row list
-constexpr int kCooCtrNextLarge = 2;          // next long row to sort
 constexpr int kCooCtrWords = 4;
 
 struct CooArgs {
     const int32_t* idx;          // kNN lists [n][k], valid slots first
     const float* w;              // union weight per slot [n][k]
-    const uint32_t* mpos;        // per slot: place of its mirror among the target row's mirrors, or kNoMirror
+    const uint8_t* mut;          // per slot: 1 when the target's list holds the row too
     const int32_t* kval;         // per row: valid slots (own entries)
-    const uint32_t* mcnt;        // per row: mirrors received
     int32_t n;
     int32_t k;
+    // transposed entries sorted by target, stably (so by source within a
+    // target): key (source << 32) | target, value the slot's weight; padding
+    // keys (~0) last
+    const unsigned long long* tkey;
+    const float* tval;
+    int32_t key_bits;            // the target's bits in a key: 2^key_bits > n
+    uint32_t* instart;           // [n] first sorted position of each target's entries (zeroed)
+    uint32_t* inend;             // [n] one past its last (zeroed): in-degree = inend - instart
+    uint32_t* mcnt;              // [n] mirrors of each row: in-degree minus mutual own entries
+    int32_t* mtot;               // [n] mutual own entries of each row
+    int32_t* scol;               // [n][k] own entries sorted by column
+    float* sw;                   // their weights
+    uint16_t* smp;               // per sorted own entry: mutual entries before it in that order
     unsigned long long* rowoff;  // [n + 1] first entry of each row; rowoff[n] = nnz
     unsigned long long* pub;     // look-back words of the row scan [tiles], zeroed
     uint32_t* ctr;               // [kCooCtrWords], zeroed
-    int32_t* large;              // [n] rows too long for one warp
-    int32_t* tcol;               // scattered rows [2 n k] (columns, unordered in a row)
-    float* tw;
-    int32_t* ccol;               // sorted rows [2 n k]
+    int32_t* ccol;               // the COO rows [<= 2 n k]: columns ascending in each row
     float* cw;
     int32_t* status;             // kStatusTimeout if a look-back wait gives up
 };
-// One zeroed block per run: mcnt [n] (16-byte padded), ctr, pub.
+// One zeroed block per run: instart, inend (each [n], 16-byte padded), ctr, pub.
 size_t coo_scratch_bytes(int32_t n);
-void coo_scratch_split(void* scratch, int32_t n, uint32_t** mcnt, uint32_t** ctr, unsigned long long** pub);
-// Row scan, scatter, warp-row sort, long-row sort (4 launches) after launch_union.
+void coo_scratch_split(void* scratch, int32_t n, uint32_t** instart, uint32_t** inend, uint32_t** ctr,
+                       unsigned long long** pub);
+// After launch_union and the stable sort of its transposed entries: target
+// ranges, own-row sort, row scan, own entries, mirrors (5 launches).
 cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* launches);
 // Rows, columns and weights of the sorted COO (up to cap entries) and nnz.
 cudaError_t launch_coo_unpack(const CooArgs& a, long long cap, int32_t* row, int32_t* col, float* w,

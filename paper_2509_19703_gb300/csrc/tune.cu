@@ -208,8 +208,8 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
                     cands.push_back(s);
                 }
     } else {
-        // the frontier engine's two merges (one thread or one warp per source)
-        for (int b : {1, 2}) {
+        // the frontier engine's merges (a group of lanes, one thread or one warp per source)
+        for (int b : {3, 1, 2}) {
             if (b == 1 && in.k > 64) continue;  // the thread build covers k <= 64
             Setting f;
             f.engine = GUMAP_ENGINE_FRONTIER;

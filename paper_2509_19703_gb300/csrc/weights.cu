@@ -163,62 +163,44 @@ __device__ __forceinline__ bool in_list(const WeightRow& rj, int i, int d) {
     return rj.last_dist == (int)kDistInf || d < rj.last_dist || (d == rj.last_dist && i <= rj.last_id);
 }
 
-// One thread per slot (i, t): union weight into w. With mcnt given, also
-// what the row-by-row COO build needs (coo.cu): a slot whose target j does
-// not list i is a mirror in row j and takes the next place among j's
-// mirrors (mpos; kNoMirror otherwise), and the row's own entries are its
-// valid slots, which come first (kval). Lanes of a warp that add a mirror to
-// the same row take their places with one atomic.
+// One thread per slot (i, t): union weight into w. With tkey given, also
+// what the row-by-row COO build needs (coo.cu): per slot whether the target
+// lists i too (mut), and the transposed entry (i -> j seen from row j) as the
+// key (i << 32) | j with the slot's weight (tval); padding slots get the key
+// ~0, which sorts after every target. Per row the count of valid slots, which
+// come first (kval).
 __global__ void __launch_bounds__(256) union_kernel(const int32_t* __restrict__ idx,
                                                     const uint16_t* __restrict__ dist,
                                                     const WeightRow* __restrict__ rec, int n, int k,
-                                                    float* __restrict__ w, uint32_t* __restrict__ mcnt,
-                                                    uint32_t* __restrict__ mpos, int32_t* __restrict__ kval) {
+                                                    float* __restrict__ w, uint8_t* __restrict__ mut,
+                                                    unsigned long long* __restrict__ tkey,
+                                                    float* __restrict__ tval, int32_t* __restrict__ kval) {
     const long long total = (long long)n * k;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const int lane = threadIdx.x & 31;
-    // whole warps iterate together (the mirror places use warp collectives)
-    for (long long s0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31); s0 < total; s0 += stride) {
-        const long long s = s0 + lane;
-        const bool live = s < total;
-        int j = -1, t = 0;
-        long long i = 0;
+    for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < total;
+         s += (long long)gridDim.x * blockDim.x) {
+        const long long i = s / k;
+        const int t = (int)(s - i * k);
+        const int j = idx[s];
         float wv = 0.0f;
-        bool mirror = false;
-        if (live) {
-            i = s / k;
-            t = (int)(s - i * k);
-            j = idx[s];
-            if (j >= 0) {
-                const int d = dist[s];
-                const WeightRow ri = rec[i];
-                const WeightRow rj = rec[j];
-                const float aij = umap_a(d, ri.rho, ri.sigma);
-                const bool mutual = in_list(rj, (int)i, d);
-                const float aji = mutual ? umap_a(d, rj.rho, rj.sigma) : 0.0f;
-                mirror = !mutual;
-                wv = aij + aji - aij * aji;
-            }
-            w[s] = wv;
+        bool mutual = false;
+        if (j >= 0) {
+            const int d = dist[s];
+            const WeightRow ri = rec[i];
+            const WeightRow rj = rec[j];
+            const float aij = umap_a(d, ri.rho, ri.sigma);
+            mutual = in_list(rj, (int)i, d);
+            const float aji = mutual ? umap_a(d, rj.rho, rj.sigma) : 0.0f;
+            wv = aij + aji - aij * aji;
         }
-        if (mcnt) {
-            const unsigned want = __ballot_sync(kFull, mirror);
-            uint32_t place = kNoMirror;
-            if (mirror) {
-                const unsigned peers = __match_any_sync(want, j);
-                const int leader = __ffs(peers) - 1;
-                uint32_t base = 0;
-                if (lane == leader) base = atomicAdd(&mcnt[j], (uint32_t)__popc(peers));
-                base = __shfl_sync(peers, base, leader);
-                place = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
-            }
-            if (live) {
-                mpos[s] = place;
-                if (j >= 0) {
-                    if (t == k - 1 || idx[s + 1] < 0) kval[i] = t + 1;
-                } else if (t == 0) {
-                    kval[i] = 0;
-                }
+        w[s] = wv;
+        if (tkey) {
+            mut[s] = mutual ? 1 : 0;
+            tkey[s] = j >= 0 ? (((unsigned long long)i << 32) | (unsigned long long)j) : ~0ull;
+            tval[s] = wv;
+            if (j >= 0) {
+                if (t == k - 1 || idx[s + 1] < 0) kval[i] = t + 1;
+            } else if (t == 0) {
+                kval[i] = 0;
             }
         }
     }
@@ -331,10 +313,11 @@ cudaError_t launch_smooth_knn(const int32_t* idx, const uint16_t* dist, int32_t 
 }
 
 cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
-                         float* w, uint32_t* mcnt, uint32_t* mpos, int32_t* kval, cudaStream_t s) {
+                         float* w, uint8_t* mut, unsigned long long* tkey, float* tval, int32_t* kval,
+                         cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int grid = grid_for((long long)n * k, 256, device_sm_count() * 16);
-    union_kernel<<<grid, 256, 0, s>>>(idx, dist, rec, n, k, w, mcnt, mpos, kval);
+    union_kernel<<<grid, 256, 0, s>>>(idx, dist, rec, n, k, w, mut, tkey, tval, kval);
     return cudaGetLastError();
 }
 

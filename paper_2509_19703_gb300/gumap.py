@@ -28,7 +28,7 @@ OPT_BATCH_WIDTH = 11
 OPT_COO_BUILD = 12
 OPT_FRONTIER_BUILD = 13
 COO_AUTO, COO_RADIX, COO_ROWS = 0, 1, 2
-FRONTIER_AUTO, FRONTIER_THREAD, FRONTIER_WARP = 0, 1, 2
+FRONTIER_AUTO, FRONTIER_THREAD, FRONTIER_WARP, FRONTIER_GROUP = 0, 1, 2, 3
 DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
 MAX_K = 256
 DIST_INF = 0xFFFF

@@ -55,6 +55,17 @@ def test_zoo_partial_both_engines(g, k):
     assert_parity(run_gpu(g, k, "partial", engine=MSBFS), ref, f"{g.name} partial/msbfs k={k}")
 
 
+@pytest.mark.parametrize("build", [gumap.FRONTIER_GROUP, gumap.FRONTIER_THREAD, gumap.FRONTIER_WARP],
+                         ids=["group", "thread", "warp"])
+@pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
+def test_zoo_partial_frontier_builds(g, k, build):
+    """Every merge build of the frontier engine (a group of lanes, one
+    thread, one warp per source) gives the oracle's rows."""
+    ref = oracle_ref(g, k, "partial")
+    assert_parity(run_gpu(g, k, "partial", engine=FRONTIER, frontier_build=build), ref,
+                  f"{g.name} partial/frontier build {build} k={k}")
+
+
 @pytest.mark.parametrize("direction", [gumap.DIRECTION_PULL, gumap.DIRECTION_PUSH])
 @pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
 def test_zoo_forced_direction(g, k, direction):
