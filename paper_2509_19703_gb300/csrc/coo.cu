@@ -76,27 +76,66 @@ __global__ void __launch_bounds__(256) in_rows_kernel(CooArgs a, long long count
 
 // One warp per row: the own entries (valid slots, distinct columns) ranked by
 // column into scol / sw, with smp = the mutual entries ranked before each;
-// the row's mutual count and its mirror count (in-degree minus mutual).
+// the row's mutual count and its mirror count (in-degree minus mutual). The
+// list is in (distance, id) order, so each distance level is a run of
+// ascending ids: an entry's rank is its place in its own run plus, in every
+// other run, the number of ids below it (a binary search). Rows of more than
+// kRunSearch levels count against every entry instead.
+constexpr int kRunSearch = 8;
+
 __global__ void __launch_bounds__(kOwnThreads) own_sort_kernel(CooArgs a) {
     __shared__ int32_t s_col[kOwnThreads / 32][kMaxK];
     __shared__ uint8_t s_mut[kOwnThreads / 32][kMaxK];
+    __shared__ int32_t s_run[kOwnThreads / 32][kRunSearch + 1];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int32_t* sc = s_col[wib];
     uint8_t* sm = s_mut[wib];
+    int32_t* sr = s_run[wib];
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int k = a.k;
     for (long long i = warp; i < a.n; i += nwarps) {
         const int kv = a.kval[i];
         const size_t base = (size_t)i * k;
-        for (int t = lane; t < kv; t += 32) sc[t] = a.idx[base + t];
+        // columns, and the starts of the distance runs (at most kRunSearch kept)
+        int runs = 0;
+        for (int t0 = 0; t0 < kv; t0 += 32) {
+            const int t = t0 + lane;
+            bool starts = false;
+            if (t < kv) {
+                sc[t] = a.idx[base + t];
+                starts = t == 0 || a.dist[base + t] != a.dist[base + t - 1];
+            }
+            const unsigned m = __ballot_sync(kFull, starts);
+            const int at = runs + __popc(m & ((1u << lane) - 1u));
+            if (starts && at < kRunSearch) sr[at] = t;
+            runs += __popc(m);
+        }
+        if (lane == 0 && runs <= kRunSearch) sr[runs] = kv;
         __syncwarp();
         int mutual = 0;
         for (int t = lane; t < kv; t += 32) {
             const int x = sc[t];
             int r = 0;
-            for (int u = 0; u < kv; ++u) r += sc[u] < x ? 1 : 0;
+            if (runs <= kRunSearch) {
+                for (int q = 0; q < runs; ++q) {
+                    int lo = sr[q], hi = sr[q + 1];
+                    if (t >= lo && t < hi) {
+                        r += t - lo;  // ids ascend within the run
+                        continue;
+                    }
+                    const int first = lo;
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (sc[mid] < x) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    r += lo - first;
+                }
+            } else {
+                for (int u = 0; u < kv; ++u) r += sc[u] < x ? 1 : 0;
+            }
             const uint8_t m = a.mut[base + t];
             a.scol[base + r] = x;
             a.sw[base + r] = a.w[base + t];
@@ -123,7 +162,7 @@ __global__ void __launch_bounds__(kOwnThreads) own_sort_kernel(CooArgs a) {
             a.mtot[i] = mutual;
             a.mcnt[i] = (a.inend[i] - a.instart[i]) - (uint32_t)mutual;
         }
-        __syncwarp();  // s_col / s_mut are rewritten by the next row
+        __syncwarp();  // the shared arrays are rewritten by the next row
     }
 }
 

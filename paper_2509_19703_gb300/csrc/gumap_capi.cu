@@ -735,6 +735,7 @@ int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_i
         CooArgs c{};
         coo_scratch_split(h->coo_scr.p, n_src, &c.instart, &c.inend, &c.ctr, &c.pub);
         c.idx = out_idx;
+        c.dist = out_dist;
         c.w = out_w;
         c.mut = static_cast<uint8_t*>(h->coo_mut.p);
         c.kval = static_cast<int32_t*>(h->coo_kval.p);

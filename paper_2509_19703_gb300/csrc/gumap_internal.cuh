@@ -265,7 +265,8 @@ constexpr int kCooCtrTile = 0;               // tile counter of the row scan
 constexpr int kCooCtrWords = 4;
 
 struct CooArgs {
-    const int32_t* idx;          // kNN lists [n][k], valid slots first
+    const int32_t* idx;          // kNN lists [n][k], valid slots first, (distance, id) order
+    const uint16_t* dist;        // their distances
     const float* w;              // union weight per slot [n][k]
     const uint8_t* mut;          // per slot: 1 when the target's list holds the row too
     const int32_t* kval;         // per row: valid slots (own entries)

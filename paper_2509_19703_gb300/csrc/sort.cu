@@ -6,13 +6,16 @@
 // single-pass scan, applied per digit as in Adinets and Merrill's Onesweep
 // radix sort): one kernel counts the digits of every pass in a single read
 // of the keys; then one kernel per pass, in which each CTA takes the next
-// tile id from a counter, ranks its 2048 keys by digit (stable: warp w owns
-// the w-th 256-key segment of the tile, ranked with warp match), publishes
+// tile id from a counter, ranks its 4096 keys by digit (stable: warp w owns
+// the w-th 512-key segment of the tile, ranked with warp match), publishes
 // its per-digit counts, adds the counts of the tiles before it by looking
-// back over their published words, and scatters. A tile only waits on tiles
-// with smaller ids, which were handed out earlier to CTAs already running,
-// so the waits end; each is bounded in time all the same and reports
-// GUMAP_ERR_TIMEOUT in the caller's status word when it gives up.
+// back over their published words, lays the tile out in shared memory in
+// digit order and writes it from there, so consecutive threads store
+// consecutive elements of each digit's run. A tile only waits on tiles with
+// smaller ids, which were handed out earlier to CTAs already running, so the
+// waits end; each is bounded in time all the same and reports
+// GUMAP_ERR_TIMEOUT in the caller's status word when it gives up. The sort
+// is stable, which the transpose of the union COO relies on.
 #include "gumap_internal.cuh"
 
 namespace gumap {
@@ -21,9 +24,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 8;                      // keys per lane
-constexpr int kTile = kThreads * kItems;       // 2048 keys per tile
+constexpr int kItems = 16;                     // keys per lane
+constexpr int kTile = kThreads * kItems;       // 4096 keys per tile
 constexpr int kSeg = 32 * kItems;              // keys of one warp's segment
+constexpr size_t kStageBytes = (size_t)kTile * (sizeof(unsigned long long) + sizeof(float));
 constexpr int kMaxPasses = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 // published word of (tile, digit): flag in the top two bits, count below
@@ -57,17 +61,22 @@ __global__ void __launch_bounds__(kThreads) hist_all_kernel(const unsigned long 
 
 // One pass (digit at bit `shift`). hist: this pass's digit counts; tile_ctr:
 // this pass's tile counter; pub: this pass's published words [tiles][256];
-// all zeroed before the first pass.
-__global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long long* __restrict__ kin,
-                                                            const float* __restrict__ vin,
-                                                            unsigned long long* __restrict__ kout,
-                                                            float* __restrict__ vout, long long count, int shift,
-                                                            const unsigned int* __restrict__ hist,
-                                                            unsigned int* tile_ctr, unsigned long long* pub,
-                                                            int32_t* status) {
+// all zeroed before the first pass. Dynamic shared memory: the tile's keys
+// and values in digit order (kStageBytes).
+__global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(const unsigned long long* __restrict__ kin,
+                                                               const float* __restrict__ vin,
+                                                               unsigned long long* __restrict__ kout,
+                                                               float* __restrict__ vout, long long count, int shift,
+                                                               const unsigned int* __restrict__ hist,
+                                                               unsigned int* tile_ctr, unsigned long long* pub,
+                                                               int32_t* status) {
+    extern __shared__ __align__(16) unsigned char os_smem[];
+    unsigned long long* skey = reinterpret_cast<unsigned long long*>(os_smem);
+    float* sval = reinterpret_cast<float*>(skey + kTile);
     __shared__ unsigned int s_tile;
-    __shared__ unsigned int wcnt[kWarps][256];  // per-warp digit counts, then per-warp offsets
-    __shared__ unsigned long long gbase[256];   // where digit d of this tile starts in the output
+    __shared__ unsigned int wcnt[kWarps][256];  // per-warp digit counts, then per-warp offsets in the digit's run
+    __shared__ unsigned int tstart[256];        // the digit's first place in the tile's digit order
+    __shared__ long long gshift[256];           // global place of the tile's digit-d run, minus tstart[d]
     __shared__ unsigned int wsum[kWarps];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const unsigned lt = (1u << lane) - 1u;
@@ -81,18 +90,20 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long 
     // key's position among the segment's keys of the same digit
     unsigned long long key[kItems];
     float val[kItems];
-    int dig[kItems];
     unsigned int rank[kItems];
+    // digit of item c, or 256 past the end (invalid keys rank apart)
+    auto digit = [&](int c) -> int {
+        return seg + c * 32 + lane < count ? (int)((key[c] >> shift) & 0xFFull) : 256;
+    };
 #pragma unroll
     for (int c = 0; c < kItems; ++c) {
         const long long i = seg + c * 32 + lane;
         key[c] = i < count ? __ldcs(kin + i) : 0ull;
         val[c] = i < count ? __ldcs(vin + i) : 0.0f;
-        dig[c] = i < count ? (int)((key[c] >> shift) & 0xFFull) : 256;  // invalid keys rank apart
     }
 #pragma unroll
     for (int c = 0; c < kItems; ++c) {
-        const int d = dig[c];
+        const int d = digit(c);
         const unsigned peers = __match_any_sync(kFull, d);
         const unsigned before = d < 256 ? wcnt[warp][d] : 0u;
         rank[c] = before + __popc(peers & lt);
@@ -102,7 +113,7 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long 
     }
     __syncthreads();
 
-    // digit tid: offsets of each warp's run within the tile, and the tile total
+    // digit tid: offsets of each warp's run within the digit's run, and the tile total
     unsigned int tile_count = 0u;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
@@ -117,18 +128,33 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long 
         *reinterpret_cast<volatile unsigned long long*>(my) = kFlagAggregate | tile_count;
     }
 
-    // start of digit tid in the output: exclusive scan of the pass's digit counts
+    // exclusive scans over the 256 digits (thread tid = digit): the pass's
+    // digit counts give the digit's start in the output, the tile's counts
+    // the digit's start in the tile's digit order
     const unsigned int hc = hist[tid];
-    unsigned int inc = hc;
+    unsigned int inc = hc, tinc = tile_count;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned int y = __shfl_up_sync(kFull, inc, o);
-        if (lane >= o) inc += y;
+        const unsigned int ty = __shfl_up_sync(kFull, tinc, o);
+        if (lane >= o) {
+            inc += y;
+            tinc += ty;
+        }
     }
-    if (lane == 31) wsum[warp] = inc;
+    __shared__ unsigned int twsum[kWarps];
+    if (lane == 31) {
+        wsum[warp] = inc;
+        twsum[warp] = tinc;
+    }
     __syncthreads();
     unsigned long long start = inc - hc;
-    for (int w = 0; w < warp; ++w) start += wsum[w];
+    unsigned int tst = tinc - tile_count;
+    for (int w = 0; w < warp; ++w) {
+        start += wsum[w];
+        tst += twsum[w];
+    }
+    tstart[tid] = tst;
 
     // look back over the tiles before this one
     unsigned long long prefix = 0ull;
@@ -155,17 +181,28 @@ __global__ void __launch_bounds__(kThreads) onesweep_kernel(const unsigned long 
         }
         *reinterpret_cast<volatile unsigned long long*>(my) = kFlagInclusive | (prefix + tile_count);
     }
-    gbase[tid] = start + prefix;
+    gshift[tid] = (long long)(start + prefix) - (long long)tst;
     __syncthreads();
 
+    // the tile in digit order in shared memory, then out in that order
 #pragma unroll
     for (int c = 0; c < kItems; ++c) {
-        const int d = dig[c];
+        const int d = digit(c);
         if (d < 256) {
-            const unsigned long long pos = gbase[d] + wcnt[warp][d] + rank[c];
-            kout[pos] = key[c];
-            vout[pos] = val[c];
+            const unsigned int at = tstart[d] + wcnt[warp][d] + rank[c];
+            skey[at] = key[c];
+            sval[at] = val[c];
         }
+    }
+    __syncthreads();
+    const long long rem = count - tile * kTile;
+    const int tile_n = rem < kTile ? (int)rem : kTile;
+    for (int e = tid; e < tile_n; e += kThreads) {
+        const unsigned long long k2 = skey[e];
+        const int d = (int)((k2 >> shift) & 0xFFull);
+        const long long pos = gshift[d] + e;
+        kout[pos] = k2;
+        vout[pos] = sval[e];
     }
 }
 
@@ -199,6 +236,9 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned lon
     unsigned int* tile_ctr = hist + P * 256;
     cudaError_t e = cudaMemsetAsync(temp, 0, need, s);
     if (e != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStageBytes)) !=
+        cudaSuccess)
+        return e;
     long long hgrid = (count + kThreads * 16 - 1) / (kThreads * 16);
     if (hgrid > device_sm_count() * 8) hgrid = device_sm_count() * 8;
     hist_all_kernel<<<(unsigned)hgrid, kThreads, 0, s>>>(keys, count, P, hist);
@@ -206,8 +246,9 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned lon
     unsigned long long *ka = keys, *kb = keys_tmp;
     float *va = vals, *vb = vals_tmp;
     for (int p = 0; p < P; ++p) {
-        onesweep_kernel<<<(unsigned)tiles, kThreads, 0, s>>>(ka, va, kb, vb, count, 8 * p, hist + p * 256,
-                                                             tile_ctr + p, pub + (size_t)p * tiles * 256, status);
+        onesweep_kernel<<<(unsigned)tiles, kThreads, kStageBytes, s>>>(ka, va, kb, vb, count, 8 * p, hist + p * 256,
+                                                                       tile_ctr + p, pub + (size_t)p * tiles * 256,
+                                                                       status);
         if (launches) *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         unsigned long long* tk = ka;

@@ -11,8 +11,9 @@
 // by FP32 bisection on a bracket [0, hi] whose hi doubles until f(hi) >= T.
 // Hop distances are integers, so with y = exp(-1/sigma) the sum is the
 // polynomial f = sum_L c_L y^(L - rho) over the row's levels L (c_L slots at
-// level L); it is evaluated by Horner's rule over the sorted row, one exp
-// per bisection step instead of one per slot. f rises strictly from
+// level L); it is evaluated by Horner's rule, on level counts kept in
+// registers when the row's levels span fewer than 16, else over the sorted
+// row's slots: one exp per bisection step instead of one per slot. f rises strictly from
 // c_eq = #{j : d_ij = rho_i} (sigma -> 0) to kv = #valid (sigma -> inf), so
 // a root exists iff c_eq < T < kv:
 //   kv <= T   -> no root, sigma = +inf, every weight 1;
@@ -76,6 +77,19 @@ __device__ __forceinline__ float f_poly(const uint16_t* __restrict__ d, int kv, 
     return acc;
 }
 
+// Rows whose levels span fewer than kLevels keep the count of each level in
+// registers: f(sigma) is then the polynomial sum_l c_l y^l, l = 0 .. kLevels - 1,
+// by Horner's rule in kLevels multiply-adds.
+constexpr int kLevels = 16;
+
+__device__ __forceinline__ float f_levels(const float (&cl)[kLevels], float sigma) {
+    const float y = expf(-1.0f / sigma);
+    float acc = cl[kLevels - 1];
+#pragma unroll
+    for (int q = kLevels - 2; q >= 0; --q) acc = acc * y + cl[q];
+    return acc;
+}
+
 // a: NULL, or [n_rows][k] directed weights (padding 0). rec: NULL, or the
 // per-row records for the union (idx then gives the last slot's id).
 __global__ void __launch_bounds__(kSkThreads) smooth_knn_kernel(const int32_t* __restrict__ idx,
@@ -119,6 +133,35 @@ __global__ void __launch_bounds__(kSkThreads) smooth_knn_kernel(const int32_t* _
                     sigma = CUDART_INF_F;
                 } else if ((float)ceq >= T) {
                     sigma = 0.0f;
+                } else if ((int)my[kv - 1] - rho < kLevels) {
+                    // level counts: the row is sorted, so each level is one run
+                    float cl[kLevels];
+#pragma unroll
+                    for (int q = 0; q < kLevels; ++q) cl[q] = 0.0f;
+                    int cur = 0, cnt = 0;
+                    for (int t = 0; t < kv; ++t) {
+                        const int l = (int)my[t] - rho;
+                        if (l != cur) {
+#pragma unroll
+                            for (int q = 0; q < kLevels; ++q)
+                                if (q == cur) cl[q] = (float)cnt;
+                            cur = l;
+                            cnt = 0;
+                        }
+                        ++cnt;
+                    }
+#pragma unroll
+                    for (int q = 0; q < kLevels; ++q)
+                        if (q == cur) cl[q] = (float)cnt;
+                    float lo = 0.0f, hi = 1.0f;
+                    for (int it = 0; it < 128 && f_levels(cl, hi) < T; ++it) hi *= 2.0f;
+                    for (int it = 0; it < 200; ++it) {
+                        const float mid = 0.5f * (lo + hi);
+                        if (!(mid > lo && mid < hi)) break;
+                        if (f_levels(cl, mid) > T) hi = mid;
+                        else lo = mid;
+                    }
+                    sigma = 0.5f * (lo + hi);
                 } else {
                     float lo = 0.0f, hi = 1.0f;
                     for (int it = 0; it < 128 && f_poly(my, kv, rho, hi) < T; ++it) hi *= 2.0f;
