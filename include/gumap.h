@@ -97,9 +97,9 @@ extern "C" {
                                    1..64, 0 = 64 (default); re-plans the batch, synchronises      */
 #define GUMAP_OPT_COO_BUILD  12 /* value: how gumap_knn_run builds the union COO: 0 = automatic (default:
                                    1 below 2^21 slots n x k, 2 from there on), 1 = LSD radix sort of
-                                   2 n k (row, col) keys, 2 = row by row (the slots sorted stably by
-                                   target give each row's in-neighbours in id order; each row's own
-                                   entries ranked by column; one scan; every entry placed by
+                                   2 n k (row, col) keys, 2 = row by row (the mirror entries, sorted
+                                   stably by target, give each row's mirrors in id order; each row's
+                                   own entries ranked by column; one scan; every entry placed by
                                    counting); same COO either way                                  */
 #define GUMAP_OPT_FRONTIER_BUILD 13 /* value: the frontier engine's merge (partial form): 0 = automatic
                                    (default: groups of lanes), 1 = one thread per source (k <= 64;
@@ -191,7 +191,7 @@ int gumap_batch_create(gumap_knn **h, int32_t n_graphs, const int32_t *vertex_of
  * (n k) by an LSD radix sort of 2 n k (row, col) keys, from there on row by
  * row (GUMAP_OPT_COO_BUILD overrides the choice). The handle keeps that
  * build's scratch: about 48 n k bytes for the radix sort (keys and values,
- * twice), about 54 n k bytes for the row build. Errors:
+ * twice), about 52 n k bytes for the row build. Errors:
  * INVALID_ARG (bad pointer/size, union with explicit sources), OOM, CUDA.
  * Device-side failures (a bounded wait that timed out) are reported by
  * gumap_knn_check().

@@ -3,30 +3,25 @@
 // Row i of the union holds (i, j) for every j in i's kNN list (its own
 // entries) and (i, j') for every j' whose list holds i while i's list does
 // not hold j' (mirrors). A column never appears twice in a row: an own
-// entry's column is in i's list, a mirror's is not. The in-neighbours of i
-// (every j' whose list holds i) split into the mutual ones, which are own
-// entries of i too, and the mirrors; so the row is the merge of two sorted
-// lists, i's own entries by column and its in-neighbours by id, with the
-// mutual ones taken once.
+// entry's column is in i's list, a mirror's is not. So the row is the merge
+// of two sorted lists with distinct columns, i's own entries by column and
+// its mirrors by id.
 //
-//   union_kernel (weights.cu): the union weight of every slot, whether its
-//     target lists the row too (mut), and the slot as a transposed entry
-//     keyed (source << 32) | target.
-//   radix sort (sort.cu): a stable sort of those keys on the target's bits,
-//     so each target's in-neighbours come out together and in ascending id
-//     (the slots were in source order). No atomic counter is shared by the
-//     many rows that list a hub, and no row needs sorting afterwards.
-//   in_rows_kernel: each target's range [instart, inend) of sorted entries.
-//   own_sort_kernel: one warp per row ranks its own entries by column, and
-//     counts for each the mutual entries ranked before it (smp).
-//   row_scan_kernel: rowoff = exclusive prefix of the row lengths, own
-//     entries plus mirrors, in one pass (decoupled look-back of Merrill and
+//   union_mirrors_kernel (weights.cu): the union weight of every slot, and
+//     the mirrors compacted in slot order, keyed (source << 32) | target.
+//   radix sort (sort.cu): a stable sort of the mirrors on the target's bits,
+//     so each row's mirrors come out together and in ascending id (they
+//     were in source order). No atomic counter is shared by the many rows
+//     that list a hub, and no row needs sorting afterwards.
+//   in_rows_kernel: each row's range [instart, inend) of sorted mirrors.
+//   own_sort_kernel: one warp per row ranks its own entries by column.
+//   row_scan_kernel: rowoff = exclusive prefix of the row lengths (own
+//     entries plus mirrors) in one pass (decoupled look-back of Merrill and
 //     Garland's single-pass scan).
-//   own_emit_kernel: an own entry of column c at rank r lands at
-//     rowoff + r + (in-neighbours below c) - (mutual own entries below c).
-//   mirror_emit_kernel: the q-th in-neighbour j' of row i, when not mutual,
-//     lands at rowoff + (q - mutual own entries below j') + (own entries
-//     below j').
+//   own_emit_kernel: an own entry of rank r and column c lands at
+//     rowoff + r + (the row's mirrors below c).
+//   mirror_emit_kernel: the q-th mirror j' of row i lands at
+//     rowoff + q + (own entries of row i below j').
 // Every write lands inside its row: row lengths come from the counts, never
 // from differences of rowoff, and rowoff never exceeds the true prefix (a
 // look-back that gives up leaves it short and reports TIMEOUT).
@@ -60,11 +55,13 @@ __device__ __forceinline__ long long row_len(const CooArgs& a, long long i) {
 
 __device__ __forceinline__ unsigned target_of(unsigned long long key, unsigned mask) { return (unsigned)key & mask; }
 
-// Ranges of the sorted transposed entries per target: a run of equal targets
-// starts at instart and ends before inend. Padding keys (target bits all
-// ones, above every vertex) end the array.
-__global__ void __launch_bounds__(256) in_rows_kernel(CooArgs a, long long count) {
+__device__ __forceinline__ long long mirror_count(const CooArgs& a) { return (long long)*a.mirrors; }
+
+// Ranges of the sorted mirrors per target: a run of equal targets starts at
+// instart and ends before inend.
+__global__ void __launch_bounds__(256) in_rows_kernel(CooArgs a) {
     const unsigned mask = (1u << a.key_bits) - 1u;
+    const long long count = mirror_count(a);
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < count;
          p += (long long)gridDim.x * blockDim.x) {
         const unsigned t = target_of(a.tkey[p], mask);
@@ -75,94 +72,36 @@ __global__ void __launch_bounds__(256) in_rows_kernel(CooArgs a, long long count
 }
 
 // One warp per row: the own entries (valid slots, distinct columns) ranked by
-// column into scol / sw, with smp = the mutual entries ranked before each;
-// the row's mutual count and its mirror count (in-degree minus mutual). The
-// list is in (distance, id) order, so each distance level is a run of
-// ascending ids: an entry's rank is its place in its own run plus, in every
-// other run, the number of ids below it (a binary search). Rows of more than
-// kRunSearch levels count against every entry instead.
-constexpr int kRunSearch = 8;
-
+// column into scol / sw, and the row's mirror count. An entry's rank is the
+// number of smaller columns in the row, counted against a shared-memory copy
+// four columns per load.
 __global__ void __launch_bounds__(kOwnThreads) own_sort_kernel(CooArgs a) {
-    __shared__ int32_t s_col[kOwnThreads / 32][kMaxK];
-    __shared__ uint8_t s_mut[kOwnThreads / 32][kMaxK];
-    __shared__ int32_t s_run[kOwnThreads / 32][kRunSearch + 1];
+    __shared__ __align__(16) int32_t s_col[kOwnThreads / 32][kMaxK];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
     int32_t* sc = s_col[wib];
-    uint8_t* sm = s_mut[wib];
-    int32_t* sr = s_run[wib];
+    const int4* sv = reinterpret_cast<const int4*>(sc);
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const int k = a.k;
     for (long long i = warp; i < a.n; i += nwarps) {
         const int kv = a.kval[i];
+        const int kv4 = (kv + 3) & ~3;
         const size_t base = (size_t)i * k;
-        // columns, and the starts of the distance runs (at most kRunSearch kept)
-        int runs = 0;
-        for (int t0 = 0; t0 < kv; t0 += 32) {
-            const int t = t0 + lane;
-            bool starts = false;
-            if (t < kv) {
-                sc[t] = a.idx[base + t];
-                starts = t == 0 || a.dist[base + t] != a.dist[base + t - 1];
-            }
-            const unsigned m = __ballot_sync(kFull, starts);
-            const int at = runs + __popc(m & ((1u << lane) - 1u));
-            if (starts && at < kRunSearch) sr[at] = t;
-            runs += __popc(m);
-        }
-        if (lane == 0 && runs <= kRunSearch) sr[runs] = kv;
+        for (int t = lane; t < kv4; t += 32) sc[t] = t < kv ? a.idx[base + t] : INT_MAX;  // columns are < INT_MAX
         __syncwarp();
-        int mutual = 0;
         for (int t = lane; t < kv; t += 32) {
             const int x = sc[t];
             int r = 0;
-            if (runs <= kRunSearch) {
-                for (int q = 0; q < runs; ++q) {
-                    int lo = sr[q], hi = sr[q + 1];
-                    if (t >= lo && t < hi) {
-                        r += t - lo;  // ids ascend within the run
-                        continue;
-                    }
-                    const int first = lo;
-                    while (lo < hi) {
-                        const int mid = (lo + hi) >> 1;
-                        if (sc[mid] < x) lo = mid + 1;
-                        else hi = mid;
-                    }
-                    r += lo - first;
-                }
-            } else {
-                for (int u = 0; u < kv; ++u) r += sc[u] < x ? 1 : 0;
+            for (int f = 0; f < (kv4 >> 2); ++f) {
+                const int4 v = sv[f];
+                r += (v.x < x) + (v.y < x) + (v.z < x) + (v.w < x);
             }
-            const uint8_t m = a.mut[base + t];
             a.scol[base + r] = x;
             a.sw[base + r] = a.w[base + t];
-            sm[r] = m;
-            mutual += m;
         }
-        __syncwarp();
-        // exclusive prefix of the mutual flags in column order, 32 ranks per step
-        int carry = 0;
-        for (int r0 = 0; r0 < kv; r0 += 32) {
-            const int r = r0 + lane;
-            const int m = r < kv ? sm[r] : 0;
-            int inc = m;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(kFull, inc, o);
-                if (lane >= o) inc += y;
-            }
-            if (r < kv) a.smp[base + r] = (uint16_t)(carry + inc - m);
-            carry += __shfl_sync(kFull, inc, 31);
-        }
-        mutual = __reduce_add_sync(kFull, mutual);
-        if (lane == 0) {
-            a.mtot[i] = mutual;
-            a.mcnt[i] = (a.inend[i] - a.instart[i]) - (uint32_t)mutual;
-        }
-        __syncwarp();  // the shared arrays are rewritten by the next row
+        if (lane == 0) a.mcnt[i] = a.inend[i] - a.instart[i];
+        __syncwarp();  // s_col is rewritten by the next row
     }
 }
 
@@ -240,8 +179,8 @@ __global__ void __launch_bounds__(kScanThreads) row_scan_kernel(CooArgs a) {
 }
 
 
-// Number of in-neighbours of row i with an id below c: a binary search of the
-// row's sorted range of transposed entries (ids are the keys' high words).
+// Number of mirrors of row i with an id below c: a binary search of the
+// row's range of sorted mirrors (ids are the keys' high words).
 __device__ __forceinline__ uint32_t in_below(const CooArgs& a, long long i, int c) {
     uint32_t lo = a.instart[i], hi = a.inend[i];
     const uint32_t first = lo;
@@ -262,34 +201,30 @@ __global__ void __launch_bounds__(256) own_emit_kernel(CooArgs a) {
         const int r = (int)(s - i * a.k);
         if (r >= a.kval[i]) continue;
         const int c = a.scol[s];
-        const unsigned long long pos = a.rowoff[i] + (unsigned long long)r + in_below(a, i, c) - a.smp[s];
+        const unsigned long long pos = a.rowoff[i] + (unsigned long long)r + in_below(a, i, c);
         a.ccol[pos] = c;
         a.cw[pos] = a.sw[s];
     }
 }
 
-// One thread per sorted transposed entry: the q-th in-neighbour j' of row i.
-// A mutual one is already an own entry of row i; the others are mirrors.
-__global__ void __launch_bounds__(256) mirror_emit_kernel(CooArgs a, long long count) {
+// One thread per sorted mirror: the q-th mirror j' of row i.
+__global__ void __launch_bounds__(256) mirror_emit_kernel(CooArgs a) {
     const unsigned mask = (1u << a.key_bits) - 1u;
+    const long long count = mirror_count(a);
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < count;
          p += (long long)gridDim.x * blockDim.x) {
         const unsigned long long key = a.tkey[p];
         const unsigned i = target_of(key, mask);
-        if (i >= (unsigned)a.n) continue;  // padding
         const int src = (int)(key >> 32);
         const size_t base = (size_t)i * a.k;
-        const int kv = a.kval[i];
-        int lo = 0, hi = kv;  // own entries of row i with a column below src
+        int lo = 0, hi = a.kval[i];  // own entries of row i with a column below src
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (a.scol[base + mid] < src) lo = mid + 1;
             else hi = mid;
         }
-        if (lo < kv && a.scol[base + lo] == src) continue;  // mutual: emitted as an own entry
-        const uint32_t mutual_below = lo < kv ? a.smp[base + lo] : (uint32_t)a.mtot[i];
         const unsigned long long q = (unsigned long long)(p - a.instart[i]);
-        const unsigned long long pos = a.rowoff[i] + (q - mutual_below) + (unsigned long long)lo;
+        const unsigned long long pos = a.rowoff[i] + q + (unsigned long long)lo;
         a.ccol[pos] = src;
         a.cw[pos] = a.tval[p];
     }
@@ -346,7 +281,7 @@ void coo_scratch_split(void* scratch, int32_t n, uint32_t** instart, uint32_t** 
 cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* launches) {
     if (a.n <= 0) return cudaSuccess;
     const long long slots = (long long)a.n * a.k;
-    in_rows_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a, slots);
+    in_rows_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     own_sort_kernel<<<grid_for((long long)a.n * 32, kOwnThreads, sms * 8), kOwnThreads, 0, s>>>(a);
@@ -356,7 +291,7 @@ cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* lau
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     own_emit_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    mirror_emit_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a, slots);
+    mirror_emit_kernel<<<grid_for(slots, 256, sms * 16), 256, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (launches) *launches += 5;
     return cudaSuccess;

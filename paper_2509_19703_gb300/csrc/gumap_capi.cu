@@ -204,7 +204,7 @@ struct gumap_knn {
     DevBuf rho, sigma, wrow;  // wrow: the smoothing step's per-row records (union weights)
     DevBuf keys, vals, keys_tmp, vals_tmp, sort_temp;  // COO as radix-sorted (key, value) pairs
     // COO by rows (with the radix build's key and value buffers for the transposed entries)
-    DevBuf coo_scr, coo_kval, coo_mcnt, coo_mtot, coo_mut, coo_scol, coo_sw, coo_smp, coo_rowoff, coo_col, coo_w;
+    DevBuf coo_scr, coo_kval, coo_mcnt, coo_scol, coo_sw, coo_rowoff, coo_col, coo_w;
 
     // last run
     int32_t last_n_src = -1;
@@ -310,8 +310,8 @@ size_t held_bytes(const gumap_knn* h) {
     for (const auto& c : h->cuts) t += (size_t)(c.grid + 1) * 4 + c.meta_bytes + c.ocol_bytes;
     const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                           &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
-                          &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_mtot, &h->coo_mut,
-                          &h->coo_scol, &h->coo_sw, &h->coo_smp, &h->coo_rowoff, &h->coo_col, &h->coo_w};
+                          &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_scol, &h->coo_sw,
+                          &h->coo_rowoff, &h->coo_col, &h->coo_w};
     for (const DevBuf* b : bs) t += b->bytes;
     return t;
 }
@@ -713,48 +713,54 @@ int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_i
         h->last_union = true;
     } else if (want_union) {
         const size_t slots2 = 2 * slots;
-        const int TB = key_bits_for(n_src + 1);  // target bits of a transposed key: 2^TB > n
-        if ((rc = ensure(h, h->coo_scr, coo_scratch_bytes(n_src), "coo scratch")) ||
+        const int TB = key_bits_for(n_src + 1);  // target bits of a mirror key: 2^TB > n
+        // one zeroed block: the COO build's row ranges and scan words, then the
+        // union's look-back words, its tile counter and the mirror total
+        const size_t coo_bytes = coo_scratch_bytes(n_src);
+        const size_t uscan_words = union_scan_words(n_src, k);
+        const size_t scr_bytes = coo_bytes + (uscan_words + 2) * sizeof(unsigned long long);
+        if ((rc = ensure(h, h->coo_scr, scr_bytes, "coo scratch")) ||
             (rc = ensure(h, h->coo_kval, (size_t)n_src * 4, "coo kval")) ||
             (rc = ensure(h, h->coo_mcnt, (size_t)n_src * 4, "coo mirror counts")) ||
-            (rc = ensure(h, h->coo_mtot, (size_t)n_src * 4, "coo mutual counts")) ||
-            (rc = ensure(h, h->coo_mut, slots, "coo mutual flags")) ||
-            (rc = ensure(h, h->keys, slots * 8, "coo transposed keys")) ||
-            (rc = ensure(h, h->vals, slots * 4, "coo transposed weights")) ||
+            (rc = ensure(h, h->keys, slots * 8, "coo mirror keys")) ||
+            (rc = ensure(h, h->vals, slots * 4, "coo mirror weights")) ||
             (rc = ensure(h, h->keys_tmp, slots * 8, "coo keys tmp")) ||
             (rc = ensure(h, h->vals_tmp, slots * 4, "coo vals tmp")) ||
             (rc = ensure(h, h->sort_temp, radix_sort_temp_bytes((long long)slots, TB), "sort temp")) ||
             (rc = ensure(h, h->coo_scol, slots * 4, "coo own columns")) ||
             (rc = ensure(h, h->coo_sw, slots * 4, "coo own weights")) ||
-            (rc = ensure(h, h->coo_smp, slots * 2, "coo mutual prefix")) ||
             (rc = ensure(h, h->coo_rowoff, ((size_t)n_src + 1) * 8, "coo rowoff")) ||
             (rc = ensure(h, h->coo_col, slots2 * 4, "coo cols")) || (rc = ensure(h, h->coo_w, slots2 * 4, "coo weights")))
             return rc;
         LaunchLimits lim;
         if ((rc = launch_limits(h->device, lim))) return rc;
+        unsigned long long* uwords =
+            reinterpret_cast<unsigned long long*>(static_cast<char*>(h->coo_scr.p) + coo_bytes);
+        UnionScan us{};
+        us.pub = uwords;
+        us.tile_ctr = reinterpret_cast<unsigned int*>(uwords + uscan_words);
+        us.total = uwords + uscan_words + 1;
+        us.status = &h->d_ctr->status;
+        us.limit_ns = 1000ull * 1000ull * 1000ull;
         CooArgs c{};
         coo_scratch_split(h->coo_scr.p, n_src, &c.instart, &c.inend, &c.ctr, &c.pub);
         c.idx = out_idx;
-        c.dist = out_dist;
         c.w = out_w;
-        c.mut = static_cast<uint8_t*>(h->coo_mut.p);
         c.kval = static_cast<int32_t*>(h->coo_kval.p);
         c.n = n_src;
         c.k = k;
         c.key_bits = TB;
+        c.mirrors = us.total;
         c.mcnt = static_cast<uint32_t*>(h->coo_mcnt.p);
-        c.mtot = static_cast<int32_t*>(h->coo_mtot.p);
         c.scol = static_cast<int32_t*>(h->coo_scol.p);
         c.sw = static_cast<float*>(h->coo_sw.p);
-        c.smp = static_cast<uint16_t*>(h->coo_smp.p);
         c.rowoff = static_cast<unsigned long long*>(h->coo_rowoff.p);
         c.ccol = static_cast<int32_t*>(h->coo_col.p);
         c.cw = static_cast<float*>(h->coo_w.p);
         c.status = &h->d_ctr->status;
-        CK(cudaMemsetAsync(h->coo_scr.p, 0, coo_scratch_bytes(n_src), st), "memset coo scratch");
-        CK(launch_union(out_idx, out_dist, wrow, n_src, k, out_w, static_cast<uint8_t*>(h->coo_mut.p),
-                        static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
-                        static_cast<int32_t*>(h->coo_kval.p), st),
+        CK(cudaMemsetAsync(h->coo_scr.p, 0, scr_bytes, st), "memset coo scratch");
+        CK(launch_union_mirrors(out_idx, out_dist, wrow, n_src, k, out_w, static_cast<int32_t*>(h->coo_kval.p),
+                                static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p), us, st),
            "union");
         h->kernel_launches++;
         if (h->opt_profile) {
@@ -768,8 +774,8 @@ int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_i
         CK(radix_sort_pairs(static_cast<unsigned long long*>(h->keys.p), static_cast<float*>(h->vals.p),
                             static_cast<unsigned long long*>(h->keys_tmp.p), static_cast<float*>(h->vals_tmp.p),
                             (long long)slots, TB, h->sort_temp.p, h->sort_temp.bytes, &h->d_ctr->status, st, &tkey,
-                            &tval, &launches),
-           "transpose sort");
+                            &tval, &launches, us.total),
+           "mirror sort");
         c.tkey = tkey;
         c.tval = tval;
         CK(launch_coo_build(c, lim.sms, st, &launches), "coo build");
@@ -820,8 +826,8 @@ int gumap_knn_destroy(gumap_knn* h) {
     pool_free(h->d_ctr, sizeof(DeviceCounters));
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
-                    &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_mtot, &h->coo_mut,
-                    &h->coo_scol, &h->coo_sw, &h->coo_smp, &h->coo_rowoff, &h->coo_col, &h->coo_w};
+                    &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_scol, &h->coo_sw,
+                    &h->coo_rowoff, &h->coo_col, &h->coo_w};
     for (DevBuf* b : bs) release(*b);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;

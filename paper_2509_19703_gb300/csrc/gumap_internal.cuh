@@ -231,13 +231,26 @@ size_t smooth_knn_smem_bytes(int32_t k);
 // padding 0xFFFF last, as every engine writes them.
 cudaError_t launch_smooth_knn(const int32_t* idx, const uint16_t* dist, int32_t n_rows, int32_t k, float T,
                               float* rho, float* sigma, WeightRow* rec, float* a, cudaStream_t s);
-// Union weights into w from the lists and the records; when tkey != NULL also
-// what the row-by-row COO build needs: per slot the mutual flag (mut) and the
-// transposed entry (key (i << 32) | j, value w; padding ~0), per row the
-// valid-slot count (kval).
+// Union weights into w from the lists and the records.
 cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
-                         float* w, uint8_t* mut, unsigned long long* tkey, float* tval, int32_t* kval,
-                         cudaStream_t s);
+                         float* w, cudaStream_t s);
+// Look-back state of the union's mirror compaction: one published word per
+// tile of slots (union_scan_words of them) and a tile counter, both zeroed;
+// the mirror total lands in *total.
+struct UnionScan {
+    unsigned long long* pub;
+    unsigned int* tile_ctr;
+    unsigned long long* total;
+    int32_t* status;                 // kStatusTimeout if a look-back wait gives up
+    unsigned long long limit_ns;
+};
+size_t union_scan_words(int32_t n, int32_t k);
+// Union weights into w, per row the valid-slot count (kval), and the mirrors
+// (slots whose target does not list the row) compacted in slot order as keys
+// (i << 32) | j with the slot's weight.
+cudaError_t launch_union_mirrors(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n,
+                                 int32_t k, float* w, int32_t* kval, unsigned long long* mkey, float* mval,
+                                 const UnionScan& scan, cudaStream_t s);
 
 // Below kCooRowsMinSlots slots the COO is 2 n k (key, value) pairs sorted by
 // the radix sort; the row-by-row build's long-row tails cost more there than
@@ -254,37 +267,36 @@ cudaError_t launch_pairs_unpack(const unsigned long long* keys, const float* val
 
 // ---- sort.cu: LSD radix sort of (u64 key, float value) on the low `bits` key bits
 // (bits <= 64). A look-back wait that gives up writes kStatusTimeout to *status.
+// count_dev (optional): the element count on the device, at most `count`
+// (which then only bounds the launch).
 size_t radix_sort_temp_bytes(long long count, int bits);
 cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned long long* keys_tmp,
                              float* vals_tmp, long long count, int bits, void* temp, size_t temp_bytes,
                              int32_t* status, cudaStream_t s, unsigned long long** keys_out, float** vals_out,
-                             int* launches);
+                             int* launches, const unsigned long long* count_dev = nullptr);
 
 // ---- coo.cu: the fuzzy union as a COO sorted by (row, col), built by rows
 constexpr int kCooCtrTile = 0;               // tile counter of the row scan
 constexpr int kCooCtrWords = 4;
 
 struct CooArgs {
-    const int32_t* idx;          // kNN lists [n][k], valid slots first, (distance, id) order
-    const uint16_t* dist;        // their distances
+    const int32_t* idx;          // kNN lists [n][k], valid slots first
     const float* w;              // union weight per slot [n][k]
-    const uint8_t* mut;          // per slot: 1 when the target's list holds the row too
     const int32_t* kval;         // per row: valid slots (own entries)
     int32_t n;
     int32_t k;
-    // transposed entries sorted by target, stably (so by source within a
-    // target): key (source << 32) | target, value the slot's weight; padding
-    // keys (~0) last
+    // the mirrors sorted by target, stably (so by source within a target):
+    // key (source << 32) | target, value the slot's weight; how many there
+    // are is on the device (*mirrors), at most n k
     const unsigned long long* tkey;
     const float* tval;
+    const unsigned long long* mirrors;
     int32_t key_bits;            // the target's bits in a key: 2^key_bits > n
-    uint32_t* instart;           // [n] first sorted position of each target's entries (zeroed)
-    uint32_t* inend;             // [n] one past its last (zeroed): in-degree = inend - instart
-    uint32_t* mcnt;              // [n] mirrors of each row: in-degree minus mutual own entries
-    int32_t* mtot;               // [n] mutual own entries of each row
+    uint32_t* instart;           // [n] first sorted mirror of each target (zeroed)
+    uint32_t* inend;             // [n] one past its last (zeroed): mirrors of row i = inend - instart
+    uint32_t* mcnt;              // [n] mirrors per row
     int32_t* scol;               // [n][k] own entries sorted by column
     float* sw;                   // their weights
-    uint16_t* smp;               // per sorted own entry: mutual entries before it in that order
     unsigned long long* rowoff;  // [n + 1] first entry of each row; rowoff[n] = nnz
     unsigned long long* pub;     // look-back words of the row scan [tiles], zeroed
     uint32_t* ctr;               // [kCooCtrWords], zeroed
@@ -296,7 +308,7 @@ struct CooArgs {
 size_t coo_scratch_bytes(int32_t n);
 void coo_scratch_split(void* scratch, int32_t n, uint32_t** instart, uint32_t** inend, uint32_t** ctr,
                        unsigned long long** pub);
-// After launch_union and the stable sort of its transposed entries: target
+// After launch_union_mirrors and the stable sort of the mirrors: target
 // ranges, own-row sort, row scan, own entries, mirrors (5 launches).
 cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* launches);
 // Rows, columns and weights of the sorted COO (up to cap entries) and nnz.

@@ -420,7 +420,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
     ck(launch_smooth_knn(L->idx, L->dist, (int32_t)N, k, T, rho, sigma, want_union ? d_rec : nullptr,
                          want_union ? nullptr : L->w, st));
     if (want_union)
-        ck(launch_union(L->idx, L->dist, d_rec, (int32_t)N, k, L->w, nullptr, nullptr, nullptr, nullptr, st));
+        ck(launch_union(L->idx, L->dist, d_rec, (int32_t)N, k, L->w, st));
     if (ng > 1) {
         long long grid = (N + 255) / 256;
         if (grid > 4096) grid = 4096;

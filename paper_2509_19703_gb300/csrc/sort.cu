@@ -43,10 +43,19 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 // Counts of every digit of every pass, one read of the keys: hist[p][d].
+// The element count: `count`, or the device count when one is given (at most `count`).
+__device__ __forceinline__ long long live_count(long long count, const unsigned long long* count_dev) {
+    if (!count_dev) return count;
+    const unsigned long long c = *count_dev;
+    return c < (unsigned long long)count ? (long long)c : count;
+}
+
 __global__ void __launch_bounds__(kThreads) hist_all_kernel(const unsigned long long* __restrict__ keys,
                                                             long long count, int passes,
-                                                            unsigned int* __restrict__ hist) {
+                                                            unsigned int* __restrict__ hist,
+                                                            const unsigned long long* count_dev) {
     __shared__ unsigned int h[kMaxPasses][256];
+    count = live_count(count, count_dev);
     for (int p = 0; p < passes; ++p) h[p][threadIdx.x] = 0u;
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
@@ -69,7 +78,7 @@ __global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(const unsigned lo
                                                                float* __restrict__ vout, long long count, int shift,
                                                                const unsigned int* __restrict__ hist,
                                                                unsigned int* tile_ctr, unsigned long long* pub,
-                                                               int32_t* status) {
+                                                               int32_t* status, const unsigned long long* count_dev) {
     extern __shared__ __align__(16) unsigned char os_smem[];
     unsigned long long* skey = reinterpret_cast<unsigned long long*>(os_smem);
     float* sval = reinterpret_cast<float*>(skey + kTile);
@@ -84,6 +93,9 @@ __global__ void __launch_bounds__(kThreads, 2) onesweep_kernel(const unsigned lo
     for (int w = 0; w < kWarps; ++w) wcnt[w][tid] = 0u;
     __syncthreads();
     const long long tile = s_tile;
+    count = live_count(count, count_dev);
+    // tiles past the live count take no part: only later tiles would look back at them
+    if (tile * kTile >= count && tile > 0) return;
     const long long seg = tile * kTile + (long long)warp * kSeg;
 
     // load the warp's segment (coalesced), then rank it: rank[c] is the
@@ -222,7 +234,8 @@ size_t radix_sort_temp_bytes(long long count, int bits) {
 
 cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned long long* keys_tmp, float* vals_tmp,
                              long long count, int bits, void* temp, size_t temp_bytes, int32_t* status,
-                             cudaStream_t s, unsigned long long** keys_out, float** vals_out, int* launches) {
+                             cudaStream_t s, unsigned long long** keys_out, float** vals_out, int* launches,
+                             const unsigned long long* count_dev) {
     *keys_out = keys;
     *vals_out = vals;
     if (count <= 1 || bits <= 0) return cudaSuccess;
@@ -241,14 +254,14 @@ cudaError_t radix_sort_pairs(unsigned long long* keys, float* vals, unsigned lon
         return e;
     long long hgrid = (count + kThreads * 16 - 1) / (kThreads * 16);
     if (hgrid > device_sm_count() * 8) hgrid = device_sm_count() * 8;
-    hist_all_kernel<<<(unsigned)hgrid, kThreads, 0, s>>>(keys, count, P, hist);
+    hist_all_kernel<<<(unsigned)hgrid, kThreads, 0, s>>>(keys, count, P, hist, count_dev);
     if (launches) *launches += 1;
     unsigned long long *ka = keys, *kb = keys_tmp;
     float *va = vals, *vb = vals_tmp;
     for (int p = 0; p < P; ++p) {
         onesweep_kernel<<<(unsigned)tiles, kThreads, kStageBytes, s>>>(ka, va, kb, vb, count, 8 * p, hist + p * 256,
                                                                        tile_ctr + p, pub + (size_t)p * tiles * 256,
-                                                                       status);
+                                                                       status, count_dev);
         if (launches) *launches += 1;
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         unsigned long long* tk = ka;

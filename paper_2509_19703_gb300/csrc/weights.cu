@@ -206,45 +206,146 @@ __device__ __forceinline__ bool in_list(const WeightRow& rj, int i, int d) {
     return rj.last_dist == (int)kDistInf || d < rj.last_dist || (d == rj.last_dist && i <= rj.last_id);
 }
 
-// One thread per slot (i, t): union weight into w. With tkey given, also
-// what the row-by-row COO build needs (coo.cu): per slot whether the target
-// lists i too (mut), and the transposed entry (i -> j seen from row j) as the
-// key (i << 32) | j with the slot's weight (tval); padding slots get the key
-// ~0, which sorts after every target. Per row the count of valid slots, which
-// come first (kval).
+// One thread per slot (i, t): union weight into w.
 __global__ void __launch_bounds__(256) union_kernel(const int32_t* __restrict__ idx,
                                                     const uint16_t* __restrict__ dist,
                                                     const WeightRow* __restrict__ rec, int n, int k,
-                                                    float* __restrict__ w, uint8_t* __restrict__ mut,
-                                                    unsigned long long* __restrict__ tkey,
-                                                    float* __restrict__ tval, int32_t* __restrict__ kval) {
+                                                    float* __restrict__ w) {
     const long long total = (long long)n * k;
     for (long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x; s < total;
          s += (long long)gridDim.x * blockDim.x) {
         const long long i = s / k;
-        const int t = (int)(s - i * k);
         const int j = idx[s];
         float wv = 0.0f;
-        bool mutual = false;
         if (j >= 0) {
             const int d = dist[s];
             const WeightRow ri = rec[i];
             const WeightRow rj = rec[j];
             const float aij = umap_a(d, ri.rho, ri.sigma);
-            mutual = in_list(rj, (int)i, d);
-            const float aji = mutual ? umap_a(d, rj.rho, rj.sigma) : 0.0f;
+            const float aji = in_list(rj, (int)i, d) ? umap_a(d, rj.rho, rj.sigma) : 0.0f;
             wv = aij + aji - aij * aji;
         }
         w[s] = wv;
-        if (tkey) {
-            mut[s] = mutual ? 1 : 0;
-            tkey[s] = j >= 0 ? (((unsigned long long)i << 32) | (unsigned long long)j) : ~0ull;
-            tval[s] = wv;
+    }
+}
+
+// The union weights, plus what the row-by-row COO build (coo.cu) needs: per
+// row its valid-slot count (kval), and the mirrors -- slots (i, t) whose
+// target j does not list i, so that (j, i) is an entry of row j that j's own
+// list lacks -- compacted in slot order as keys (i << 32) | j with the slot's
+// weight. One CTA per tile of kUnionTile slots (tile ids from a counter, so
+// a tile only waits for tiles handed out before it): chunk c of the tile is
+// slots c * 256 + thread, a mirror's place is the mirrors before it in the
+// tile (ballots per warp and chunk) plus those of the tiles before (decoupled
+// look-back on published per-tile counts). The last tile stores the total.
+constexpr int kUnionChunks = 8;
+constexpr int kUnionTile = 256 * kUnionChunks;
+constexpr unsigned long long kUFlagAggregate = 1ull << 62;
+constexpr unsigned long long kUFlagInclusive = 2ull << 62;
+constexpr unsigned long long kUCountMask = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ unsigned long long u_globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__global__ void __launch_bounds__(256) union_mirrors_kernel(const int32_t* __restrict__ idx,
+                                                            const uint16_t* __restrict__ dist,
+                                                            const WeightRow* __restrict__ rec, int n, int k,
+                                                            float* __restrict__ w, int32_t* __restrict__ kval,
+                                                            unsigned long long* __restrict__ mkey,
+                                                            float* __restrict__ mval, UnionScan scan) {
+    __shared__ unsigned s_tile;
+    __shared__ unsigned s_cnt[kUnionChunks][8];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_tile = atomicAdd(scan.tile_ctr, 1u);
+    __syncthreads();
+    const long long tile = s_tile;
+    const long long total = (long long)n * k;
+    int jv[kUnionChunks];
+    float wv[kUnionChunks];
+    unsigned ball[kUnionChunks];
+#pragma unroll
+    for (int c = 0; c < kUnionChunks; ++c) {
+        const long long s = tile * kUnionTile + c * 256 + tid;
+        bool mirror = false;
+        jv[c] = -1;
+        wv[c] = 0.0f;
+        if (s < total) {
+            const long long i = s / k;
+            const int t = (int)(s - i * k);
+            const int j = idx[s];
+            jv[c] = j;
             if (j >= 0) {
+                const int d = dist[s];
+                const WeightRow ri = rec[i];
+                const WeightRow rj = rec[j];
+                const float aij = umap_a(d, ri.rho, ri.sigma);
+                const bool mutual = in_list(rj, (int)i, d);
+                const float aji = mutual ? umap_a(d, rj.rho, rj.sigma) : 0.0f;
+                wv[c] = aij + aji - aij * aji;
+                mirror = !mutual;
                 if (t == k - 1 || idx[s + 1] < 0) kval[i] = t + 1;
             } else if (t == 0) {
                 kval[i] = 0;
             }
+            w[s] = wv[c];
+        }
+        ball[c] = __ballot_sync(0xFFFFFFFFu, mirror);
+        if (lane == 0) s_cnt[c][warp] = __popc(ball[c]);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // mirrors of the tile in slot order: chunk by chunk, warp by warp
+        unsigned run = 0;
+        for (int c = 0; c < kUnionChunks; ++c)
+            for (int q = 0; q < 8; ++q) {
+                const unsigned x = s_cnt[c][q];
+                s_cnt[c][q] = run;
+                run += x;
+            }
+        volatile unsigned long long* pub = scan.pub;
+        unsigned long long prefix = 0;
+        if (tile == 0) {
+            pub[0] = kUFlagInclusive | run;
+        } else {
+            pub[tile] = kUFlagAggregate | run;
+            long long t = tile - 1;
+            unsigned long long t0 = 0;
+            bool timed = false;
+            while (t >= 0) {
+                const unsigned long long v = pub[t];
+                if ((v >> 62) == 0ull) {  // not published yet
+                    if (!timed) {
+                        t0 = u_globaltimer_ns();
+                        timed = true;
+                    } else if (u_globaltimer_ns() - t0 > scan.limit_ns) {
+                        atomicExch(scan.status, kStatusTimeout);
+                        break;
+                    }
+                    continue;
+                }
+                timed = false;
+                prefix += v & kUCountMask;
+                if ((v >> 62) == 2ull) break;
+                --t;
+            }
+            pub[tile] = kUFlagInclusive | (prefix + run);
+        }
+        s_base = prefix;
+        if (tile == (total - 1) / kUnionTile) *scan.total = prefix + run;
+    }
+    __syncthreads();
+    const unsigned long long base = s_base;
+#pragma unroll
+    for (int c = 0; c < kUnionChunks; ++c) {
+        if ((ball[c] >> lane) & 1u) {
+            const long long s = tile * kUnionTile + c * 256 + tid;
+            const unsigned long long pos = base + s_cnt[c][warp] + __popc(ball[c] & ((1u << lane) - 1u));
+            mkey[pos] = ((unsigned long long)(s / k) << 32) | (unsigned long long)(unsigned)jv[c];
+            mval[pos] = wv[c];
         }
     }
 }
@@ -356,11 +457,23 @@ cudaError_t launch_smooth_knn(const int32_t* idx, const uint16_t* dist, int32_t 
 }
 
 cudaError_t launch_union(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n, int32_t k,
-                         float* w, uint8_t* mut, unsigned long long* tkey, float* tval, int32_t* kval,
-                         cudaStream_t s) {
+                         float* w, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     const int grid = grid_for((long long)n * k, 256, device_sm_count() * 16);
-    union_kernel<<<grid, 256, 0, s>>>(idx, dist, rec, n, k, w, mut, tkey, tval, kval);
+    union_kernel<<<grid, 256, 0, s>>>(idx, dist, rec, n, k, w);
+    return cudaGetLastError();
+}
+
+size_t union_scan_words(int32_t n, int32_t k) {
+    return (size_t)(((long long)n * k + kUnionTile - 1) / kUnionTile);
+}
+
+cudaError_t launch_union_mirrors(const int32_t* idx, const uint16_t* dist, const WeightRow* rec, int32_t n,
+                                 int32_t k, float* w, int32_t* kval, unsigned long long* mkey, float* mval,
+                                 const UnionScan& scan, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const long long tiles = ((long long)n * k + kUnionTile - 1) / kUnionTile;
+    union_mirrors_kernel<<<(unsigned)tiles, 256, 0, s>>>(idx, dist, rec, n, k, w, kval, mkey, mval, scan);
     return cudaGetLastError();
 }
 
