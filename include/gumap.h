@@ -373,6 +373,53 @@ int64_t gumap_pool_cached_bytes(void);
 int gumap_knn_run_noalloc(const int32_t *row_ptr, const int32_t *col_idx, int32_t n, int64_t nnz, int32_t k,
                           int mode, int32_t *out_idx, uint16_t *out_dist, int32_t *status_out, void *stream);
 
+/* -------------------------------------------------- quality metrics -- */
+/*
+ * gumap_quality_np - neighbourhood preservation of a drawing X of the
+ * handle's graph (Section 4.1.3): for each vertex v, N_G(v, r) is the set of
+ * other vertices within r hops and N_D(v, r) the |N_G(v, r)| other vertices
+ * closest to v in X; the metric is the sum over v of
+ * |N_G cap N_D| / |N_G cup N_D| (the paper sets r = 2).
+ *
+ *   X          device float[n][dim], row-major: the drawing's coordinates.
+ *   dim        1 .. 8.
+ *   r          hop radius, >= 1.
+ *   out_c      device int32[n] or NULL: |N_G(v, r)|.
+ *   out_inter  device int32[n] or NULL: |N_G(v, r) cap N_D(v, r)|.
+ *   out_sum    device double[1]: the sum over v (a vertex with an empty
+ *              N_G(v, r) adds 1: two empty sets are identical).
+ *
+ * Closeness in X is the squared Euclidean distance in FP32 (each coordinate's
+ * difference, its square and the running sum rounded to float in coordinate
+ * order), ties broken by ascending vertex id; the counts are exact for that
+ * order. Work grows as n^2 (every vertex ranks all others): n <= 2^20.
+ * Asynchronous on `stream`. Errors: INVALID_ARG (batch handle, NULL pointer,
+ * dim, r, n), OOM, CUDA.
+ */
+int gumap_quality_np(gumap_knn *h, const float *X, int32_t dim, int32_t r, int32_t *out_c, int32_t *out_inter,
+                     double *out_sum, void *stream);
+
+/*
+ * gumap_quality_stress - aggregated stress of a drawing X of the handle's
+ * graph (Section 4.1.3):
+ *   1/(n^2 - n) * sum over ordered pairs i != j of ((d_ij - |X_i - X_j|) / d_ij)^2
+ * with d_ij the hop distance (the all-pairs matrix of Algorithm 1, from the
+ * bit-parallel BFS run to completion whatever the handle's form); a pair with
+ * no connecting path adds 1, the limit of its term as d_ij grows without
+ * bound (Section 3.2 gives such pairs an "infinite" distance).
+ *
+ *   X           device float[n][dim], row-major; dim 1 .. 8.
+ *   out_rows    device double[n] or NULL: each row's sum over j.
+ *   out_stress  device double[1]: the stress.
+ *
+ * Each term is evaluated in FP32 and summed in FP64. The handle keeps n^2
+ * uint16 hop distances of scratch (n <= 65535). Asynchronous on `stream`.
+ * Errors: INVALID_ARG (batch handle, NULL pointer, dim, n), OOM, CUDA;
+ * device-side errors via gumap_knn_check().
+ */
+int gumap_quality_stress(gumap_knn *h, const float *X, int32_t dim, double *out_rows, double *out_stress,
+                         void *stream);
+
 /* ------------------------------------------------------------ serving -- */
 /*
  * A server computes the same rows as gumap_knn_run (kNN lists of every vertex

@@ -72,9 +72,9 @@ def _bind(lib):
     lib.oracle_slot_union.restype = None
     lib.oracle_coo_union.argtypes = [vp, vp, i32, i32, vp, vp, vp]
     lib.oracle_coo_union.restype = i64
-    lib.oracle_np.argtypes = [vp, vp, i32, vp, i32, i32, vp, vp]
+    lib.oracle_np.argtypes = [vp, vp, i32, vp, i32, i32, vp, i32, vp, vp]
     lib.oracle_np.restype = ctypes.c_double
-    lib.oracle_stress.argtypes = [vp, vp, i32, vp, i32, vp]
+    lib.oracle_stress.argtypes = [vp, vp, i32, vp, i32, vp, i32, vp]
     lib.oracle_stress.restype = ctypes.c_double
     return lib
 
@@ -176,31 +176,36 @@ class Oracle:
             raise MemoryError
         return row[:nnz], col[:nnz], w[:nnz]
 
-    def np_metric(self, g, X, r: int = 2):
-        """(c int32 [n], inter int32 [n], total float): |N_G(v, r)|, |N_G ∩ N_D|
-        and the sum over v of |∩| / |∪| for the drawing X (float32 [n, dim])."""
+    def np_metric(self, g, X, r: int = 2, vertices=None):
+        """(c int32, inter int32, total float): |N_G(v, r)|, |N_G ∩ N_D| per
+        vertex (all, or the given ones) and the sum of |∩| / |∪| over them, for
+        the drawing X (float32 [n, dim])."""
         rp, col = _csr(g)
         X = np.ascontiguousarray(X, dtype=np.float32)
         assert X.ndim == 2 and X.shape[0] == g.n
-        c = np.empty(max(g.n, 1), dtype=np.int32)
-        inter = np.empty(max(g.n, 1), dtype=np.int32)
+        vs, nv = _sources(g, vertices)
+        c = np.empty(max(nv, 1), dtype=np.int32)
+        inter = np.empty(max(nv, 1), dtype=np.int32)
         total = self.lib.oracle_np(rp.ctypes.data, col.ctypes.data, g.n, X.ctypes.data, X.shape[1], int(r),
-                                   c.ctypes.data, inter.ctypes.data)
+                                   None if vs is None else vs.ctypes.data, nv, c.ctypes.data, inter.ctypes.data)
         if total < 0:
             raise ValueError("oracle_np failed")
-        return c[:g.n], inter[:g.n], float(total)
+        return c[:nv], inter[:nv], float(total)
 
-    def stress(self, g, X):
-        """(stress, per-row sums float64 [n]) of the drawing X (float32 [n, dim])."""
+    def stress(self, g, X, vertices=None):
+        """(stress, per-row sums float64) of the drawing X (float32 [n, dim]);
+        with `vertices`, only those rows (the first value is then their sum
+        over n^2 - n)."""
         rp, col = _csr(g)
         X = np.ascontiguousarray(X, dtype=np.float32)
         assert X.ndim == 2 and X.shape[0] == g.n
-        rows = np.empty(max(g.n, 1), dtype=np.float64)
+        vs, nv = _sources(g, vertices)
+        rows = np.empty(max(nv, 1), dtype=np.float64)
         total = self.lib.oracle_stress(rp.ctypes.data, col.ctypes.data, g.n, X.ctypes.data, X.shape[1],
-                                       rows.ctypes.data)
+                                       None if vs is None else vs.ctypes.data, nv, rows.ctypes.data)
         if total < 0:
             raise ValueError("oracle_stress failed")
-        return float(total), rows[:g.n]
+        return float(total), rows[:nv]
 
     def knn_pipeline(self, g, k: int, mode: str = "full"):
         """The whole path for all vertices: idx, dist, rho, sigma, a, w, coo."""
@@ -254,9 +259,9 @@ def knn_pipeline(g, k, mode="full"):
     return default().knn_pipeline(g, k, mode)
 
 
-def np_metric(g, X, r=2):
-    return default().np_metric(g, X, r)
+def np_metric(g, X, r=2, vertices=None):
+    return default().np_metric(g, X, r, vertices)
 
 
-def stress(g, X):
-    return default().stress(g, X)
+def stress(g, X, vertices=None):
+    return default().stress(g, X, vertices)

@@ -381,20 +381,23 @@ static int cmp_gd(const void *a, const void *b) {
  *   N_G(v, r) = the other vertices at hop distance at most r (BFS);
  *   N_D(v, r) = the |N_G(v, r)| other vertices closest to v in the drawing,
  *               by (FP32 squared distance, id);
- * out_c[v] = |N_G(v, r)|, out_inter[v] = |N_G(v, r) ∩ N_D(v, r)|. Returns the
- * printed sum over v of |∩| / |∪|, where |∪| = 2 |N_G| - |∩| because both
- * sets have |N_G| elements; a vertex with an empty N_G(v, r) adds 1.
+ * For the vertices verts[0 .. n_verts) (verts NULL: all n in order) it writes
+ * out_c[i] = |N_G(v, r)|, out_inter[i] = |N_G(v, r) ∩ N_D(v, r)|, and returns
+ * the printed sum over them of |∩| / |∪|, where |∪| = 2 |N_G| - |∩| because
+ * both sets have |N_G| elements; a vertex with an empty N_G(v, r) adds 1.
  * Returns -1 on failure.
  */
 double oracle_np(const int32_t *row_ptr, const int32_t *col, int32_t n, const float *X, int32_t dim, int32_t r,
-                 int32_t *out_c, int32_t *out_inter) {
+                 const int32_t *verts, int32_t n_verts, int32_t *out_c, int32_t *out_inter) {
     if (n < 1 || dim < 1 || r < 1) return -1.0;
     int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     gd_pair *geo = (gd_pair *)malloc(sizeof(gd_pair) * (size_t)n);
     if (!dist || !queue || !geo) { free(dist); free(queue); free(geo); return -1.0; }
     double total = 0.0;
-    for (int32_t v = 0; v < n; ++v) {
+    for (int32_t vi = 0; vi < n_verts; ++vi) {
+        int32_t v = verts ? verts[vi] : vi;
+        if (v < 0 || v >= n) { free(dist); free(queue); free(geo); return -1.0; }
         oracle_bfs(row_ptr, col, n, v, dist, queue);
         int32_t c = 0;
         for (int32_t u = 0; u < n; ++u)
@@ -408,8 +411,8 @@ double oracle_np(const int32_t *row_ptr, const int32_t *col, int32_t n, const fl
             int32_t u = geo[t].v;
             if (dist[u] >= 0 && dist[u] <= r) inter++;
         }
-        out_c[v] = c;
-        out_inter[v] = inter;
+        out_c[vi] = c;
+        out_inter[vi] = inter;
         total += c == 0 ? 1.0 : (double)inter / (double)(2 * c - inter);
     }
     free(dist);
@@ -422,17 +425,21 @@ double oracle_np(const int32_t *row_ptr, const int32_t *col, int32_t n, const fl
  * Aggregated stress (Section 4.1.3):
  *   1/(n^2 - n) * sum over ordered pairs i != j of ((d_ij - ||X_i - X_j||) / d_ij)^2
  * with d_ij the hop distance (BFS) and ||.|| the Euclidean distance in FP64.
- * A pair with no connecting path adds 1. row_out (optional) receives each
- * row's sum over j. Returns -1 on failure.
+ * A pair with no connecting path adds 1. row_out (optional) receives the sum
+ * over j of each row i = verts[ii] (verts NULL: all n rows in order); the
+ * return value is the sum of those rows / (n^2 - n), the stress itself when
+ * every row is taken. Returns -1 on failure.
  */
 double oracle_stress(const int32_t *row_ptr, const int32_t *col, int32_t n, const float *X, int32_t dim,
-                     double *row_out) {
+                     const int32_t *verts, int32_t n_verts, double *row_out) {
     if (n < 2 || dim < 1) return -1.0;
     int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
     if (!dist || !queue) { free(dist); free(queue); return -1.0; }
     double total = 0.0;
-    for (int32_t i = 0; i < n; ++i) {
+    for (int32_t ii = 0; ii < n_verts; ++ii) {
+        int32_t i = verts ? verts[ii] : ii;
+        if (i < 0 || i >= n) { free(dist); free(queue); return -1.0; }
         oracle_bfs(row_ptr, col, n, i, dist, queue);
         double row = 0.0;
         for (int32_t j = 0; j < n; ++j) {
@@ -446,7 +453,7 @@ double oracle_stress(const int32_t *row_ptr, const int32_t *col, int32_t n, cons
             double t = ((double)dist[j] - sqrt(sq)) / (double)dist[j];
             row += t * t;
         }
-        if (row_out) row_out[i] = row;
+        if (row_out) row_out[ii] = row;
         total += row;
     }
     free(dist);

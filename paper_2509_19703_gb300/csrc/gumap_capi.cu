@@ -205,6 +205,8 @@ struct gumap_knn {
     DevBuf keys, vals, keys_tmp, vals_tmp, sort_temp;  // COO as radix-sorted (key, value) pairs
     // COO by rows (with the radix build's key and value buffers for the transposed entries)
     DevBuf coo_scr, coo_kval, coo_mcnt, coo_scol, coo_sw, coo_rowoff, coo_col, coo_w;
+    // quality metrics of a drawing: per-vertex terms, all-pairs rows, kNN rows of that BFS
+    DevBuf q_term, q_apsp, q_idx, q_dist;
 
     // last run
     int32_t last_n_src = -1;
@@ -311,7 +313,7 @@ size_t held_bytes(const gumap_knn* h) {
     const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                           &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
                           &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_scol, &h->coo_sw,
-                          &h->coo_rowoff, &h->coo_col, &h->coo_w};
+                          &h->coo_rowoff, &h->coo_col, &h->coo_w, &h->q_term, &h->q_apsp, &h->q_idx, &h->q_dist};
     for (const DevBuf* b : bs) t += b->bytes;
     return t;
 }
@@ -495,7 +497,7 @@ int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut**
 // identity: src is the handle's 0 .. n-1 (all vertices as sources); apsp: the
 // all-pairs rows [n_src][n] (preset to 0xFFFF) or NULL
 int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
-              cudaStream_t st, uint16_t* apsp = nullptr) {
+              cudaStream_t st, uint16_t* apsp = nullptr, bool force_full = false) {
     const int S = choose_block_bits(h, n_src);
     if (S % 128 != 0 || S <= 0) return fail(GUMAP_ERR_INVALID_ARG, "block bits must be a positive multiple of 128");
     const int W = S / 32;
@@ -534,7 +536,7 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
         a.out_idx = out_idx + (size_t)b * S * h->k;
         a.out_dist = out_dist + (size_t)b * S * h->k;
         a.k = h->k;
-        a.partial = h->mode == GUMAP_PARTIAL ? 1 : 0;
+        a.partial = (h->mode == GUMAP_PARTIAL && !force_full) ? 1 : 0;
         a.apsp = apsp ? apsp + (size_t)b * S * (size_t)h->n : nullptr;
         a.apsp_ld = h->n;
         a.ctr = h->d_ctr;
@@ -827,7 +829,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
                     &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_scol, &h->coo_sw,
-                    &h->coo_rowoff, &h->coo_col, &h->coo_w};
+                    &h->coo_rowoff, &h->coo_col, &h->coo_w, &h->q_term, &h->q_apsp, &h->q_idx, &h->q_dist};
     for (DevBuf* b : bs) release(*b);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -1060,6 +1062,56 @@ int gumap_knn_apsp(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t*
                              out_apsp);
     h->last_stream = st;
     return rc;
+}
+
+int gumap_quality_np(gumap_knn* h, const float* X, int32_t dim, int32_t r, int32_t* out_c, int32_t* out_inter,
+                     double* out_sum, void* stream) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    if (h->batch) return fail(GUMAP_ERR_INVALID_ARG, "quality metrics take a single graph's handle");
+    if (!X || !out_sum) return fail(GUMAP_ERR_INVALID_ARG, "NULL drawing or output");
+    if (dim < 1 || dim > 8) return fail(GUMAP_ERR_INVALID_ARG, "dim must be in [1, 8]");
+    if (r < 1) return fail(GUMAP_ERR_INVALID_ARG, "r must be >= 1");
+    if (h->n > (1 << 20)) return fail(GUMAP_ERR_INVALID_ARG, "neighbourhood preservation takes n <= 2^20");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    reap(h, false);
+    int rc;
+    if ((rc = ensure(h, h->q_term, (size_t)h->n * sizeof(double), "np terms"))) return rc;
+    CK(launch_np(h->d_rp, h->d_col, h->n, X, dim, r, out_c, out_inter, static_cast<double*>(h->q_term.p), out_sum, st),
+       "neighbourhood preservation");
+    h->kernel_launches += 2;
+    h->last_stream = st;
+    return GUMAP_OK;
+}
+
+int gumap_quality_stress(gumap_knn* h, const float* X, int32_t dim, double* out_rows, double* out_stress,
+                         void* stream) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    if (h->batch) return fail(GUMAP_ERR_INVALID_ARG, "quality metrics take a single graph's handle");
+    if (!X || !out_stress) return fail(GUMAP_ERR_INVALID_ARG, "NULL drawing or output");
+    if (dim < 1 || dim > 8) return fail(GUMAP_ERR_INVALID_ARG, "dim must be in [1, 8]");
+    if (h->n > 65535) return fail(GUMAP_ERR_INVALID_ARG, "stress takes n <= 65535 (uint16 hop distances)");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    reap(h, false);
+    const size_t n = (size_t)h->n;
+    int rc;
+    if ((rc = ensure(h, h->q_apsp, n * n * sizeof(uint16_t), "all-pairs rows")) ||
+        (rc = ensure(h, h->q_idx, n * (size_t)h->k * sizeof(int32_t), "kNN rows")) ||
+        (rc = ensure(h, h->q_dist, n * (size_t)h->k * sizeof(uint16_t), "kNN distances")) ||
+        (!out_rows && (rc = ensure(h, h->q_term, n * sizeof(double), "stress rows"))))
+        return rc;
+    uint16_t* D = static_cast<uint16_t*>(h->q_apsp.p);
+    double* rows = out_rows ? out_rows : static_cast<double*>(h->q_term.p);
+    CK(cudaMemsetAsync(D, 0xFF, n * n * sizeof(uint16_t), st), "preset rows");
+    if ((rc = run_msbfs(h, h->d_identity, true, h->n, static_cast<int32_t*>(h->q_idx.p),
+                        static_cast<uint16_t*>(h->q_dist.p), st, D, true)))
+        return rc;
+    CK(launch_stress_rows(D, (long long)n, h->n, 0, h->n, X, dim, rows, st), "stress rows");
+    CK(launch_sum(rows, (long long)n, 1.0 / ((double)n * (double)n - (double)n), out_stress, st), "stress sum");
+    h->kernel_launches += 2;
+    h->last_stream = st;
+    return GUMAP_OK;
 }
 
 int gumap_selftest_wait_timeout(int device, double limit_s) {

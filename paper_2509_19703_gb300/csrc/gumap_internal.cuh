@@ -315,6 +315,18 @@ cudaError_t launch_coo_build(const CooArgs& a, int sms, cudaStream_t s, int* lau
 cudaError_t launch_coo_unpack(const CooArgs& a, long long cap, int32_t* row, int32_t* col, float* w,
                               int64_t* nnz_out, cudaStream_t s);
 
+// ---- quality.cu: quality metrics of a drawing (Section 4.1.3)
+// Neighbourhood preservation: per vertex |N_G(v, r)| (out_c) and |N_G cap N_D|
+// (out_inter), both optional; term [n] receives each vertex's Jaccard term;
+// *out_sum their sum.
+cudaError_t launch_np(const int32_t* row_ptr, const int32_t* col, int32_t n, const float* X, int32_t dim, int32_t r,
+                      int32_t* out_c, int32_t* out_inter, double* term, double* out_sum, cudaStream_t s);
+// Stress terms of `rows` all-pairs rows (row q is source src_lo + q, leading dimension ld) summed per row.
+cudaError_t launch_stress_rows(const uint16_t* D, long long ld, int32_t rows, int32_t src_lo, int32_t n,
+                               const float* X, int32_t dim, double* out_rows, cudaStream_t s);
+// *out = scale * sum of vals[0 .. count), in a fixed order.
+cudaError_t launch_sum(const double* vals, long long count, double scale, double* out, cudaStream_t s);
+
 // ---- validate.cu
 // Device-side CSR validation; writes 0 to *bad if the graph is valid.
 cudaError_t launch_validate_csr(const int32_t* row_ptr, const int32_t* col, int32_t n, int64_t nnz,

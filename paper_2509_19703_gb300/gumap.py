@@ -121,6 +121,8 @@ def _signatures() -> dict:
         "gumap_server_destroy": [vp],
         "gumap_knn_get_info": [vp, ctypes.POINTER(_Info)],
         "gumap_knn_autotune": [vp, ctypes.c_char_p, ctypes.POINTER(_Tune)],
+        "gumap_quality_np": [vp, vp, i32, i32, vp, vp, vp, vp],
+        "gumap_quality_stress": [vp, vp, i32, vp, vp, vp],
     }
     out = {name: (args, ctypes.c_int) for name, args in sig.items()}
     out.update({
@@ -297,6 +299,21 @@ def gumap_knn_run_noalloc(row_ptr, col_idx, n: int, nnz: int, k: int, mode: int,
                                         _stream(stream)), "gumap_knn_run_noalloc")
 
 
+def gumap_quality_np(h, X, r: int = 2, out_c=None, out_inter=None, out_sum=None, stream=None):
+    """Neighbourhood preservation of the drawing X (CUDA float32 tensor [n, dim])."""
+    _check(load().gumap_quality_np(h, _dptr(X, torch.float32, "X"), int(X.shape[1]), int(r),
+                                   _dptr(out_c, torch.int32, "out_c"), _dptr(out_inter, torch.int32, "out_inter"),
+                                   _dptr(out_sum, torch.float64, "out_sum"), _stream(stream)), "gumap_quality_np")
+
+
+def gumap_quality_stress(h, X, out_rows=None, out_stress=None, stream=None):
+    """Aggregated stress of the drawing X (CUDA float32 tensor [n, dim])."""
+    _check(load().gumap_quality_stress(h, _dptr(X, torch.float32, "X"), int(X.shape[1]),
+                                       _dptr(out_rows, torch.float64, "out_rows"),
+                                       _dptr(out_stress, torch.float64, "out_stress"), _stream(stream)),
+           "gumap_quality_stress")
+
+
 def gumap_pool_trim(device: int = -1):
     _check(load().gumap_pool_trim(int(device)), "gumap_pool_trim")
 
@@ -443,6 +460,23 @@ class KnnGraph:
         out["apsp"] = torch.empty((n_src, self.n), dtype=torch.int16, device=torch.device("cuda", self.device))
         gumap_knn_apsp(self.h, sources, n_src, out["idx"], out["dist"], out["apsp"], stream)
         return out
+
+    def quality_np(self, X, r: int = 2, stream=None):
+        """(c int32 [n], inter int32 [n], sum float64 [1]) of the drawing X (Section 4.1.3)."""
+        dev = torch.device("cuda", self.device)
+        c = torch.empty(self.n, dtype=torch.int32, device=dev)
+        inter = torch.empty(self.n, dtype=torch.int32, device=dev)
+        total = torch.empty(1, dtype=torch.float64, device=dev)
+        gumap_quality_np(self.h, X, r, c, inter, total, stream)
+        return c, inter, total
+
+    def quality_stress(self, X, stream=None):
+        """(stress float64 [1], per-row sums float64 [n]) of the drawing X (Section 4.1.3)."""
+        dev = torch.device("cuda", self.device)
+        rows = torch.empty(self.n, dtype=torch.float64, device=dev)
+        total = torch.empty(1, dtype=torch.float64, device=dev)
+        gumap_quality_stress(self.h, X, rows, total, stream)
+        return total, rows
 
     def rho_sigma(self, n_src: int | None = None, stream=None):
         n_src = self.n if n_src is None else n_src
