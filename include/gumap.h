@@ -412,7 +412,8 @@ int gumap_quality_np(gumap_knn *h, const float *X, int32_t dim, int32_t r, int32
  *   out_rows    device double[n] or NULL: each row's sum over j.
  *   out_stress  device double[1]: the stress.
  *
- * Each term is evaluated in FP32 and summed in FP64. The handle keeps n^2
+ * Each term's difference d_ij - |X_i - X_j| is taken in FP64, its division
+ * and square in FP32 (about 3e-7 relative), the sums in FP64. The handle keeps n^2
  * uint16 hop distances of scratch (n <= 65535). Asynchronous on `stream`.
  * Errors: INVALID_ARG (batch handle, NULL pointer, dim, n), OOM, CUDA;
  * device-side errors via gumap_knn_check().

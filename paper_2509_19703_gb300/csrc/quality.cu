@@ -20,8 +20,12 @@
 // Stress: 1/(n^2 - n) sum over ordered pairs i != j of
 // ((d_ij - |X_i - X_j|) / d_ij)^2 with d_ij the hop distance, a pair with no
 // path adding 1. stress_rows_kernel reads the all-pairs hop-distance rows
-// (from the bit-parallel BFS of msbfs.cu), one warp per row; each term is
-// FP32, each row's sum FP64.
+// (from the bit-parallel BFS of msbfs.cu), one warp per row. A term cancels
+// in d_ij - |X_i - X_j| when the drawing is good, so that difference is taken
+// in FP64: the squared norm from FP64 coordinate differences (exact for
+// float inputs), its square root in FP32 refined by one Newton step on the
+// FP64 residual; the division by d_ij and the square are FP32 (about 3e-7
+// relative per term); each row's sum is FP64.
 #include "gumap_internal.cuh"
 
 #include <climits>
@@ -218,9 +222,9 @@ __global__ void __launch_bounds__(256) stress_rows_kernel(const uint16_t* __rest
     for (long long rr = warp; rr < rows; rr += nwarps) {
         const int i = src_lo + (int)rr;
         const uint16_t* drow = D + rr * ld;
-        float xi[8];
+        double xi[8];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) xi[c] = c < dim ? __ldg(X + (size_t)i * dim + c) : 0.0f;
+        for (int c = 0; c < 8; ++c) xi[c] = c < dim ? (double)__ldg(X + (size_t)i * dim + c) : 0.0;
         double acc = 0.0;
         for (int j = lane; j < n; j += 32) {
             if (j == i) continue;
@@ -229,16 +233,24 @@ __global__ void __launch_bounds__(256) stress_rows_kernel(const uint16_t* __rest
                 acc += 1.0;
                 continue;
             }
-            float sq = 0.0f;
+            // |X_i - X_j|^2 exactly enough in FP64 (the difference of two floats is exact there)
+            double sq = 0.0;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
                 if (c < dim) {
-                    const float dx = xi[c] - __ldg(X + (size_t)j * dim + c);
-                    sq = fmaf(dx, dx, sq);
+                    const double dx = xi[c] - (double)__ldg(X + (size_t)j * dim + c);
+                    sq = fma(dx, dx, sq);
                 }
             }
-            const float dd = (float)dij;
-            const float t = (dd - sqrtf(sq)) / dd;
+            // its square root: FP32, refined by one Newton step on the FP64 residual
+            double x = 0.0;
+            if (sq > 0.0) {
+                const float x0 = sqrtf((float)sq);
+                const double res = fma(-(double)x0, (double)x0, sq);
+                x = (double)x0 + (double)((float)res / (2.0f * x0));
+            }
+            // d - x in FP64 (it cancels when the drawing is good), the rest in FP32
+            const float t = (float)((double)dij - x) / (float)dij;
             acc += (double)(t * t);
         }
 #pragma unroll
