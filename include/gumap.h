@@ -421,6 +421,43 @@ int gumap_quality_np(gumap_knn *h, const float *X, int32_t dim, int32_t r, int32
 int gumap_quality_stress(gumap_knn *h, const float *X, int32_t dim, double *out_rows, double *out_stress,
                          void *stream);
 
+/* -------------------------------------------------- spectral layout -- */
+typedef struct {
+    int32_t iterations;   /* Lanczos steps taken (over all restarts) */
+    int32_t restarts;     /* restarts from the current Ritz vectors */
+    double residual;      /* largest |M y - theta y| bound of the returned pairs */
+    int32_t converged;    /* 1 when residual <= 1e-10 */
+} gumap_spectral_info;
+
+/*
+ * gumap_spectral_layout - the spectral layout of the last run's kNN graph
+ * G_k with its fuzzy-union weights W (the initial coordinates of the layout
+ * stage, Algorithm 1's initialisation; Section 3.2, after Koren's spectral
+ * graph drawing): the solutions x of L x = mu D x (L = D - W, D = diag(W 1))
+ * for the `dim` smallest mu after the trivial mu = 0 (x constant), each
+ * D-normalised (x^T D x = 1).
+ *
+ *   dim     1 .. 8 coordinates.
+ *   out_X   device float[n][dim], row-major: column c is the c-th eigenvector;
+ *           its sign makes the entry of largest magnitude (the first such
+ *           vertex) positive; a vertex with no edge gets 0.
+ *   out_mu  host double[dim] or NULL: the eigenvalues mu, ascending (NaN for
+ *           a column the graph is too small to have).
+ *   info    host, or NULL: iterations, restarts, residual bound.
+ *
+ * The handle's last gumap_knn_run must have built the union COO (union
+ * weights). Eigenvectors of a repeated eigenvalue are any D-orthonormal basis
+ * of its eigenspace; on a disconnected G_k only D^(1/2) 1 counts as trivial,
+ * so the eigenvalue 0 of the other components comes first. Lanczos iteration
+ * with full reorthogonalisation in FP64 on the device (basis of up to 400
+ * vectors of n doubles, at most 4 GiB), restarted from its Ritz vectors until
+ * the residual bound falls below 1e-10 (30 restarts at most). Synchronous on
+ * `stream`. (Library extension: the paper's layout stage itself is out of
+ * scope.) Errors: INVALID_ARG (no union COO, dim, NULL), OOM, CUDA.
+ */
+int gumap_spectral_layout(gumap_knn *h, int32_t dim, float *out_X, double *out_mu, gumap_spectral_info *info,
+                          void *stream);
+
 /* ------------------------------------------------------------ serving -- */
 /*
  * A server computes the same rows as gumap_knn_run (kNN lists of every vertex

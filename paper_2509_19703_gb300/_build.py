@@ -19,7 +19,8 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB = os.path.join(OUT_DIR, "libgumap.so")
 
 SOURCES = ["gumap_capi.cu", "msbfs.cu", "frontier.cu", "weights.cu", "coo.cu", "sort.cu", "validate.cu", "noalloc.cu",
-           "batch.cu", "server.cu", "tune.cu", "pool.cu", "quality.cu"]
+           "batch.cu", "server.cu", "tune.cu", "pool.cu", "quality.cu",
+           "spectral.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

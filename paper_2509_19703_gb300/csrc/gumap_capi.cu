@@ -207,6 +207,8 @@ struct gumap_knn {
     DevBuf coo_scr, coo_kval, coo_mcnt, coo_scol, coo_sw, coo_rowoff, coo_col, coo_w;
     // quality metrics of a drawing: per-vertex terms, all-pairs rows, kNN rows of that BFS
     DevBuf q_term, q_apsp, q_idx, q_dist;
+    // spectral layout: CSR of a radix-built COO, vectors, basis, partial sums
+    DevBuf sp_rowoff, sp_col, sp_vec, sp_Q, sp_part;
 
     // last run
     int32_t last_n_src = -1;
@@ -313,7 +315,8 @@ size_t held_bytes(const gumap_knn* h) {
     const DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                           &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
                           &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_scol, &h->coo_sw,
-                          &h->coo_rowoff, &h->coo_col, &h->coo_w, &h->q_term, &h->q_apsp, &h->q_idx, &h->q_dist};
+                          &h->coo_rowoff, &h->coo_col, &h->coo_w, &h->q_term, &h->q_apsp, &h->q_idx, &h->q_dist,
+                          &h->sp_rowoff, &h->sp_col, &h->sp_vec, &h->sp_Q, &h->sp_part};
     for (const DevBuf* b : bs) t += b->bytes;
     return t;
 }
@@ -829,7 +832,8 @@ int gumap_knn_destroy(gumap_knn* h) {
     DevBuf* bs[] = {&h->bits, &h->act, &h->need, &h->cnt, &h->rho, &h->sigma, &h->wrow,
                     &h->keys, &h->vals, &h->keys_tmp, &h->vals_tmp, &h->sort_temp,
                     &h->coo_scr, &h->coo_kval, &h->coo_mcnt, &h->coo_scol, &h->coo_sw,
-                    &h->coo_rowoff, &h->coo_col, &h->coo_w, &h->q_term, &h->q_apsp, &h->q_idx, &h->q_dist};
+                    &h->coo_rowoff, &h->coo_col, &h->coo_w, &h->q_term, &h->q_apsp, &h->q_idx, &h->q_dist,
+                    &h->sp_rowoff, &h->sp_col, &h->sp_vec, &h->sp_Q, &h->sp_part};
     for (DevBuf* b : bs) release(*b);
     for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
     delete h;
@@ -1111,6 +1115,65 @@ int gumap_quality_stress(gumap_knn* h, const float* X, int32_t dim, double* out_
     CK(launch_sum(rows, (long long)n, 1.0 / ((double)n * (double)n - (double)n), out_stress, st), "stress sum");
     h->kernel_launches += 2;
     h->last_stream = st;
+    return GUMAP_OK;
+}
+
+int gumap_spectral_layout(gumap_knn* h, int32_t dim, float* out_X, double* out_mu, gumap_spectral_info* info,
+                          void* stream) {
+    if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    if (!out_X) return fail(GUMAP_ERR_INVALID_ARG, "NULL output");
+    if (dim < 1 || dim > 8) return fail(GUMAP_ERR_INVALID_ARG, "dim must be in [1, 8]");
+    if (!h->last_union) return fail(GUMAP_ERR_INVALID_ARG, "the last run built no union COO");
+    CK(cudaSetDevice(h->device), "cudaSetDevice");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    reap(h, false);
+    const int32_t n = h->last_n_src;
+    int rc;
+    SpectralInput in{};
+    in.n = n;
+    if (h->coo_rows) {
+        in.rowoff = h->coo.rowoff;
+        in.col = h->coo.ccol;
+        in.w = h->coo.cw;
+    } else {
+        unsigned long long nnz = 0;
+        CK(cudaMemcpyAsync(&nnz, &h->d_ctr->coo_nnz, sizeof(nnz), cudaMemcpyDeviceToHost, st), "read nnz");
+        CK(cudaStreamSynchronize(st), "read nnz");
+        if ((rc = ensure(h, h->sp_rowoff, ((size_t)n + 1) * 8, "spectral rows")) ||
+            (rc = ensure(h, h->sp_col, std::max<size_t>(nnz, 1) * 4, "spectral columns")))
+            return rc;
+        CK(launch_radix_csr(h->coo_keys, (long long)nnz, h->coo_key_bits, n,
+                            static_cast<unsigned long long*>(h->sp_rowoff.p), static_cast<int32_t*>(h->sp_col.p), st),
+           "spectral csr");
+        in.rowoff = static_cast<unsigned long long*>(h->sp_rowoff.p);
+        in.col = static_cast<int32_t*>(h->sp_col.p);
+        in.w = h->coo_vals;
+    }
+    const size_t nn = (size_t)n;
+    const long long by_memory = (long long)((4ull << 30) / (8ull * nn));
+    const int m_max = (int)std::max<long long>(1, std::min<long long>({(long long)n - 1, 400ll, by_memory}));
+    const size_t chunks = (nn + kSpectralChunk - 1) / kSpectralChunk;
+    if ((rc = ensure(h, h->sp_vec, (5 + (size_t)dim) * nn * 8, "spectral vectors")) ||
+        (rc = ensure(h, h->sp_Q, (size_t)m_max * nn * 8, "spectral basis")) ||
+        (rc = ensure(h, h->sp_part, ((size_t)m_max + 1) * (chunks + 1) * 8, "spectral partial sums")))
+        return rc;
+    double* v = static_cast<double*>(h->sp_vec.p);
+    SpectralScratch scr{};
+    scr.s = v;
+    scr.sq = v + nn;
+    scr.t = v + 2 * nn;
+    scr.w = v + 3 * nn;
+    scr.z = v + 4 * nn;
+    scr.Y = v + 5 * nn;
+    scr.Q = static_cast<double*>(h->sp_Q.p);
+    scr.part = static_cast<double*>(h->sp_part.p);
+    scr.h = scr.part + ((size_t)m_max + 1) * chunks;
+    scr.m_max = m_max;
+    const int r = spectral_layout(in, dim, out_X, out_mu, info, scr, st);
+    h->last_stream = st;
+    if (r == -2) return fail(GUMAP_ERR_INVALID_ARG, "the union graph has no edge");
+    if (r != 0) return cuda_fail(static_cast<cudaError_t>(r), "spectral layout");
+    h->kernel_launches += 1;
     return GUMAP_OK;
 }
 

@@ -9,6 +9,8 @@
 
 #include <cuda_runtime.h>
 
+#include "gumap.h"
+
 namespace gumap {
 
 constexpr uint16_t kDistInf = 0xFFFFu;
@@ -326,6 +328,29 @@ cudaError_t launch_stress_rows(const uint16_t* D, long long ld, int32_t rows, in
                                const float* X, int32_t dim, double* out_rows, cudaStream_t s);
 // *out = scale * sum of vals[0 .. count), in a fixed order.
 cudaError_t launch_sum(const double* vals, long long count, double scale, double* out, cudaStream_t s);
+
+// ---- spectral.cu: spectral layout of the union graph (the layout stage's initial coordinates)
+struct SpectralInput {
+    const unsigned long long* rowoff;  // CSR of the symmetric weighted graph, [n + 1]
+    const int32_t* col;
+    const float* w;
+    int32_t n;
+};
+struct SpectralScratch {
+    double *s, *sq, *t, *w, *z;  // [n] each
+    double* Q;                   // [m_max][n] Lanczos basis
+    double* Y;                   // [dim][n] Ritz vectors
+    double* part;                // [(m_max + 1) * ceil(n / 4096)] partial sums
+    double* h;                   // [m_max + 1]
+    int32_t m_max;
+};
+constexpr int kSpectralChunk = 4096;
+// Returns 0, a cudaError_t value (> 0), or -2 when the graph has no edge. Synchronous on st.
+int spectral_layout(const SpectralInput& in, int dim, float* out_X, double* out_mu, gumap_spectral_info* info,
+                    SpectralScratch& scr, cudaStream_t st);
+// rowoff [n + 1] and col [nnz] of the COO whose sorted keys are (row << key_bits) | col.
+cudaError_t launch_radix_csr(const unsigned long long* keys, long long nnz, int key_bits, int32_t n,
+                             unsigned long long* rowoff, int32_t* col, cudaStream_t s);
 
 // ---- validate.cu
 // Device-side CSR validation; writes 0 to *bad if the graph is valid.

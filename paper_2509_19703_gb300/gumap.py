@@ -71,6 +71,11 @@ class _Tune(ctypes.Structure):
                 ("batch_width", ctypes.c_int32), ("frontier_build", ctypes.c_int32)]
 
 
+class _SpectralInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("restarts", ctypes.c_int32), ("residual", ctypes.c_double),
+                ("converged", ctypes.c_int32)]
+
+
 class _ServerOpts(ctypes.Structure):
     _fields_ = [("n_streams", ctypes.c_int32), ("max_batch_graphs", ctypes.c_int32),
                 ("max_batch_vertices", ctypes.c_int64), ("max_queue", ctypes.c_int32),
@@ -123,6 +128,7 @@ def _signatures() -> dict:
         "gumap_knn_autotune": [vp, ctypes.c_char_p, ctypes.POINTER(_Tune)],
         "gumap_quality_np": [vp, vp, i32, i32, vp, vp, vp, vp],
         "gumap_quality_stress": [vp, vp, i32, vp, vp, vp],
+        "gumap_spectral_layout": [vp, i32, vp, vp, ctypes.POINTER(_SpectralInfo), vp],
     }
     out = {name: (args, ctypes.c_int) for name, args in sig.items()}
     out.update({
@@ -314,6 +320,17 @@ def gumap_quality_stress(h, X, out_rows=None, out_stress=None, stream=None):
            "gumap_quality_stress")
 
 
+def gumap_spectral_layout(h, X, stream=None):
+    """Spectral layout of the last run's union graph into X (CUDA float32 [n, dim]);
+    returns (mu numpy float64 [dim], info dict)."""
+    dim = int(X.shape[1])
+    mu = np.empty(dim, dtype=np.float64)
+    info = _SpectralInfo()
+    _check(load().gumap_spectral_layout(h, dim, _dptr(X, torch.float32, "X"), mu.ctypes.data, ctypes.byref(info),
+                                        _stream(stream)), "gumap_spectral_layout")
+    return mu, {f: getattr(info, f) for f, _ in _SpectralInfo._fields_}
+
+
 def gumap_pool_trim(device: int = -1):
     _check(load().gumap_pool_trim(int(device)), "gumap_pool_trim")
 
@@ -477,6 +494,12 @@ class KnnGraph:
         total = torch.empty(1, dtype=torch.float64, device=dev)
         gumap_quality_stress(self.h, X, rows, total, stream)
         return total, rows
+
+    def spectral_layout(self, dim: int = 2, stream=None):
+        """(X float32 CUDA [n, dim], mu, info): spectral layout of the last run's union graph."""
+        X = torch.empty((self.n, dim), dtype=torch.float32, device=torch.device("cuda", self.device))
+        mu, info = gumap_spectral_layout(self.h, X, stream)
+        return X, mu, info
 
     def rho_sigma(self, n_src: int | None = None, stream=None):
         n_src = self.n if n_src is None else n_src

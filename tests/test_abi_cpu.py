@@ -65,7 +65,8 @@ def test_binding_matches_the_header():
 
 
 STRUCTS = {"_Stats": "gumap_knn_stats", "_Info": "gumap_knn_info", "_Tune": "gumap_tune_result",
-           "_ServerOpts": "gumap_server_opts", "_Result": "gumap_result", "_ServerStats": "gumap_server_stats"}
+           "_ServerOpts": "gumap_server_opts", "_Result": "gumap_result", "_ServerStats": "gumap_server_stats",
+           "_SpectralInfo": "gumap_spectral_info"}
 
 
 def test_binding_structs_match_the_header(tmp_path):
