@@ -448,12 +448,14 @@ typedef struct {
  * The handle's last gumap_knn_run must have built the union COO (union
  * weights). Eigenvectors of a repeated eigenvalue are any D-orthonormal basis
  * of its eigenspace; on a disconnected G_k only D^(1/2) 1 counts as trivial,
- * so the eigenvalue 0 of the other components comes first. Lanczos iteration
- * with full reorthogonalisation in FP64 on the device (basis of up to 400
- * vectors of n doubles, at most 4 GiB), restarted from its Ritz vectors until
- * the residual bound falls below 1e-10 (30 restarts at most). Synchronous on
+ * so the eigenvalue 0 of the other components comes first. One Lanczos run
+ * per coordinate, with full reorthogonalisation in FP64 on the device (basis
+ * of up to 400 vectors of n doubles, at most 4 GiB), each projecting out the
+ * vectors found before and restarted from its Ritz vector until the residual
+ * bound falls below 1e-10 (30 restarts at most). Synchronous on
  * `stream`. (Library extension: the paper's layout stage itself is out of
- * scope.) Errors: INVALID_ARG (no union COO, dim, NULL), OOM, CUDA.
+ * scope.) Errors: INVALID_ARG (no union COO, a union graph with no edge,
+ * dim, NULL), OOM, CUDA.
  */
 int gumap_spectral_layout(gumap_knn *h, int32_t dim, float *out_X, double *out_mu, gumap_spectral_info *info,
                           void *stream);

@@ -19,11 +19,14 @@
 // host: its largest eigenvalues by bisection on Sturm counts, their vectors
 // by inverse iteration with a pivoted tridiagonal factorisation,
 // orthogonalised within clusters of equal eigenvalues. A Ritz pair's
-// residual is beta_j |s_last|; when the wanted pairs' residuals are below
-// the tolerance, the Ritz vectors Q s give y, and x = D^(-1/2) y. When the
-// basis is full first, Lanczos restarts from the sum of the current Ritz
-// vectors. Vertices with no edge keep coordinate 0 (the start vector is zero
-// there, and M maps the rest to the rest).
+// residual is beta_j |s_last|. A Krylov space from one start vector holds
+// one vector per distinct eigenvalue, so each run of Lanczos locks only its
+// top Ritz vector once converged, and later runs project the locked vectors
+// out as well: run r finds the r-th largest eigenvalue, copies of a repeated
+// one included. A run whose basis fills first restarts from its current top
+// Ritz vector. x = D^(-1/2) y for each locked y. Vertices with no edge keep
+// coordinate 0 (the start vector is zero there, and M maps the rest to the
+// rest).
 #include "gumap.h"
 #include "gumap_internal.cuh"
 
@@ -132,10 +135,11 @@ __global__ void axpby_kernel(long long n, double a, const double* __restrict__ x
 }
 
 // start vector: a counter-based pseudo-random value per vertex (splitmix64 of
-// the index), zero where the vertex has no edge
-__global__ void start_kernel(long long n, const double* __restrict__ s, double* __restrict__ q) {
+// the index and the run), zero where the vertex has no edge
+__global__ void start_kernel(long long n, const double* __restrict__ s, double* __restrict__ q,
+                             unsigned long long seed) {
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+        unsigned long long z = (unsigned long long)i + (seed + 1) * 0x9E3779B97F4A7C15ull;
         z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
         z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
         z ^= z >> 31;
@@ -357,84 +361,97 @@ int spectral_layout(const SpectralInput& in, int dim, float* out_X, double* out_
         return cudaGetLastError();
     };
 
-    start_kernel<<<vgrid, kVecThreads, 0, st>>>(n, s, wv);
-    SCK(cudaGetLastError());
+    // Runs of Lanczos, each locking one vector: the largest eigenvalue of M
+    // with t and the vectors locked so far projected out. A Krylov space
+    // holds one vector per distinct eigenvalue, so a repeated eigenvalue's
+    // other copies are found by the runs after the first.
     const double tol = 1e-10;
-    int iters = 0, restarts = 0, max_restarts = 30;
-    double worst = 1e300;
-    std::vector<double> al, be, theta;
+    const int max_restarts = 30;
+    int iters = 0, restarts = 0;
+    double worst = 0.0;
+    std::vector<double> al, be, theta_run, locked_theta;
     std::vector<std::vector<double>> vecs;
-    int have = 0;  // Ritz pairs of the last solve
-    for (;;) {
-        SCK(deflate(wv));
-        double nrm = 0.0;
-        SCK(normalize_into(wv, Q, &nrm));
-        if (!(nrm > 0.0)) break;
-        al.clear();
-        be.clear();
-        bool done = false;
-        int j = 0;
-        for (; j < m_max; ++j) {
-            double* qj = Q + (long long)j * ld;
-            mul_kernel<<<vgrid, kVecThreads, 0, st>>>(n, s, qj, z);
-            spmv_kernel<<<wgrid, kVecThreads, 0, st>>>(g, s, z, wv);
-            SCK(cudaGetLastError());
-            double alpha = 0.0;
-            SCK(dots(qj, 1, wv, &alpha));
-            al.push_back(alpha);
-            SCK(reorth(wv, j + 1));  // removes the alpha q_j and beta q_(j-1) parts as well
-            double beta = 0.0;
-            ++iters;
-            const bool last = j + 1 == m_max;
-            double bn = 0.0;
-            SCK(dots(wv, 1, wv, &bn));
-            beta = std::sqrt(bn);
-            const bool exhausted = beta <= 1e-13;  // the Krylov space is invariant: nothing more to find
-            const int want = std::min(dim, j + 1);
-            const bool check = (j + 1 >= dim && ((j + 1) % 8 == 0 || last)) || exhausted;
-            if (check) {
-                tri_top(al, be, want, theta, vecs);
-                have = want;
-                worst = 0.0;
-                for (int r = 0; r < want; ++r) worst = std::max(worst, std::fabs(beta * vecs[(size_t)r][(size_t)j]));
-                if (want == dim && worst <= tol) done = true;
-            }
-            if (done || exhausted || last) {
-                if (exhausted) done = true;
-                ++j;
+    double* Y = scr.Y;
+    int nl = 0;  // locked vectors, the columns Y[0 .. nl)
+    // project t and the locked vectors out of w
+    auto deflate_all = [&](double* w) -> cudaError_t {
+        cudaError_t e2 = deflate(w);
+        if (e2 != cudaSuccess || nl == 0) return e2;
+        if ((e2 = dots(Y, nl, w, nullptr)) != cudaSuccess) return e2;
+        return sub(Y, nl, w);
+    };
+    bool out_of_space = false;
+    for (int run = 0; nl < dim && !out_of_space; ++run) {
+        start_kernel<<<vgrid, kVecThreads, 0, st>>>(n, s, wv, (unsigned long long)run);
+        SCK(cudaGetLastError());
+        bool locked = false;
+        for (int rs = 0; !locked; ++rs) {
+            SCK(deflate_all(wv));
+            double nrm = 0.0;
+            SCK(normalize_into(wv, Q, &nrm));
+            if (!(nrm > 1e-12)) {  // nothing left outside the locked space
+                out_of_space = true;
                 break;
             }
-            be.push_back(beta);
-            axpby_kernel<<<vgrid, kVecThreads, 0, st>>>(n, 1.0 / beta, wv, 0.0, wv, Q + (long long)(j + 1) * ld);
-            SCK(cudaGetLastError());
-        }
-        // Ritz vectors y_r = Q s_r into the columns of Y (the spare space after Q's last used column)
-        const int mused = j;
-        if (have < dim) {
-            tri_top(al, be, std::min(dim, mused), theta, vecs);
-            have = std::min(dim, mused);
-        }
-        double* Y = scr.Y;
-        for (int r = 0; r < have; ++r) {
-            SCK(cudaMemcpyAsync(hdev, vecs[(size_t)r].data(), sizeof(double) * (size_t)mused, cudaMemcpyHostToDevice,
-                                st));
-            SCK(cudaMemsetAsync(Y + (long long)r * ld, 0, sizeof(double) * (size_t)n, st));
-            // Y_r = -(-Q s_r)
-            SCK(sub(Q, mused, Y + (long long)r * ld));
-            axpby_kernel<<<vgrid, kVecThreads, 0, st>>>(n, -1.0, Y + (long long)r * ld, 0.0, Y + (long long)r * ld,
-                                                        Y + (long long)r * ld);
+            al.clear();
+            be.clear();
+            bool conv = false;
+            double resid = 1e300;
+            int j = 0;
+            for (; j < m_max; ++j) {
+                double* qj = Q + (long long)j * ld;
+                mul_kernel<<<vgrid, kVecThreads, 0, st>>>(n, s, qj, z);
+                spmv_kernel<<<wgrid, kVecThreads, 0, st>>>(g, s, z, wv);
+                SCK(cudaGetLastError());
+                double alpha = 0.0;
+                SCK(dots(qj, 1, wv, &alpha));
+                al.push_back(alpha);
+                // full reorthogonalisation (it removes the alpha q_j and beta q_(j-1) parts too)
+                for (int pass = 0; pass < 2; ++pass) {
+                    SCK(dots(Q, j + 1, wv, nullptr));
+                    SCK(sub(Q, j + 1, wv));
+                }
+                SCK(deflate_all(wv));
+                ++iters;
+                double bn = 0.0;
+                SCK(dots(wv, 1, wv, &bn));
+                const double beta = std::sqrt(bn);
+                const bool exhausted = beta <= 1e-13;  // the Krylov space is invariant
+                const bool last = j + 1 == m_max;
+                if ((j + 1) % 8 == 0 || last || exhausted) {
+                    tri_top(al, be, 1, theta_run, vecs);
+                    resid = std::fabs(beta * vecs[0][(size_t)j]);
+                    conv = resid <= tol || exhausted;
+                }
+                if (conv || last) {
+                    ++j;
+                    break;
+                }
+                be.push_back(beta);
+                axpby_kernel<<<vgrid, kVecThreads, 0, st>>>(n, 1.0 / beta, wv, 0.0, wv, Q + (long long)(j + 1) * ld);
+                SCK(cudaGetLastError());
+            }
+            // the top Ritz vector Q s into Y[nl]
+            const int mused = j;
+            SCK(cudaMemcpyAsync(hdev, vecs[0].data(), sizeof(double) * (size_t)mused, cudaMemcpyHostToDevice, st));
+            double* y = Y + (long long)nl * ld;
+            SCK(cudaMemsetAsync(y, 0, sizeof(double) * (size_t)n, st));
+            SCK(sub(Q, mused, y));  // y = -Q s
+            axpby_kernel<<<vgrid, kVecThreads, 0, st>>>(n, -1.0, y, 0.0, y, y);
             SCK(cudaGetLastError());
             SCK(cudaStreamSynchronize(st));
-        }
-        if (done || restarts >= max_restarts || have < dim) break;
-        // restart from the sum of the current Ritz vectors
-        ++restarts;
-        SCK(cudaMemcpyAsync(wv, Y, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st));
-        for (int r = 1; r < have; ++r) {
-            axpby_kernel<<<vgrid, kVecThreads, 0, st>>>(n, 1.0, wv, 1.0, Y + (long long)r * ld, wv);
-            SCK(cudaGetLastError());
+            if (conv || rs >= max_restarts) {
+                locked_theta.push_back(theta_run[0]);
+                worst = std::max(worst, resid);
+                ++nl;
+                locked = true;
+            } else {  // restart from the current Ritz vector
+                ++restarts;
+                SCK(cudaMemcpyAsync(wv, y, sizeof(double) * (size_t)n, cudaMemcpyDeviceToDevice, st));
+            }
         }
     }
+    const int have = nl;
     // x = D^(-1/2) y, sign: the entry of largest magnitude positive (first such index)
     std::vector<double> host_y((size_t)n);
     for (int r = 0; r < dim; ++r) {
@@ -454,7 +471,7 @@ int spectral_layout(const SpectralInput& in, int dim, float* out_X, double* out_
                 }
             if (host_y[(size_t)arg] < 0.0) sign = -1.0;
             emit_kernel<<<vgrid, kVecThreads, 0, st>>>(n, s, scr.Y + (long long)r * ld, sign, r, dim, out_X);
-            if (out_mu) out_mu[r] = 1.0 - theta[(size_t)r];
+            if (out_mu) out_mu[r] = 1.0 - locked_theta[(size_t)r];
         } else {
             SCK(cudaMemsetAsync(z, 0, sizeof(double) * (size_t)n, st));
             emit_kernel<<<vgrid, kVecThreads, 0, st>>>(n, s, z, 1.0, r, dim, out_X);
