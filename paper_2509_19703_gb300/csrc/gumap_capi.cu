@@ -40,6 +40,17 @@ int fail(int status, const char* fmt, ...) {
     return status;
 }
 
+}  // namespace
+
+// Records the calling thread's last-error message for an entry point defined
+// in another translation unit; returns status.
+int gumap::report_error(int status, const char* msg) {
+    g_last_error = msg ? msg : "";
+    return status;
+}
+
+namespace {
+
 int cuda_fail(cudaError_t e, const char* what) {
     if (e == cudaErrorMemoryAllocation)
         return fail(GUMAP_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));

@@ -176,6 +176,8 @@ struct BatchArgs {
 constexpr size_t kBatchSmemBudget = 220000;
 
 // ---- gumap_capi.cu (host helpers shared with the server)
+// Sets the calling thread's gumap_last_error() message; returns status.
+int report_error(int status, const char* msg);
 bool host_csr_ok(const int32_t* rp, const int32_t* col, int32_t n, int64_t nnz, std::string& why);
 // graph_edges[g]: adjacency entries of graph g; max_w: widest unit allowed (words, <= kMaxBatchW).
 int32_t plan_batch(int32_t n_graphs, const int32_t* vertex_offsets, const int64_t* graph_edges, const int32_t* modes,

@@ -63,25 +63,31 @@ using namespace gumap;
 extern "C" int gumap_knn_run_noalloc(const int32_t* row_ptr, const int32_t* col_idx, int32_t n, int64_t nnz,
                                      int32_t k, int mode, int32_t* out_idx, uint16_t* out_dist,
                                      int32_t* status_out, void* stream) {
-    if (!row_ptr || (!col_idx && nnz > 0) || !out_idx || !out_dist) return GUMAP_ERR_INVALID_ARG;
-    if (n < 2 || nnz < 0 || nnz > 0x7FFFFFFFll) return GUMAP_ERR_INVALID_ARG;
-    if (k < 1 || k > GUMAP_MAX_K || k > n - 1) return GUMAP_ERR_INVALID_ARG;
-    if (mode != GUMAP_FULL && mode != GUMAP_PARTIAL) return GUMAP_ERR_INVALID_ARG;
-    if (scratch_bytes(n, 128) > kNoallocScratchBytes) return GUMAP_ERR_TOO_LARGE;
+    report_error(GUMAP_OK, "");
+    if (!row_ptr || (!col_idx && nnz > 0) || !out_idx || !out_dist)
+        return report_error(GUMAP_ERR_INVALID_ARG, "NULL CSR or output pointer");
+    if (n < 2 || nnz < 0 || nnz > 0x7FFFFFFFll) return report_error(GUMAP_ERR_INVALID_ARG, "n or nnz out of range");
+    if (k < 1 || k > GUMAP_MAX_K || k > n - 1) return report_error(GUMAP_ERR_INVALID_ARG, "k must be in [1, min(n-1, 256)]");
+    if (mode != GUMAP_FULL && mode != GUMAP_PARTIAL) return report_error(GUMAP_ERR_INVALID_ARG, "bad mode");
+    if (scratch_bytes(n, 128) > kNoallocScratchBytes)
+        return report_error(GUMAP_ERR_TOO_LARGE, "the graph's scratch exceeds the fixed 16 MiB array");
 
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GUMAP_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return report_error(GUMAP_ERR_CUDA, "no current CUDA device");
     DeviceSetup setup;
     {
         std::lock_guard<std::mutex> lock(g_setup_mutex);
         DeviceSetup& s = g_setup[dev];
         if (!s.ready) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return GUMAP_ERR_CUDA;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
+                return report_error(GUMAP_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed");
             int sms = 0;
-            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return GUMAP_ERR_CUDA;
+            if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return report_error(GUMAP_ERR_CUDA, "device attribute query failed");
             const int per_sm = msbfs_max_blocks_per_sm(256);
-            if (per_sm <= 0) return GUMAP_ERR_CUDA;
+            if (per_sm <= 0) return report_error(GUMAP_ERR_CUDA, "the MS-BFS kernel cannot be resident");
             s.scratch = static_cast<unsigned char*>(p);
             s.coop_grid = sms * per_sm;
             s.ready = true;
@@ -109,8 +115,10 @@ extern "C" int gumap_knn_run_noalloc(const int32_t* row_ptr, const int32_t* col_
     const size_t words = (size_t)n * W;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(ctr, 0, sizeof(DeviceCounters), st) != cudaSuccess) return GUMAP_ERR_CUDA;
-    if (launch_identity(order, n, st) != cudaSuccess) return GUMAP_ERR_CUDA;  // sources and pull order
+    if (cudaMemsetAsync(ctr, 0, sizeof(DeviceCounters), st) != cudaSuccess)
+        return report_error(GUMAP_ERR_CUDA, "clearing the counters failed");
+    if (launch_identity(order, n, st) != cudaSuccess)  // sources and pull order
+        return report_error(GUMAP_ERR_CUDA, "identity launch failed");
     const int nblocks = (n + S - 1) / S;
     for (int b = 0; b < nblocks; ++b) {
         MsbfsArgs a{};
@@ -138,11 +146,14 @@ extern "C" int gumap_knn_run_noalloc(const int32_t* row_ptr, const int32_t* col_
         a.partial = mode == GUMAP_PARTIAL ? 1 : 0;
         a.ctr = ctr;
         a.direction = 1;  // pull only: the push levels' queues would need more scratch
-        if (cudaMemsetAsync(ctr, 0, kLaunchCounterBytes, st) != cudaSuccess) return GUMAP_ERR_CUDA;
-        if (launch_msbfs(a, setup.coop_grid, 256, st) != cudaSuccess) return GUMAP_ERR_CUDA;
+        if (cudaMemsetAsync(ctr, 0, kLaunchCounterBytes, st) != cudaSuccess)
+            return report_error(GUMAP_ERR_CUDA, "clearing the launch counters failed");
+        // as many CTAs as the block's items need, at most the resident grid
+        if (launch_msbfs(a, msbfs_grid_for(a, setup.coop_grid), 256, st) != cudaSuccess)
+            return report_error(GUMAP_ERR_CUDA, "msbfs launch failed");
     }
     if (status_out &&
         cudaMemcpyAsync(status_out, &ctr->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-        return GUMAP_ERR_CUDA;
+        return report_error(GUMAP_ERR_CUDA, "copying the status word failed");
     return GUMAP_OK;
 }

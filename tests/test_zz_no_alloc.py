@@ -3,7 +3,8 @@ cannot allocate device memory where they need kNN lists (a framework that
 owns all device memory, or a latency-bound loop that cannot afford
 cudaMalloc's synchronisation). Its scratch is a fixed array inside the
 library; these checks compare its rows with gumap_knn_run's on two calls in a
-row (the second call reuses the array the first one left behind).
+row (the second call reuses the array the first one left behind), with the
+CPU oracle's rows, and on a graph whose scratch needs many source blocks.
 
 This file is named so that pytest collects it after every other test file.
 """
@@ -12,6 +13,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 from paper_2509_19703_gb300 import graphgen as gg
 from paper_2509_19703_gb300 import gumap
 
@@ -55,6 +57,29 @@ def test_noalloc_matches_existing_entry_point_two_calls_in_a_row():
         assert np.array_equal(got_dist, want_dist), g.name
 
 
+def test_noalloc_matches_the_oracle():
+    for g, k, mode in [(gg.barabasi_albert(3000, 3, 81), 15, gumap.FULL),
+                       (gg.disjoint_union([gg.grid(40, 30), gg.path(5)], "grid+path"), 20, gumap.PARTIAL)]:
+        got_idx, got_dist = _noalloc(g, k, mode)
+        want_idx, want_dist = oracle.knn_full(g, k) if mode == gumap.FULL else oracle.knn_partial(g, k)
+        assert np.array_equal(got_idx, want_idx) and np.array_equal(got_dist, want_dist), g.name
+
+
+@pytest.mark.parametrize("mode", [gumap.FULL, gumap.PARTIAL], ids=["full", "partial"])
+def test_noalloc_many_source_blocks(mode):
+    """n = 40,000: the fixed array holds about 1024 sources per block, so some
+    40 launches share it, with a short last block."""
+    g = gg.barabasi_albert(40000, 3, 82)
+    k = 15
+    want_idx, want_dist = _existing_entry_point(g, k, mode)
+    for _ in range(2):
+        got_idx, got_dist = _noalloc(g, k, mode)
+        assert np.array_equal(got_idx, want_idx) and np.array_equal(got_dist, want_dist)
+    sample = np.random.default_rng(83).choice(g.n, size=200, replace=False).astype(np.int32)
+    ref_idx, ref_dist = oracle.knn_partial(g, k, sources=sample)  # full and partial lists are the same
+    assert np.array_equal(got_idx[sample], ref_idx) and np.array_equal(got_dist[sample], ref_dist)
+
+
 def test_noalloc_rejects_graphs_beyond_its_scratch():
     n = 1_000_000
     rp = torch.zeros(n + 1, dtype=torch.int32, device="cuda")
@@ -64,3 +89,4 @@ def test_noalloc_rejects_graphs_beyond_its_scratch():
     with pytest.raises(gumap.GumapError) as e:
         gumap.gumap_knn_run_noalloc(rp, col, n, 0, 1, gumap.FULL, idx, dist)
     assert e.value.status == gumap.ERR_TOO_LARGE
+    assert "16 MiB" in str(e.value)  # the reason reaches gumap_last_error()
