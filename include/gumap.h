@@ -78,7 +78,11 @@ extern "C" {
 #define GUMAP_ENGINE_MSBFS    1 /* bit-parallel multi-source BFS, bitsets in global memory (L2) */
 #define GUMAP_ENGINE_MSBFS_SM 2 /* reserved, not accepted (small graphs in shared memory: GUMAP_ENGINE_BATCH) */
 #define GUMAP_ENGINE_FRONTIER 3 /* partial form only: warp per source, bounded merge of sorted rows */
-#define GUMAP_ENGINE_BATCH    4 /* batch handles: one persistent launch, one CTA per (graph, source block) */
+#define GUMAP_ENGINE_BATCH    4 /* one persistent launch, one CTA per (graph, source block), bitsets in
+                                   shared memory: batch handles, and single graphs small enough for a
+                                   CTA (selecting it for one graph plans a one-graph batch, which
+                                   synchronises; TOO_LARGE beyond about 27,000 vertices); a run with
+                                   explicit sources uses GUMAP_ENGINE_MSBFS instead                */
 
 /* --------------------------------------------------------------- options */
 #define GUMAP_OPT_ENGINE      1 /* value: GUMAP_ENGINE_*                                 */
@@ -93,7 +97,7 @@ extern "C" {
 #define GUMAP_OPT_PULL_WIDTH  8 /* value: 32-bit words per MS-BFS pull item, 4 (default) or 2     */
 #define GUMAP_OPT_CTAS_PER_SM 9 /* value: resident 256-thread MS-BFS CTAs per SM the kernel is built
                                    for: 3 (default, up to 80 registers a thread) or 4 (64)        */
-#define GUMAP_OPT_BATCH_WIDTH 11 /* value: batch handles: widest unit in 32-bit words (32 sources each),
+#define GUMAP_OPT_BATCH_WIDTH 11 /* value: batched engine: widest unit in 32-bit words (32 sources each),
                                    1..64, 0 = 64 (default); re-plans the batch, synchronises      */
 #define GUMAP_OPT_COO_BUILD  12 /* value: how gumap_knn_run builds the union COO: 0 = automatic (default:
                                    1 below 2^21 slots n x k, 2 from there on), 1 = LSD radix sort of

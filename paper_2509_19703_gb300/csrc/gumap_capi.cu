@@ -233,8 +233,10 @@ struct gumap_knn {
     int last_block_bits = 0;
     int last_blocks = 0;
 
-    // batched engine (handles made by gumap_batch_create)
+    // batched engine (handles made by gumap_batch_create; a single graph's
+    // handle plans itself as a one-graph batch when that engine is chosen)
     bool batch = false;
+    bool batch_planned = false;
     int32_t n_graphs = 0;
     BatchUnit* d_units = nullptr;
     int32_t n_units = 0;
@@ -678,8 +680,15 @@ int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_i
         if (h->mode != GUMAP_PARTIAL) return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
         rc = run_frontier(h, src, n_src, out_idx, out_dist, st);
     } else if (engine == GUMAP_ENGINE_BATCH) {
-        if (!h->batch || sources) return fail(GUMAP_ERR_INVALID_ARG, "the batched engine needs a batch handle and sources == NULL");
-        rc = run_batch(h, out_idx, out_dist, st);
+        if (sources) {
+            // the batched engine runs every vertex of its units; a single graph's
+            // explicit sources go to the MS-BFS engine
+            if (h->batch) return fail(GUMAP_ERR_INVALID_ARG, "the batched engine needs sources == NULL");
+            h->last_engine = GUMAP_ENGINE_MSBFS;
+            rc = run_msbfs(h, src, false, n_src, out_idx, out_dist, st);
+        } else {
+            rc = run_batch(h, out_idx, out_dist, st);
+        }
     } else {
         return fail(GUMAP_ERR_INVALID_ARG, "engine %d not available", engine);
     }
@@ -989,6 +998,7 @@ int apply_batch_plan(gumap_knn* h, int32_t max_w) {
     CK(cudaMemcpy(h->d_units, sorted.data(), sizeof(BatchUnit) * sorted.size(), cudaMemcpyHostToDevice),
        "batch units");
     h->batch_width = max_w;
+    h->batch_planned = true;
     return GUMAP_OK;
 }
 
@@ -1254,8 +1264,15 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
         case GUMAP_OPT_ENGINE:
             if (value < GUMAP_ENGINE_AUTO || value > GUMAP_ENGINE_BATCH || value == GUMAP_ENGINE_MSBFS_SM)
                 return fail(GUMAP_ERR_INVALID_ARG, "bad engine");
-            if (value == GUMAP_ENGINE_BATCH && !h->batch)
-                return fail(GUMAP_ERR_INVALID_ARG, "the batched engine needs a handle from gumap_batch_create");
+            if (value == GUMAP_ENGINE_BATCH && !h->batch && !h->batch_planned) {
+                // a single graph as a one-graph batch (TOO_LARGE when it does not fit a CTA)
+                CK(cudaSetDevice(h->device), "cudaSetDevice");
+                CK(cudaDeviceSynchronize(), "sync");
+                h->batch_offsets = {0, h->n};
+                h->batch_modes = {h->mode};
+                h->batch_edges = {h->nnz};
+                if (int rc = apply_batch_plan(h, kMaxBatchW)) return rc;
+            }
             if (value == GUMAP_ENGINE_FRONTIER && h->mode != GUMAP_PARTIAL)
                 return fail(GUMAP_ERR_INVALID_ARG, "the frontier engine computes the partial form only");
             h->opt_engine = (int)value;
@@ -1280,7 +1297,8 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
             h->opt_pull_width = (int)value;
             return GUMAP_OK;
         case GUMAP_OPT_BATCH_WIDTH:
-            if (!h->batch) return fail(GUMAP_ERR_INVALID_ARG, "batch width applies to batch handles");
+            if (!h->batch && !h->batch_planned)
+                return fail(GUMAP_ERR_INVALID_ARG, "batch width applies to batch handles and the batched engine");
             if (value < 0 || value > kMaxBatchW) return fail(GUMAP_ERR_INVALID_ARG, "batch width must be in [0, 64]");
             CK(cudaSetDevice(h->device), "cudaSetDevice");
             CK(cudaDeviceSynchronize(), "sync");

@@ -7,7 +7,9 @@
 // those the CTAs per SM (the CTA shape), the staging of rows in shared
 // memory and the automatic level direction at three push thresholds; for the
 // partial form the engine and the frontier engine's merge (one thread or
-// one warp per source); for batch handles the widest unit (the
+// one warp per source); for single graphs that fit a CTA's shared memory
+// also the batched engine with four unit widths; for batch handles the
+// widest unit (the
 // source-block width of the batched engine). Each candidate runs once to
 // warm up, then three times with the L2 flushed before each run; the median
 // device time decides. The winner is kept in a JSON-lines cache under a key
@@ -60,9 +62,9 @@ bool read_cache(const char* path, const std::string& key, Setting* s) {
         if (sscanf(line.c_str(),
                    "{\"key\": \"%199[^\"]\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, "
                    "\"direction\": %d, \"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, "
-                   "\"push_div\": %d, \"frontier_build\": %d, \"ms\": %lf}",
+                   "\"push_div\": %d, \"frontier_build\": %d, \"batch_width\": %d, \"ms\": %lf}",
                    k, &t.engine, &t.pull_width, &t.heavy_mult, &t.direction, &t.state_bytes, &t.ctas_per_sm,
-                   &t.stage, &t.push_div, &t.frontier_build, &ms) == 11 &&
+                   &t.stage, &t.push_div, &t.frontier_build, &t.batch_width, &ms) == 12 &&
             key == k) {
             *s = t;  // the last entry of a key wins
             found = true;
@@ -77,9 +79,9 @@ void append_cache(const char* path, const std::string& key, const Setting& s, do
     fprintf(f,
             "{\"key\": \"%s\", \"engine\": %d, \"pull_width\": %d, \"heavy_mult\": %d, \"direction\": %d, "
             "\"state_bytes\": %lld, \"ctas_per_sm\": %d, \"stage\": %d, \"push_div\": %d, "
-            "\"frontier_build\": %d, \"ms\": %.6f}\n",
+            "\"frontier_build\": %d, \"batch_width\": %d, \"ms\": %.6f}\n",
             key.c_str(), s.engine, s.pull_width, s.heavy_mult, s.direction, s.state_bytes, s.ctas_per_sm, s.stage,
-            s.push_div, s.frontier_build, ms);
+            s.push_div, s.frontier_build, s.batch_width, ms);
     fclose(f);
 }
 
@@ -87,6 +89,7 @@ int apply(gumap_knn* h, const gumap_knn_info& in, const Setting& s) {
     int rc;
     if (in.batch) return gumap_knn_set_option(h, GUMAP_OPT_BATCH_WIDTH, s.batch_width);
     if ((rc = gumap_knn_set_option(h, GUMAP_OPT_ENGINE, s.engine))) return rc;
+    if (s.engine == GUMAP_ENGINE_BATCH) return gumap_knn_set_option(h, GUMAP_OPT_BATCH_WIDTH, s.batch_width);
     if (s.engine == GUMAP_ENGINE_FRONTIER &&
         (rc = gumap_knn_set_option(h, GUMAP_OPT_FRONTIER_BUILD, s.frontier_build)))
         return rc;
@@ -102,6 +105,19 @@ int apply(gumap_knn* h, const gumap_knn_info& in, const Setting& s) {
             return rc;
     }
     return GUMAP_OK;
+}
+
+// A single graph small enough for one CTA's shared memory may run on the
+// batched engine (a level costs a __syncthreads instead of a grid barrier):
+// units of 32, 8, 2 and 1 words.
+void add_batch_candidates(const gumap_knn_info& in, std::vector<Setting>& cands) {
+    if (in.batch || in.n > 27000) return;
+    for (int w : {32, 8, 2, 1}) {
+        Setting s;
+        s.engine = GUMAP_ENGINE_BATCH;
+        s.batch_width = w;
+        cands.push_back(s);
+    }
 }
 
 }  // namespace
@@ -196,6 +212,7 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
             cands.push_back(s);
         }
     } else if (in.mode == GUMAP_FULL) {
+        add_batch_candidates(in, cands);
         for (long long budget : {96ll << 20, 256ll << 20, 1024ll << 20})
             for (int width : {4, 2})
                 for (int hm : {2, 4, 8}) {
@@ -208,6 +225,7 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
                     cands.push_back(s);
                 }
     } else {
+        add_batch_candidates(in, cands);
         // the frontier engine's merges (a group of lanes, one thread or one warp per source)
         for (int b : {3, 1, 2}) {
             if (b == 1 && in.k > 64) continue;  // the thread build covers k <= 64
@@ -237,7 +255,9 @@ extern "C" int gumap_knn_autotune(gumap_knn* h, const char* cache_path, gumap_tu
     double best_ms = 1e300;
     for (const Setting& s : cands) {
         double ms = 0.0;
-        if ((rc = apply(h, in, s)) || (rc = time_run(&ms))) {
+        rc = apply(h, in, s);
+        if (rc == GUMAP_ERR_TOO_LARGE && s.engine == GUMAP_ENGINE_BATCH) continue;  // the graph does not fit a CTA
+        if (rc || (rc = time_run(&ms))) {
             cleanup();
             return rc;
         }

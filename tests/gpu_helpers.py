@@ -13,7 +13,7 @@ SIGMA_RTOL = 1e-5  # relative tolerance on sigma
 
 
 def run_gpu(g, k, mode="full", engine=None, block_bits=None, sources=None, directed=False, coo=True,
-            direction=None, coo_build=None, frontier_build=None):
+            direction=None, coo_build=None, frontier_build=None, batch_width=None):
     flags = gumap.WEIGHTS_DIRECTED if directed else gumap.WEIGHTS_UNION
     m = gumap.FULL if mode == "full" else gumap.PARTIAL
     with gumap.KnnGraph.from_graph(g, k, mode=m, flags=flags) as kg:
@@ -27,6 +27,8 @@ def run_gpu(g, k, mode="full", engine=None, block_bits=None, sources=None, direc
             kg.set_option(gumap.OPT_COO_BUILD, coo_build)
         if frontier_build is not None:
             kg.set_option(gumap.OPT_FRONTIER_BUILD, frontier_build)
+        if batch_width is not None:
+            kg.set_option(gumap.OPT_BATCH_WIDTH, batch_width)
         src_t = None
         if sources is not None:
             src_t = torch.as_tensor(np.asarray(sources, dtype=np.int32), device="cuda")

@@ -66,6 +66,28 @@ def test_zoo_partial_frontier_builds(g, k, build):
                   f"{g.name} partial/frontier build {build} k={k}")
 
 
+@pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
+def test_zoo_single_graph_on_the_batched_engine(g, k):
+    """A single graph small enough for one CTA runs on the batched engine
+    (shared-memory bitsets, __syncthreads levels) with the oracle's rows, in
+    both forms and at several unit widths."""
+    for mode in ("full", "partial"):
+        ref = oracle_ref(g, k, mode)
+        for width in (None, 2):
+            res = run_gpu(g, k, mode, engine=gumap.ENGINE_BATCH, batch_width=width)
+            assert_parity(res, ref, f"{g.name} {mode} k={k} batched engine width {width}")
+            assert res["stats"]["engine"] == gumap.ENGINE_BATCH
+
+
+def test_batched_engine_with_explicit_sources_uses_msbfs():
+    g = gg.grid(20, 17)
+    src = [5, 300, 5, 0, 339]
+    ref = oracle_ref(g, 7, "full", sources=src, directed=True)
+    res = run_gpu(g, 7, "full", engine=gumap.ENGINE_BATCH, sources=src, directed=True)
+    assert_parity(res, ref, "explicit sources on the batched engine")
+    assert res["stats"]["engine"] == gumap.ENGINE_MSBFS
+
+
 @pytest.mark.parametrize("direction", [gumap.DIRECTION_PULL, gumap.DIRECTION_PUSH])
 @pytest.mark.parametrize("g,k", CASES, ids=[f"{g.name}-k{k}" for g, k in CASES])
 def test_zoo_forced_direction(g, k, direction):
