@@ -71,9 +71,12 @@ def parse_args():
                         "graphs; batch: the 2000-graph batching comparison; serve: the request-stream "
                         "latency sweep")
     p.add_argument("--batch-graphs", type=int, default=2000)
-    p.add_argument("--serve-requests", type=int, default=1000)
+    p.add_argument("--serve-requests", type=int, default=10000)
     p.add_argument("--serve-n-cap", type=int, default=200000)
-    p.add_argument("--serve-rates", type=float, nargs="*", default=[0.5, 0.9])
+    p.add_argument("--serve-rates", type=float, nargs="*", default=[0.25, 0.5, 0.75, 0.9, 1.0, 1.2])
+    p.add_argument("--no-extras", action="store_true",
+                   help="headline line only: skip the summaries of the other workloads (config 1, partial form, "
+                        "batching, serving, quality metrics, spectral layout)")
     return p.parse_args()
 
 
@@ -244,12 +247,10 @@ def frontier_alg_bytes(entries, rows, k):
 
 
 def coo_alg_bytes(n, k, nnz):
-    """Algorithmic bytes of one COO build (gumap_knn_run with union weights),
-    after the union kernel: the row scan reads the per-row counts and writes
-    the row offsets (16 n); the scatter reads each slot's id, weight and
-    mirror place (12 n k) and writes every entry's column and weight
-    (8 nnz); the row sorts read those and write the sorted rows (16 nnz)."""
-    return 16 * n + 12 * n * k + 24 * nnz
+    """Algorithmic bytes of one COO build (gumap_knn_run with union weights):
+    every slot's id and weight read once (8 n k), every entry's column and
+    weight written once (8 nnz), the row offsets written (8 n)."""
+    return 8 * n * k + 8 * nnz + 8 * n
 
 
 def cpu_cores():
@@ -257,6 +258,40 @@ def cpu_cores():
         return len(os.sched_getaffinity(0))
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def oracle_union_rows(g, k, mode, rows):
+    """The oracle's lists, distances and union weights of the given rows, for
+    the CPU-baseline legs' parity figures. Only oracle functions compute: the
+    lists of the rows and of every vertex they list, the FP64 weights of
+    those lists, and the union weight of each slot of the rows, whose reverse
+    weight comes from the target's list (so the targets' rows are enough)."""
+    import numpy as np
+
+    import oracle
+    knn = oracle.knn_full if mode == "full" else oracle.knn_partial
+    rows = np.asarray(rows, dtype=np.int32)
+    idx_r, _ = knn(g, k, sources=rows)
+    verts = np.unique(np.concatenate([rows, idx_r[idx_r >= 0]])).astype(np.int32)
+    idx_v, dist_v = knn(g, k, sources=verts)
+    _, _, a_v = oracle.smooth_knn(dist_v)
+    pos = np.full(g.n, -1, dtype=np.int32)
+    pos[verts] = np.arange(len(verts), dtype=np.int32)
+    # compact ids; ids outside `verts` appear only in targets' rows, where no lookup of a row's slot reads them
+    idx_c = np.where(idx_v >= 0, pos[np.maximum(idx_v, 0)], -1).astype(np.int32)
+    w_c = oracle.slot_union(idx_c, a_v)
+    sel = pos[rows]
+    return idx_v[sel], dist_v[sel], w_c[sel]
+
+
+def sampled_parity(g, k, mode, idx, dist, w, rows):
+    """Rows of the GPU's output against the oracle's: (rows whose ids or
+    distances differ, max |w_gpu - w_oracle|)."""
+    import numpy as np
+    ri, rd, rw = oracle_union_rows(g, k, mode, rows)
+    gi, gd, gw = idx[rows], dist[rows], w[rows].astype(np.float64)
+    bad = int(np.sum(np.any(gi != ri, axis=1) | np.any(gd != rd, axis=1)))
+    return bad, float(np.max(np.abs(gw - rw))) if rw.size else 0.0
 
 
 def oracle_sample(graphs, works, budget_s):
@@ -550,6 +585,15 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, desc, _ = oracle_sample(graphs, works, args.cpu_seconds)
         cpu = {"value": v, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": desc}
+        # parity of the timed run's rows on a seeded sample: ids and distances exact, weights vs FP64
+        bad, dw = 0, 0.0
+        for g, o in zip(graphs, outs):
+            rows = np.random.default_rng(4321).choice(g.n, size=min(g.n, 200), replace=False).astype(np.int32)
+            b, e = sampled_parity(g, K_NEIGHBOURS, "full", o["idx"].cpu().numpy(), gumap.dist_u16(o["dist"]),
+                                  o["w"].cpu().numpy(), rows)
+            bad, dw = bad + b, max(dw, e)
+        cpu["parity"] = {"rows_checked": sum(min(g.n, 200) for g in graphs), "rows_differing": bad,
+                         "max_abs_dw": dw}
         procs = min(cpu_cores(), 64)
         if procs > 1:
             try:
@@ -557,6 +601,12 @@ def run_ours(args):
                 cpu_all = {"value": v, "unit": "GTEPS", "cores": procs, "kind": "oracle", "sample": desc}
             except Exception as e:  # a reported baseline only: never lose the bench line over it
                 cpu_all = {"unavailable": f"{type(e).__name__}: {e}"}
+
+    for kg in kgs:
+        kg.close()
+    extras = {}
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras = run_extras(args)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -574,17 +624,17 @@ def run_ours(args):
                                          for t in tuned]},
                 "roofline": roofline, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all, "e2e": e2e,
                 "gpu_launches": gpu_launches, "clocks": clocks}
+        line.update(extras)
         print(json.dumps(line), flush=True)
-    for kg in kgs:
-        kg.close()
     if world > 1:
         dist.destroy_process_group()
 
 
-def run_batch_workload(args):
+def run_batch_workload(args, emit=True):
     """Batching (the 2000-graph mix, k = 15): graphs/s of one persistent
     launch per step (gumap_batch_create) against one handle and one run per
-    graph on the same GPU and stream. Prints its own JSON line."""
+    graph on the same GPU and stream. Returns its JSON line (printed when
+    emit)."""
     import torch
 
     from paper_2509_19703_gb300 import graphgen as gg
@@ -608,8 +658,9 @@ def run_batch_workload(args):
             ts.append(a.elapsed_time(b))
         return statistics.median(ts)
 
-    kb, _ = gumap.KnnGraph.batch(graphs, K_NEIGHBOURS, modes)
+    kb, offs = gumap.KnnGraph.batch(graphs, K_NEIGHBOURS, modes)
     tuned = kb.autotune()  # the widest unit (source-block width), timed before any timed step
+    kb.set_option(gumap.OPT_PROFILE, 1)
     out = kb.alloc_outputs(kb.n)
     for _ in range(args.warmup):
         kb.run(out=out)
@@ -619,6 +670,37 @@ def run_batch_workload(args):
     st = kb.stats()
     kb.check()
     kb.close()
+    # roofline of the batched engine: its units' bytes on the per-level model of
+    # the bit-parallel BFS (the bitset rows live in shared memory here) over its
+    # own launch time
+    peak, peak_kind = measured_peak_gbs()
+    bfs_ms = st["bfs_ms"] / max(1, st["bfs_launches"])
+    model = st["batch_model_bytes"] / max(1, st["bfs_launches"])
+    achieved = model / (bfs_ms * 1e-3) / 1e9 if bfs_ms > 0 else 0.0
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if peak else None, "traffic": None, "peak_source": peak_kind,
+                "kernel": "batch_kernel", "avg_launch_ms": bfs_ms, "model_bytes_per_launch": model,
+                "kernel_share_of_step": bfs_ms / ms_batch if ms_batch else None,
+                "model": "per unit and level 12 n W (frontier, visited, next rows; shared memory here) + the "
+                         "graph's CSR 4 (n + 1) + 4 nnz"}
+    parity = None
+    if not args.no_cpu_baseline:  # a seeded sample of the graphs against the oracle (all rows of each)
+        import numpy as np
+
+        import oracle
+        idx = out["idx"].cpu().numpy()
+        dist = gumap.dist_u16(out["dist"])
+        w = out["w"].cpu().numpy().astype(np.float64)
+        pick = np.random.default_rng(44).choice(len(graphs), size=min(len(graphs), 40), replace=False)
+        bad, dw = 0, 0.0
+        for gi in pick:
+            g, m = graphs[gi], items[gi].mode
+            ref = oracle.knn_pipeline(g, K_NEIGHBOURS, m)
+            lo, hi = int(offs[gi]), int(offs[gi + 1])
+            li = np.where(idx[lo:hi] >= 0, idx[lo:hi] - lo, -1)
+            bad += int(np.sum(np.any(li != ref["idx"], axis=1) | np.any(dist[lo:hi] != ref["dist"], axis=1)))
+            dw = max(dw, float(np.max(np.abs(w[lo:hi] - ref["w"]))))
+        parity = {"graphs_checked": len(pick), "rows_differing": bad, "max_abs_dw": dw}
 
     singles = [gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=m) for g, m in zip(graphs, modes)]
     souts = [s.alloc_outputs(g.n) for s, g in zip(singles, graphs)]
@@ -645,17 +727,20 @@ def run_batch_workload(args):
                        "l2": "flushed (512 MB write) before each timed step"},
             "one_launch_per_graph": {"graphs_per_s": len(graphs) / (ms_single * 1e-3), "ms_per_step": ms_single},
             "speedup_vs_one_launch_per_graph": ms_single / ms_batch,
+            "roofline": roofline, "parity": parity,
             "gpu_launches": st["kernel_launches"]}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
 
 
-def run_partial_workload(args):
+def run_partial_workload(args, emit=True):
     """Partial form (SL-GUMAP, Algorithm 4) on the two 1,000,000-vertex
     graphs at k = 15 and k = 50: one step runs gumap_knn_run (kNN lists,
     weights, union, sorted COO, all sources) for each (graph, k). Work per
     source: the adjacency entries of the vertices it expands (closer than
     the distance of its k-th neighbour) / 2, counted from the lists.
-    Prints its own JSON line."""
+    Returns its JSON line (printed when emit)."""
     import numpy as np
     import torch
 
@@ -728,22 +813,23 @@ def run_partial_workload(args):
     value = work_per_step / (ms * 1e-3) / 1e9
     stage_ms = {key: sum(r[key] for r in per_run) for key in ("engine_ms", "weights_ms", "coo_ms")}
 
-    # roofline of the kernel that takes the largest share of the step
+    # roofline of the BFS engine (the partial BFS of Algorithm 4); the other
+    # stages' model fractions beside it
     peak, peak_kind = measured_peak_gbs()
-    if stage_ms["coo_ms"] > stage_ms["engine_ms"]:
-        kernel, t_ms = "COO build (row_scan + scatter + row sorts)", stage_ms["coo_ms"]
-        alg = sum(r["coo_alg_bytes"] for r in per_run)
-        launches = sum(r["coo_launches"] for r in per_run)
-    else:
-        kernel, t_ms = "BFS engine (frontier_kernel)", stage_ms["engine_ms"]
-        alg = sum(r["engine_alg_bytes"] for r in per_run)
-        launches = sum(r["engine_launches"] for r in per_run)
+    t_ms = stage_ms["engine_ms"]
+    alg = sum(r["engine_alg_bytes"] for r in per_run)
+    launches = sum(r["engine_launches"] for r in per_run)
     achieved = alg / (t_ms * 1e-3) / 1e9 if t_ms > 0 else 0.0
+    coo_alg = sum(r["coo_alg_bytes"] for r in per_run)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if peak else None, "traffic": None, "peak_source": peak_kind,
-                "kernel": kernel, "launches_per_step": launches, "alg_bytes_per_step": alg,
+                "kernel": "BFS engine (frontier kernels, merge build per graph by the autotuner)",
+                "launches_per_step": launches, "alg_bytes_per_step": alg,
+                "avg_launch_ms": t_ms / launches if launches else None,
                 "kernel_share_of_step": t_ms / ms if ms else None,
-                "stage_ms_per_step": stage_ms}
+                "stage_ms_per_step": stage_ms,
+                "coo_stage": {"alg_bytes_per_step": coo_alg,
+                              "achieved_gbs": coo_alg / (stage_ms["coo_ms"] * 1e-3) / 1e9 if stage_ms["coo_ms"] else None}}
     gpu_launches = sum(st["kernel_launches"] for st in stats)
 
     e2e = None
@@ -795,6 +881,14 @@ def run_partial_workload(args):
             parts.append(f"{done} of {g.n} sources of {g.name} at k={k}")
         cpu = {"value": total_work / 2 / total_t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
                "sample": "; ".join(parts) + " (seeded random order, partial BFS + FP64 weights, 1 thread)"}
+        # parity of the timed runs' rows on a seeded sample of each (graph, k)
+        bad, dw, checked = 0, 0.0, 0
+        for (g, k), o in zip(runs, outs):
+            rows = np.random.default_rng(4322).choice(g.n, size=200, replace=False).astype(np.int32)
+            b, e = sampled_parity(g, k, "partial", o["idx"].cpu().numpy(), gumap.dist_u16(o["dist"]),
+                                  o["w"].cpu().numpy(), rows)
+            bad, dw, checked = bad + b, max(dw, e), checked + len(rows)
+        cpu["parity"] = {"rows_checked": checked, "rows_differing": bad, "max_abs_dw": dw}
 
     for r in per_run:
         r.pop("entries")
@@ -811,9 +905,11 @@ def run_partial_workload(args):
                                      for t in tuned]},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
             "clocks": clocks}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
     for kg in kgs:
         kg.close()
+    return line
 
 
 def serve_requests(count, seed, n_cap):
@@ -843,29 +939,37 @@ def serve_requests(count, seed, n_cap):
     return out
 
 
-def run_serve_workload(args):
+def run_serve_workload(args, emit=True):
     """Serving: a Poisson stream of config-5 requests through gumap_server_*;
     saturated graphs/s, then p50/p99 latency (submit to completion, server
-    clock) at offered rates below saturation; against the same requests run
-    one handle at a time."""
+    clock) at offered rates around saturation, overall and per request class
+    (graphs that a batched launch takes, n <= 27,000, or larger ones that run
+    alone; partial or full form); against the same requests run one handle at
+    a time. A seeded sample of the saturated run's results is read back and
+    compared with the oracle. Returns its JSON line (printed when emit)."""
     import numpy as np
     import torch
 
-    from paper_2509_19703_gb300 import graphgen as gg
     from paper_2509_19703_gb300 import gumap
 
     torch.cuda.set_device(0)
     reqs = serve_requests(args.serve_requests, 5, args.serve_n_cap)
     budget = 64 << 30
+    small_n = 27000
 
-    def run_stream(rate):
+    def cls(g, m):
+        return ("small" if g.n <= small_n else "large") + ("_partial" if m == gumap.PARTIAL else "_full")
+
+    def pct(x, q):
+        return float(np.percentile(np.asarray(x), q) * 1e3) if len(x) else None
+
+    def run_stream(rate, sub, check=()):
         s = gumap.gumap_server_create(0, budget)
         rng = np.random.default_rng(55)
-        gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+        gaps = rng.exponential(1.0 / rate, size=len(sub)) if rate else np.zeros(len(sub))
         ids = []
-        t_start = time.perf_counter()
-        t_next = t_start
-        for (g, k, m), gap in zip(reqs, gaps):
+        t_next = time.perf_counter()
+        for (g, k, m), gap in zip(sub, gaps):
             t_next += gap
             while time.perf_counter() < t_next:
                 pass
@@ -878,29 +982,55 @@ def run_serve_workload(args):
                         raise
                     time.sleep(0.0005)
         lat, t_first, t_last, batched = [], None, 0.0, []
-        for rid in ids:
+        by_cls = {}
+        rows = {}
+        for i, rid in enumerate(ids):
             st, r = gumap.gumap_serve_wait(s, rid, 600.0)
             assert st == gumap.OK, gumap.gumap_status_string(st)
             lat.append(r["t_done"] - r["t_submit"])
+            by_cls.setdefault(cls(sub[i][0], sub[i][2]), []).append(r["t_done"] - r["t_submit"])
             t_first = r["t_submit"] if t_first is None else min(t_first, r["t_submit"])
             t_last = max(t_last, r["t_done"])
             batched.append(r["batch_graphs"])
+            if i in check:
+                g, k, _ = sub[i]
+                o = dict(idx=torch.empty((g.n, k), dtype=torch.int32, device="cuda"),
+                         dist=torch.empty((g.n, k), dtype=torch.int16, device="cuda"),
+                         w=torch.empty((g.n, k), dtype=torch.float32, device="cuda"))
+                gumap.gumap_serve_read(s, rid, o["idx"], o["dist"], o["w"])
+                torch.cuda.synchronize()
+                rows[i] = (o["idx"].cpu().numpy(), gumap.dist_u16(o["dist"]), o["w"].cpu().numpy())
             gumap.gumap_serve_release(s, rid)
         stats = gumap.gumap_server_get_stats(s)
         gumap.gumap_server_destroy(s)
-        lat = np.array(lat)
-        return {"graphs_per_s": len(ids) / (t_last - t_first), "p50_ms": float(np.percentile(lat, 50) * 1e3),
-                "p99_ms": float(np.percentile(lat, 99) * 1e3), "launches": stats["launches"],
-                "mean_graphs_per_launch": float(np.mean(batched)),
-                "arena_peak_gb": stats["arena_peak_bytes"] / 2**30}
+        res = {"graphs_per_s": len(ids) / (t_last - t_first), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+               "launches": stats["launches"], "mean_graphs_per_launch": float(np.mean(batched)),
+               "arena_peak_gb": stats["arena_peak_bytes"] / 2**30,
+               "by_class": {c: {"requests": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99)}
+                            for c, v in sorted(by_cls.items())}}
+        return res, rows
 
-    run_stream(0)  # warm-up (module loading, allocator)
-    sat = run_stream(0)
+    run_stream(0, reqs[:500])  # warm-up (module loading, allocator)
+    check = set()
+    if not args.no_cpu_baseline:  # a seeded sample of graphs small enough for the oracle's full BFS
+        cand = [i for i, (g, _, _) in enumerate(reqs) if g.n <= 3000]
+        check = set(int(i) for i in np.random.default_rng(56).choice(cand, size=min(len(cand), 40), replace=False))
+    sat, rows = run_stream(0, reqs, check)
     points = []
     for frac in args.serve_rates:
-        p = run_stream(frac * sat["graphs_per_s"])
+        p, _ = run_stream(frac * sat["graphs_per_s"], reqs)
         p["offered_rate_frac"] = frac
         points.append(p)
+    parity = None
+    if check:
+        import oracle
+        bad, dw = 0, 0.0
+        for i, (gi, gd, gw) in rows.items():
+            g, k, m = reqs[i]
+            ref = oracle.knn_pipeline(g, k, "partial" if m == gumap.PARTIAL else "full")
+            bad += int(np.sum(np.any(gi != ref["idx"], axis=1) | np.any(gd != ref["dist"], axis=1)))
+            dw = max(dw, float(np.max(np.abs(gw.astype(np.float64) - ref["w"]))))
+        parity = {"requests_checked": len(rows), "rows_differing": bad, "max_abs_dw": dw}
 
     # baseline: the same requests, one handle and one synchronous run each
     t0 = time.perf_counter()
@@ -909,6 +1039,9 @@ def run_serve_workload(args):
             kg.run()
             kg.check()
     single = len(reqs) / (time.perf_counter() - t0)
+    classes = {}
+    for g, _, m in reqs:
+        classes[cls(g, m)] = classes.get(cls(g, m), 0) + 1
     line = {"metric": "served graphs/s with p50/p99 latency (config-5 request stream)",
             "value": sat["graphs_per_s"], "unit": "graphs/s", "n_gpus": 1, "steps": len(reqs), "warmup": 1,
             "ms_per_step": 1e3 / sat["graphs_per_s"], "higher_is_better": True, "scaling": "weak",
@@ -916,11 +1049,178 @@ def run_serve_workload(args):
             "config": {"workload": "config 5: Poisson stream, n lognormal median 5000 sigma_ln 1.0 clamped "
                                    f"[64, {args.serve_n_cap}], BA/grid/G(n,p) thirds, 70% partial / 30% full, "
                                    "k in {15, 30}, 64 GiB budget", "requests": len(reqs),
-                       "vertices": int(sum(g.n for g, _, _ in reqs))},
-            "saturated": sat, "latency_sweep": points,
+                       "vertices": int(sum(g.n for g, _, _ in reqs)), "classes": classes},
+            "saturated": sat, "latency_sweep": points, "parity": parity,
             "one_handle_per_request_graphs_per_s": single,
             "speedup_vs_one_handle_per_request": sat["graphs_per_s"] / single}
-    print(json.dumps(line), flush=True)
+    if emit:
+        print(json.dumps(line), flush=True)
+    return line
+
+
+def event_ms(fn, reps=20, warm=3):
+    """Median device time of fn() on the current stream (CUDA events)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def config1_summary(args):
+    """Config 1: the 32 x 32 grid, full form, k = 15, every source, weights,
+    union and COO through gumap_knn_run, after the autotuner; the default
+    engine beside it; every row against the oracle."""
+    import numpy as np
+
+    from paper_2509_19703_gb300 import graphgen as gg
+    from paper_2509_19703_gb300 import gumap
+    g = gg.grid(32, 32)
+    kg = gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=gumap.FULL)
+    out = kg.alloc_outputs(g.n)
+    default_ms = event_ms(lambda: kg.run(out=out))
+    tuned = kg.autotune()
+    ms = event_ms(lambda: kg.run(out=out), reps=50)
+    kg.check()
+    res = {"workload": "grid 32x32 (n=1024, m=1984), full form, k=15, all sources, weights + union + sorted COO",
+           "ms_per_run": ms, "default_engine_ms_per_run": default_ms,
+           "gteps": 1024 * 1984 / (ms * 1e-3) / 1e9,
+           "autotuned": {key: tuned[key] for key in ("engine", "batch_width", "best_ms")}}
+    if not args.no_cpu_baseline:
+        import oracle
+        ref = oracle.knn_pipeline(g, K_NEIGHBOURS, "full")
+        idx, dist = out["idx"].cpu().numpy(), gumap.dist_u16(out["dist"])
+        res["parity"] = {"rows_checked": g.n,
+                         "rows_differing": int(np.sum(np.any(idx != ref["idx"], axis=1) |
+                                                      np.any(dist != ref["dist"], axis=1))),
+                         "max_abs_dw": float(np.max(np.abs(out["w"].cpu().numpy().astype(np.float64) - ref["w"])))}
+    kg.close()
+    return res
+
+
+def quality_summary(args):
+    """Quality metrics (Section 4.1.3) of a seeded drawing of each headline
+    graph: neighbourhood preservation (r = 2) and stress, device time; the
+    oracle on a seeded sample of vertices, timed, and compared."""
+    import numpy as np
+    import torch
+
+    from paper_2509_19703_gb300 import gumap
+    res = {}
+    for g in build_graphs(None):
+        X = np.random.default_rng(9).standard_normal((g.n, 2)).astype(np.float32)
+        Xd = torch.as_tensor(X, device="cuda")
+        kg = gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=gumap.FULL)
+        got = {}
+
+        def np_run():
+            got["np"] = kg.quality_np(Xd, 2)
+
+        def st_run():
+            got["st"] = kg.quality_stress(Xd)
+
+        np_ms = event_ms(np_run, reps=5, warm=1)
+        st_ms = event_ms(st_run, reps=5, warm=1)
+        kg.check()
+        r = {"n": g.n, "np_ms": np_ms, "np_vertices_per_s": g.n / (np_ms * 1e-3),
+             "np": float(got["np"][2].item()), "stress_ms": st_ms,
+             "stress_pairs_per_s": g.n * (g.n - 1) / (st_ms * 1e-3), "stress": float(got["st"][0].item())}
+        if not args.no_cpu_baseline:
+            import oracle
+            sample = np.random.default_rng(10).choice(g.n, size=20, replace=False).astype(np.int32)
+            t0 = time.perf_counter()
+            rc, ri, _ = oracle.np_metric(g, X, 2, vertices=sample)
+            t_np = time.perf_counter() - t0
+            t0 = time.perf_counter()
+            _, rr = oracle.stress(g, X, vertices=sample)
+            t_st = time.perf_counter() - t0
+            c, inter = got["np"][0].cpu().numpy(), got["np"][1].cpu().numpy()
+            rows = got["st"][1].cpu().numpy()
+            r["cpu_baseline"] = {"kind": "oracle", "cores": 1, "sample": f"{len(sample)} seeded vertices",
+                                 "np_vertices_per_s": len(sample) / t_np,
+                                 "stress_pairs_per_s": len(sample) * (g.n - 1) / t_st}
+            r["parity"] = {"np_counts_equal": bool(np.array_equal(c[sample], rc) and np.array_equal(inter[sample], ri)),
+                           "stress_rows_max_rel_err": float(np.max(np.abs(rows[sample] - rr) / np.abs(rr)))}
+        res[g.name] = r
+        kg.close()
+    return res
+
+
+def spectral_summary(args):
+    """Spectral layout (2 coordinates) of the headline graphs' union kNN
+    graphs after a full-form run: device time, Lanczos steps, residual; the
+    oracle's dense eigensolve timed on a smaller union graph (grid 40 x 40),
+    where both are compared."""
+    import numpy as np
+    import torch
+
+    from paper_2509_19703_gb300 import graphgen as gg
+    from paper_2509_19703_gb300 import gumap
+    res = {}
+    for g in build_graphs(None) + [gg.grid(40, 40)]:
+        kg = gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=gumap.FULL)
+        kg.run()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X, mu, info = kg.spectral_layout(2)
+        ms = (time.perf_counter() - t0) * 1e3
+        r = {"n": g.n, "ms": ms, "mu": mu.tolist(), **info}
+        if g.n <= 2000 and not args.no_cpu_baseline:
+            from oracle import spectral
+            row, col, w = kg.coo()
+            row, col, w = row.cpu().numpy(), col.cpu().numpy(), w.cpu().numpy().astype(np.float64)
+            t0 = time.perf_counter()
+            Xr, mur = spectral.spectral_layout(g.n, row, col, w, 2)
+            r["cpu_baseline"] = {"kind": "oracle", "cores": 1, "ms": (time.perf_counter() - t0) * 1e3,
+                                 "sample": "the whole graph (dense FP64 eigensolve)"}
+            Xg = X.cpu().numpy().astype(np.float64)
+            r["parity"] = {"max_abs_dmu": float(np.max(np.abs(mu - mur))),
+                           "max_abs_dx_up_to_sign": float(max(min(np.max(np.abs(Xg[:, c] - Xr[:, c])),
+                                                                  np.max(np.abs(Xg[:, c] + Xr[:, c])))
+                                                              for c in range(2)))}
+        res[g.name] = r
+        kg.close()
+    return res
+
+
+def summary_of(line, keys):
+    return {key: line.get(key) for key in keys}
+
+
+def run_extras(args):
+    """Summaries of the other workloads for the headline line (each also has
+    its own --workload line): config 1, the partial form (config 3), batching
+    (config 4), serving (config 5), the quality metrics and the spectral
+    layout."""
+    import copy
+    out = {}
+    out["config1"] = config1_summary(args)
+    pa = copy.copy(args)
+    pa.steps, pa.warmup, pa.e2e_steps, pa.cpu_seconds, pa.only, pa.frontier_build = 10, 3, 2, 4.0, None, "tuned"
+    line = run_partial_workload(pa, emit=False)
+    out["partial_form"] = summary_of(line, ("metric", "value", "unit", "ms_per_step", "roofline", "cpu_baseline",
+                                            "e2e", "gpu_launches", "clocks"))
+    out["partial_form"]["stage_ms_per_step"] = line["roofline"]["stage_ms_per_step"]
+    ba = copy.copy(args)
+    ba.steps, ba.warmup, ba.batch_graphs = 3, 1, 2000
+    line = run_batch_workload(ba, emit=False)
+    out["batched"] = summary_of(line, ("metric", "value", "unit", "ms_per_step", "one_launch_per_graph",
+                                       "speedup_vs_one_launch_per_graph", "roofline", "parity", "gpu_launches"))
+    line = run_serve_workload(args, emit=False)
+    out["served"] = summary_of(line, ("metric", "value", "unit", "saturated", "latency_sweep", "parity",
+                                      "one_handle_per_request_graphs_per_s", "speedup_vs_one_handle_per_request"))
+    out["served"]["requests"] = line["config"]["requests"]
+    out["quality_metrics"] = quality_summary(args)
+    out["spectral_layout"] = spectral_summary(args)
+    return out
 
 
 def main():

@@ -276,6 +276,9 @@ typedef struct {
     double  weights_ms;      /* device time of rho/sigma, weights and union (GUMAP_OPT_PROFILE on), ms */
     double  sort_ms;         /* device time of the COO build, radix sort or rows (GUMAP_OPT_PROFILE on), ms */
     int64_t sort_launches;   /* COO build kernel launches since the last reset */
+    int64_t batch_model_bytes; /* batched engine: its units' bytes on the per-level model of the
+                                  bit-parallel BFS (3 bitset rows of n x W words, in shared memory
+                                  there, plus the CSR, per level), since the last reset */
 } gumap_knn_stats;
 
 typedef struct {
@@ -473,7 +476,8 @@ int gumap_spectral_layout(gumap_knn *h, int32_t dim, float *out_X, double *out_m
  * creation, so nothing is allocated while serving), groups waiting small
  * graphs of equal k into one batched launch (gumap_batch_create's engine),
  * runs large graphs alone, and keeps several launches in flight on separate
- * streams, so requests that arrive while others run are admitted as soon as
+ * streams (one of them reserved for small-graph batches, so long launches of
+ * large graphs never hold every stream), so requests that arrive while others run are admitted as soon as
  * a stream and memory free up and their work overlaps on the device. Results
  * stay resident in the arena until released. All calls are thread-safe.
  */

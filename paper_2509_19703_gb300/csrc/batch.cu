@@ -250,6 +250,15 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchArgs a) {
         }
         level_sum += last;
         if (last > level_max) level_max = last;
+        // the unit's bytes on the model of the global engine: per level the
+        // frontier, visited and next rows of n vertices and W words (here in
+        // shared memory) plus the graph's CSR
+        if (tid == 0) {
+            const unsigned long long nnz_g =
+                (unsigned long long)(__ldg(a.row_ptr + v0 + n) - __ldg(a.row_ptr + v0));
+            atomicAdd(&a.ctr->model_bytes, (unsigned long long)last * (12ull * (unsigned long long)n * W +
+                                                                      4ull * (unsigned long long)(n + 1) + 4ull * nnz_g));
+        }
         __syncthreads();  // the next unit reuses shared memory
     }
     if (tid == 0 && level_sum) {

@@ -1383,6 +1383,7 @@ int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
     out->weights_ms = h->weights_ms_done;
     out->sort_ms = h->sort_ms_done;
     out->sort_launches = h->sort_launches;
+    out->batch_model_bytes = (int64_t)c.model_bytes;
     return GUMAP_OK;
 }
 
@@ -1404,6 +1405,7 @@ int gumap_knn_reset_stats(gumap_knn* h) {
     c.level_sum = 0;
     c.t_init_ns = c.t_pull_ns = c.t_extract_ns = c.t_push_ns = 0;
     c.push_levels = 0;
+    c.model_bytes = 0;
     CK(cudaMemcpy(h->d_ctr, &c, sizeof(c), cudaMemcpyHostToDevice), "write counters");
     return GUMAP_OK;
 }

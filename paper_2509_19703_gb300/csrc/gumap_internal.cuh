@@ -55,6 +55,9 @@ struct DeviceCounters {
     unsigned long long t_extract_ns;
     long long push_levels;           // push levels run since the last host reset
     unsigned long long t_push_ns;    // device time of push levels (prep + push)
+    // batched engine: bytes of its units on the global engine's per-level
+    // model (bitset streams plus CSR), summed since the last host reset
+    unsigned long long model_bytes;
 };
 constexpr size_t kLaunchCounterBytes = offsetof(DeviceCounters, status);
 

@@ -6,7 +6,8 @@
 // never calls cudaMalloc or cudaFree), forms launches -- waiting small
 // graphs of the same k together in one batched launch (batch.cu), a graph too
 // large for it alone (frontier.cu for the partial form, msbfs.cu for the full
-// form) -- and keeps up to n_streams launches in flight on separate streams.
+// form) -- and keeps up to n_streams launches in flight on separate streams,
+// the last of which takes small-graph batches only.
 // Each launch runs the whole path of gumap_knn_run without the COO: BFS kNN
 // lists, rho/sigma and the weights (weights.cu), the fuzzy union, then ids made local to
 // each request's graph. A host callback enqueued after the launch stamps its
@@ -496,20 +497,32 @@ void scheduler(gumap_server* s) {
         bool progress = !done_now.empty();
         // admission and launches
         while (!s->stop && !s->waiting.empty()) {
-            int stream = -1;
-            for (int i = 0; i < (int)s->streams.size(); ++i)
+            // The last stream serves small graphs only, so large launches (a
+            // full-form BFS over a large graph runs hundreds of levels) can never
+            // hold every stream while small requests wait behind them.
+            const int ns = (int)s->streams.size();
+            int stream = -1, small_stream = -1;
+            for (int i = 0; i < ns; ++i)
                 if (s->in_flight[i] == 0) {
-                    stream = i;
+                    if (ns > 1 && i == ns - 1) small_stream = i;
+                    else if (stream < 0) stream = i;
+                }
+            // the oldest waiting request that a free stream may take
+            Request* r0 = nullptr;
+            for (Request* r : s->waiting) {
+                if (is_small(r) ? (stream >= 0 || small_stream >= 0) : stream >= 0) {
+                    r0 = r;
                     break;
                 }
-            if (stream < 0) break;
-            Request* r0 = s->waiting.front();
+            }
+            if (!r0) break;
+            if (is_small(r0) && stream < 0) stream = small_stream;
             std::vector<Request*> group{r0};
             if (is_small(r0)) {
                 long long verts = r0->n;
-                for (size_t i = 1; i < s->waiting.size() && (int)group.size() < s->opts.max_batch_graphs; ++i) {
+                for (size_t i = 0; i < s->waiting.size() && (int)group.size() < s->opts.max_batch_graphs; ++i) {
                     Request* r = s->waiting[i];
-                    if (r->k != r0->k || !is_small(r)) continue;
+                    if (r == r0 || r->k != r0->k || !is_small(r)) continue;
                     if (verts + r->n > s->opts.max_batch_vertices) break;
                     group.push_back(r);
                     verts += r->n;
@@ -529,7 +542,7 @@ void scheduler(gumap_server* s) {
                 r0->status = GUMAP_ERR_TOO_LARGE;
                 r0->t_done = s->now();
                 s->n_failed++;
-                s->waiting.pop_front();
+                s->waiting.erase(std::find(s->waiting.begin(), s->waiting.end(), r0));
                 progress = true;
                 continue;
             }

@@ -55,7 +55,8 @@ class _Stats(ctypes.Structure):
                 ("bfs_pull_ms", ctypes.c_double), ("bfs_extract_ms", ctypes.c_double),
                 ("bfs_push_ms", ctypes.c_double), ("bfs_push_levels", ctypes.c_int64),
                 ("bfs_staged_launches", ctypes.c_int64), ("weights_ms", ctypes.c_double),
-                ("sort_ms", ctypes.c_double), ("sort_launches", ctypes.c_int64)]
+                ("sort_ms", ctypes.c_double), ("sort_launches", ctypes.c_int64),
+                ("batch_model_bytes", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
