@@ -74,6 +74,8 @@ def parse_args():
     p.add_argument("--serve-requests", type=int, default=10000)
     p.add_argument("--serve-n-cap", type=int, default=200000)
     p.add_argument("--serve-rates", type=float, nargs="*", default=[0.25, 0.5, 0.75, 0.9, 1.0, 1.2])
+    p.add_argument("--serve-batch-vertices", type=int, default=0,
+                   help="server option max_batch_vertices (0: the library's default)")
     p.add_argument("--no-extras", action="store_true",
                    help="headline line only: skip the summaries of the other workloads (config 1, partial form, "
                         "batching, serving, quality metrics, spectral layout)")
@@ -964,29 +966,19 @@ def run_serve_workload(args, emit=True):
         return float(np.percentile(np.asarray(x), q) * 1e3) if len(x) else None
 
     def run_stream(rate, sub, check=()):
-        s = gumap.gumap_server_create(0, budget)
+        """Submit `sub` with Poisson gaps at `rate` (0: all at once), taking
+        every finished result back (and releasing it) while submitting, as a
+        client does; latency is submit to completion on the server clock."""
+        s = gumap.gumap_server_create(0, budget, max_batch_vertices=args.serve_batch_vertices)
         rng = np.random.default_rng(55)
         gaps = rng.exponential(1.0 / rate, size=len(sub)) if rate else np.zeros(len(sub))
-        ids = []
-        t_next = time.perf_counter()
-        for (g, k, m), gap in zip(sub, gaps):
-            t_next += gap
-            while time.perf_counter() < t_next:
-                pass
-            while True:
-                try:
-                    ids.append(gumap.gumap_serve_submit(s, g.row_ptr, g.col, g.n, g.nnz, k, m))
-                    break
-                except gumap.GumapError as e:
-                    if e.status != gumap.ERR_AGAIN:
-                        raise
-                    time.sleep(0.0005)
         lat, t_first, t_last, batched = [], None, 0.0, []
         by_cls = {}
         rows = {}
-        for i, rid in enumerate(ids):
-            st, r = gumap.gumap_serve_wait(s, rid, 600.0)
-            assert st == gumap.OK, gumap.gumap_status_string(st)
+        pending = {}
+
+        def take(i, rid, r):
+            nonlocal t_first, t_last
             lat.append(r["t_done"] - r["t_submit"])
             by_cls.setdefault(cls(sub[i][0], sub[i][2]), []).append(r["t_done"] - r["t_submit"])
             t_first = r["t_submit"] if t_first is None else min(t_first, r["t_submit"])
@@ -1001,9 +993,35 @@ def run_serve_workload(args, emit=True):
                 torch.cuda.synchronize()
                 rows[i] = (o["idx"].cpu().numpy(), gumap.dist_u16(o["dist"]), o["w"].cpu().numpy())
             gumap.gumap_serve_release(s, rid)
+
+        def drain():
+            for i in list(pending):
+                st, r = gumap.gumap_serve_poll(s, pending[i])
+                if st == gumap.PENDING:
+                    continue
+                assert st == gumap.OK, gumap.gumap_status_string(st)
+                take(i, pending.pop(i), r)
+
+        t_next = time.perf_counter()
+        for i, ((g, k, m), gap) in enumerate(zip(sub, gaps)):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                drain()
+            while True:
+                try:
+                    pending[i] = gumap.gumap_serve_submit(s, g.row_ptr, g.col, g.n, g.nnz, k, m)
+                    break
+                except gumap.GumapError as e:
+                    if e.status != gumap.ERR_AGAIN:
+                        raise
+                    drain()
+        for i in list(pending):
+            st, r = gumap.gumap_serve_wait(s, pending[i], 600.0)
+            assert st == gumap.OK, gumap.gumap_status_string(st)
+            take(i, pending.pop(i), r)
         stats = gumap.gumap_server_get_stats(s)
         gumap.gumap_server_destroy(s)
-        res = {"graphs_per_s": len(ids) / (t_last - t_first), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+        res = {"graphs_per_s": len(lat) / (t_last - t_first), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                "launches": stats["launches"], "mean_graphs_per_launch": float(np.mean(batched)),
                "arena_peak_gb": stats["arena_peak_bytes"] / 2**30,
                "by_class": {c: {"requests": len(v), "p50_ms": pct(v, 50), "p99_ms": pct(v, 99)}
@@ -1032,13 +1050,19 @@ def run_serve_workload(args, emit=True):
             dw = max(dw, float(np.max(np.abs(gw.astype(np.float64) - ref["w"]))))
         parity = {"requests_checked": len(rows), "rows_differing": bad, "max_abs_dw": dw}
 
-    # baseline: the same requests, one handle and one synchronous run each
+    # baseline: the same requests, one handle and one synchronous run each;
+    # each one's time alone gives the service time of its class
     t0 = time.perf_counter()
+    alone = {}
     for g, k, m in reqs:
+        t1 = time.perf_counter()
         with gumap.KnnGraph.from_graph(g, k, mode=m) as kg:
             kg.run()
             kg.check()
+        alone.setdefault(cls(g, m), []).append(time.perf_counter() - t1)
     single = len(reqs) / (time.perf_counter() - t0)
+    alone_ms = {c: {"p50_ms": pct(v, 50), "p99_ms": pct(v, 99), "max_ms": max(v) * 1e3}
+                for c, v in sorted(alone.items())}
     classes = {}
     for g, _, m in reqs:
         classes[cls(g, m)] = classes.get(cls(g, m), 0) + 1
@@ -1049,9 +1073,10 @@ def run_serve_workload(args, emit=True):
             "config": {"workload": "config 5: Poisson stream, n lognormal median 5000 sigma_ln 1.0 clamped "
                                    f"[64, {args.serve_n_cap}], BA/grid/G(n,p) thirds, 70% partial / 30% full, "
                                    "k in {15, 30}, 64 GiB budget", "requests": len(reqs),
+                       "max_batch_vertices": args.serve_batch_vertices or "library default",
                        "vertices": int(sum(g.n for g, _, _ in reqs)), "classes": classes},
             "saturated": sat, "latency_sweep": points, "parity": parity,
-            "one_handle_per_request_graphs_per_s": single,
+            "one_handle_per_request_graphs_per_s": single, "alone_ms_by_class": alone_ms,
             "speedup_vs_one_handle_per_request": sat["graphs_per_s"] / single}
     if emit:
         print(json.dumps(line), flush=True)
@@ -1216,7 +1241,8 @@ def run_extras(args):
                                        "speedup_vs_one_launch_per_graph", "roofline", "parity", "gpu_launches"))
     line = run_serve_workload(args, emit=False)
     out["served"] = summary_of(line, ("metric", "value", "unit", "saturated", "latency_sweep", "parity",
-                                      "one_handle_per_request_graphs_per_s", "speedup_vs_one_handle_per_request"))
+                                      "one_handle_per_request_graphs_per_s", "speedup_vs_one_handle_per_request",
+                                      "alone_ms_by_class"))
     out["served"]["requests"] = line["config"]["requests"]
     out["quality_metrics"] = quality_summary(args)
     out["spectral_layout"] = spectral_summary(args)
