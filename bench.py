@@ -994,13 +994,21 @@ def run_serve_workload(args, emit=True):
                 rows[i] = (o["idx"].cpu().numpy(), gumap.dist_u16(o["dist"]), o["w"].cpu().numpy())
             gumap.gumap_serve_release(s, rid)
 
+        cursor = [0]
+
         def drain():
-            for i in list(pending):
+            # poll a round-robin slice of the pending requests (bounded work per call)
+            keys = list(pending)
+            if not keys:
+                return
+            start = cursor[0] % len(keys)
+            for i in (keys[start:] + keys[:start])[:32]:
                 st, r = gumap.gumap_serve_poll(s, pending[i])
                 if st == gumap.PENDING:
                     continue
                 assert st == gumap.OK, gumap.gumap_status_string(st)
                 take(i, pending.pop(i), r)
+            cursor[0] = start + 32
 
         t_next = time.perf_counter()
         for i, ((g, k, m), gap) in enumerate(zip(sub, gaps)):

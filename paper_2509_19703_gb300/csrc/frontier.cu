@@ -205,7 +205,7 @@ cudaError_t launch_thread(const FrontierArgs& a, cudaStream_t s) {
     while (threads > 32 && thread_smem_bytes(a.k, threads) > 48 * 1024) threads -= 32;
     const size_t smem = thread_smem_bytes(a.k, threads);
     long long g = ((long long)a.n_src + threads - 1) / threads;
-    const long long cap = (long long)device_sm_count() * 64;
+    const long long cap = (long long)(a.sms > 0 ? a.sms : device_sm_count()) * 64;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     frontier_thread_kernel<<<(unsigned)g, threads, smem, s>>>(a);
@@ -346,7 +346,7 @@ template <int G, int LPL>
 cudaError_t launch_group_t(const FrontierArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)kWarpsPerBlock * (32 / G) * (a.k + 1) * sizeof(int32_t);
     long long g = ((long long)a.n_src + kWarpsPerBlock * (32 / G) - 1) / (kWarpsPerBlock * (32 / G));
-    const long long cap = (long long)device_sm_count() * 8;
+    const long long cap = (long long)(a.sms > 0 ? a.sms : device_sm_count()) * 8;
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     frontier_group_kernel<G, LPL><<<(unsigned)g, kThreads, smem, s>>>(a);
@@ -369,7 +369,8 @@ template <int LPL>
 cudaError_t launch_lpl(const FrontierArgs& a, cudaStream_t s) {
     const size_t smem = (size_t)kWarpsPerBlock * (a.k + 1) * sizeof(int32_t);
     long long g = ((long long)a.n_src + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (g > device_sm_count() * 64ll) g = device_sm_count() * 64ll;
+    const long long cap = (long long)(a.sms > 0 ? a.sms : device_sm_count()) * 64;
+    if (g > cap) g = cap;
     if (g < 1) g = 1;
     frontier_kernel<LPL><<<(unsigned)g, kThreads, smem, s>>>(a);
     return cudaGetLastError();

@@ -144,6 +144,7 @@ struct FrontierArgs {
     uint16_t* out_dist;
     int32_t* status;         // set to kStatusBadSource for a source outside [0, n)
     int32_t build;           // GUMAP_OPT_FRONTIER_BUILD: 0 automatic (3), 1 thread, 2 warp, 3 group of lanes per source
+    int32_t sms;             // SMs the launch may fill (its grid is sized for that many); 0 = all
 };
 
 // One unit of the batched engine: a block of sources of one graph of the

@@ -7,7 +7,8 @@
 // graphs of the same k together in one batched launch (batch.cu), a graph too
 // large for it alone (frontier.cu for the partial form, msbfs.cu for the full
 // form) -- and keeps up to n_streams launches in flight on separate streams,
-// the last of which takes small-graph batches only.
+// the last of which takes small-graph batches only. A large graph's launches
+// are sized for half the SMs, so small batches keep running beside them.
 // Each launch runs the whole path of gumap_knn_run without the COO: BFS kNN
 // lists, rho/sigma and the weights (weights.cu), the fuzzy union, then ids made local to
 // each request's graph. A host callback enqueued after the launch stamps its
@@ -373,6 +374,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
         a.out_idx = L->idx;
         a.out_dist = L->dist;
         a.status = &ctr->status;
+        a.sms = (s->num_sms + 1) / 2;  // a large graph fills half the GPU: batches of small ones keep the rest
         ck(launch_frontier(a, st));
         L->engine = GUMAP_ENGINE_FRONTIER;
     } else {
@@ -411,7 +413,8 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
             a.queue = reinterpret_cast<int32_t*>(dptr(o_queue));
             a.inq = a.queue + 4 * (size_t)N;
             ck(cudaMemsetAsync(ctr, 0, kLaunchCounterBytes, st));
-            ck(launch_msbfs(a, msbfs_grid_for(a, s->coop_grid), 256, st));
+            // half the resident grid: a large graph's hundreds of levels never hold the whole GPU
+            ck(launch_msbfs(a, msbfs_grid_for(a, std::max(1, s->coop_grid / 2)), 256, st));
         }
         L->engine = GUMAP_ENGINE_MSBFS;
     }

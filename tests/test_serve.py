@@ -1,7 +1,9 @@
 """Request server (gumap_server_*): continuous batching under a device-memory
 budget. Every result must be identical to the same graph computed alone by
 a gumap_knn handle, whether it ran batched with others, alone, or was
-admitted late because memory was short."""
+admitted late because memory was short; and every result of the mixed
+stream is checked against the CPU oracle (ids and distances exact, weights
+within 1e-5)."""
 import time
 
 import numpy as np
@@ -9,6 +11,8 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
+from gpu_helpers import W_TOL
 from paper_2509_19703_gb300 import graphgen as gg
 from paper_2509_19703_gb300 import gumap
 
@@ -53,7 +57,7 @@ def request_mix(count, seed):
     return out
 
 
-def check_all(s, reqs):
+def check_all(s, reqs, against_oracle=False):
     for rid, (g, k, mode) in reqs:
         st, res = gumap.gumap_serve_wait(s, rid, 120.0)
         assert st == gumap.OK, (g.name, gumap.gumap_status_string(st))
@@ -61,6 +65,14 @@ def check_all(s, reqs):
         want = alone(g, k, mode)
         for a, b, name in zip(got, want, ("idx", "dist", "w")):
             assert np.array_equal(a, b), (g.name, name, res["batch_graphs"], res["engine"])
+        if against_oracle:
+            # the two forms give the same rows (a pinned property of the oracle); the full
+            # form's all-pairs BFS is used up to 6000 vertices, the partial one beyond
+            form = "full" if mode == gumap.FULL and g.n <= 6000 else "partial"
+            ref = oracle.knn_pipeline(g, k, form)
+            assert np.array_equal(got[0], ref["idx"]) and np.array_equal(got[1], ref["dist"]), g.name
+            err = float(np.max(np.abs(got[2].astype(np.float64) - ref["w"])))
+            assert err <= W_TOL, (g.name, err)
         gumap.gumap_serve_release(s, rid)
 
 
@@ -71,7 +83,7 @@ def test_results_identical_alone_and_in_the_mix():
     s = gumap.gumap_server_create(0, 4 << 30)
     try:
         reqs = [(gumap.gumap_serve_submit(s, g.row_ptr, g.col, g.n, g.nnz, k, m), (g, k, m)) for g, k, m in mix]
-        check_all(s, reqs)
+        check_all(s, reqs, against_oracle=True)
         st = gumap.gumap_server_get_stats(s)
         assert st["completed"] == len(mix) and st["failed"] == 0
     finally:
