@@ -1247,7 +1247,9 @@ def run_extras(args):
     line = run_batch_workload(ba, emit=False)
     out["batched"] = summary_of(line, ("metric", "value", "unit", "ms_per_step", "one_launch_per_graph",
                                        "speedup_vs_one_launch_per_graph", "roofline", "parity", "gpu_launches"))
-    line = run_serve_workload(args, emit=False)
+    sa = copy.copy(args)
+    sa.serve_rates = [0.25, 0.5, 0.9]
+    line = run_serve_workload(sa, emit=False)
     out["served"] = summary_of(line, ("metric", "value", "unit", "saturated", "latency_sweep", "parity",
                                       "one_handle_per_request_graphs_per_s", "speedup_vs_one_handle_per_request",
                                       "alone_ms_by_class"))

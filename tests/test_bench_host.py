@@ -60,8 +60,8 @@ def test_frontier_and_coo_byte_models():
     entries = np.array([4, 12, 0], dtype=np.int64)
     rows = np.array([1, 3, 1], dtype=np.int64)
     assert bench.frontier_alg_bytes(entries, rows, 15) == 8 * 5 + 4 * 16 + 6 * 15 * 3
-    # row scan 16 n, scatter 12 n k + 8 nnz, row sorts 16 nnz
-    assert bench.coo_alg_bytes(1000, 15, 24000) == 16 * 1000 + 12 * 15000 + 24 * 24000
+    # each slot's id and weight read once, each entry's column and weight written once, row offsets
+    assert bench.coo_alg_bytes(1000, 15, 24000) == 8 * 15000 + 8 * 24000 + 8 * 1000
 
 
 def test_all_core_oracle_sample_covers_each_source_once():
