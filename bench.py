@@ -685,7 +685,7 @@ def run_batch_workload(args, emit=True):
                 "kernel_share_of_step": bfs_ms / ms_batch if ms_batch else None,
                 "model": "per unit and level 12 n W (frontier, visited, next rows; shared memory here) + the "
                          "graph's CSR 4 (n + 1) + 4 nnz"}
-    parity = None
+    parity, cpu = None, None
     if not args.no_cpu_baseline:  # a seeded sample of the graphs against the oracle (all rows of each)
         import numpy as np
 
@@ -694,15 +694,19 @@ def run_batch_workload(args, emit=True):
         dist = gumap.dist_u16(out["dist"])
         w = out["w"].cpu().numpy().astype(np.float64)
         pick = np.random.default_rng(44).choice(len(graphs), size=min(len(graphs), 40), replace=False)
-        bad, dw = 0, 0.0
+        bad, dw, busy = 0, 0.0, 0.0
         for gi in pick:
             g, m = graphs[gi], items[gi].mode
+            t0 = time.perf_counter()
             ref = oracle.knn_pipeline(g, K_NEIGHBOURS, m)
+            busy += time.perf_counter() - t0
             lo, hi = int(offs[gi]), int(offs[gi + 1])
             li = np.where(idx[lo:hi] >= 0, idx[lo:hi] - lo, -1)
             bad += int(np.sum(np.any(li != ref["idx"], axis=1) | np.any(dist[lo:hi] != ref["dist"], axis=1)))
             dw = max(dw, float(np.max(np.abs(w[lo:hi] - ref["w"]))))
         parity = {"graphs_checked": len(pick), "rows_differing": bad, "max_abs_dw": dw}
+        cpu = {"value": len(pick) / busy, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+               "sample": f"{len(pick)} seeded graphs of the mix, every source (1 thread)"}
 
     singles = [gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=m) for g, m in zip(graphs, modes)]
     souts = [s.alloc_outputs(g.n) for s, g in zip(singles, graphs)]
@@ -729,7 +733,7 @@ def run_batch_workload(args, emit=True):
                        "l2": "flushed (512 MB write) before each timed step"},
             "one_launch_per_graph": {"graphs_per_s": len(graphs) / (ms_single * 1e-3), "ms_per_step": ms_single},
             "speedup_vs_one_launch_per_graph": ms_single / ms_batch,
-            "roofline": roofline, "parity": parity,
+            "roofline": roofline, "parity": parity, "cpu_baseline": cpu,
             "gpu_launches": st["kernel_launches"]}
     if emit:
         print(json.dumps(line), flush=True)
@@ -1129,7 +1133,11 @@ def config1_summary(args):
            "autotuned": {key: tuned[key] for key in ("engine", "batch_width", "best_ms")}}
     if not args.no_cpu_baseline:
         import oracle
+        t0 = time.perf_counter()
         ref = oracle.knn_pipeline(g, K_NEIGHBOURS, "full")
+        busy = time.perf_counter() - t0
+        res["cpu_baseline"] = {"ms_per_run": busy * 1e3, "gteps": 1024 * 1984 / busy / 1e9, "cores": 1,
+                               "kind": "oracle", "sample": "the whole graph, every source (1 thread)"}
         idx, dist = out["idx"].cpu().numpy(), gumap.dist_u16(out["dist"])
         res["parity"] = {"rows_checked": g.n,
                          "rows_differing": int(np.sum(np.any(idx != ref["idx"], axis=1) |
@@ -1246,7 +1254,8 @@ def run_extras(args):
     ba.steps, ba.warmup, ba.batch_graphs = 3, 1, 2000
     line = run_batch_workload(ba, emit=False)
     out["batched"] = summary_of(line, ("metric", "value", "unit", "ms_per_step", "one_launch_per_graph",
-                                       "speedup_vs_one_launch_per_graph", "roofline", "parity", "gpu_launches"))
+                                       "speedup_vs_one_launch_per_graph", "roofline", "parity", "cpu_baseline",
+                                       "gpu_launches"))
     sa = copy.copy(args)
     sa.serve_rates = [0.25, 0.5, 0.9]
     line = run_serve_workload(sa, emit=False)
