@@ -41,6 +41,9 @@ struct DeviceCounters {
     int32_t qvalid[4];               // 1 if that queue was built
     unsigned long long f_edges[4];   // sum of deg(v) over nonzero (v, group) items of level d
     unsigned long long u_edges[4];   // sum of deg(v) over (v, group) items left unvisited after a pull
+    // full form: (v, group) items all of whose active sources have reached v
+    // after the pull of level d; when it is every item, level d + 1 is empty
+    unsigned long long sat_items[4];
     // ---- kept across launches
     int32_t status;
     int32_t levels;            // deepest level reached by the last MS-BFS launch

@@ -268,6 +268,8 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
 // atomics touch the bitsets. Each source's level-1 kNN entries (the first k of its row)
 // and padding are written by one warp, the act/need masks one 32-source word
 // per warp. The per-launch counters were zeroed by the host.
+constexpr int kInitRound = 8;  // row entries per lane loaded together by the level-1 pull
+
 __device__ void phase_init_identity(const MsbfsArgs& a) {
     __shared__ __align__(16) uint32_t s_chunk[8][128];  // per warp: 128 words = 4096 source bits
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -288,8 +290,8 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
     clear_sat(a, gtid, nthr);
     for (long long v = gwarp; v < a.n; v += nwarps) {
         const int r0 = __ldg(a.row_ptr + v), r1 = __ldg(a.row_ptr + v + 1);
-        int lo = r0, hi = r1;  // first neighbour >= src_lo
-        while (lo < hi) {
+        int lo = r0, hi = r1;  // first neighbour >= src_lo (every one when the block starts at vertex 0)
+        while (a.src_lo > 0 && lo < hi) {
             const int mid = (lo + hi) >> 1;
             if (__ldg(a.col + mid) < a.src_lo) lo = mid + 1;
             else hi = mid;
@@ -301,14 +303,24 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
             __syncwarp();
             const long long base = (long long)a.src_lo + 4096ll * c;
             const long long top = base + 4096 < src_hi ? base + 4096 : src_hi;
-            while (true) {  // the neighbours in [base, top) are the next entries of the sorted row
-                const int idx = e + lane;
-                const long long u = idx < r1 ? (long long)__ldg(a.col + idx) : src_hi;
-                const bool in = u < top;
-                if (in) atomicOr(&sc[(u - base) >> 5], 1u << ((u - base) & 31));
-                const unsigned m = __ballot_sync(kFull, in);
-                e += __popc(m);
-                if (m != kFull) break;
+            // the neighbours in [base, top) are the next entries of the sorted row;
+            // kInitRound of them per lane are loaded at once
+            while (true) {
+                long long u[kInitRound];
+#pragma unroll
+                for (int j = 0; j < kInitRound; ++j) {
+                    const int idx = e + 32 * j + lane;
+                    u[j] = idx < r1 ? (long long)__ldg(a.col + idx) : src_hi;
+                }
+                int taken = 0;
+#pragma unroll
+                for (int j = 0; j < kInitRound; ++j) {
+                    const bool in = u[j] < top;
+                    if (in) atomicOr(&sc[(u[j] - base) >> 5], 1u << ((u[j] - base) & 31));
+                    taken += __popc(__ballot_sync(kFull, in));
+                }
+                e += taken;  // the row is sorted: the entries below top are a prefix
+                if (taken < 32 * kInitRound) break;
             }
             __syncwarp();
             const int g = c * 32 + lane;
@@ -485,16 +497,20 @@ __device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* _
                                                 const typename PullVec<GW>::T* __restrict__ actV, int G, int g, int v,
                                                 const int32_t* __restrict__ col, int e0, int e1, bool fold,
                                                 uint8_t* __restrict__ sat, unsigned long long& fe,
-                                                unsigned long long& ue, int& any) {
+                                                unsigned long long& ue, int& any, unsigned& nsat) {
     using VT = typename PullVec<GW>::T;
     const VT zero = vzero(VT{});
     const size_t off = (size_t)v * G + g;
     if (sat) {  // a saturated item: zero the N buffer once more, then skip it for good
         const uint8_t st = sat[off];
-        if (st == 2) return;
+        if (st == 2) {
+            ++nsat;
+            return;
+        }
         if (st == 1) {
             NV[off] = zero;
             sat[off] = 2;
+            ++nsat;
             return;
         }
     }
@@ -525,6 +541,7 @@ __device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* _
     if (vnz(vandnot(s1, s0))) SV[off] = s1;
     any |= vnz(acc) ? 1 : 0;
     if (sat && !vnz(todo)) sat[off] = 1;
+    if (!vnz(vandnot(todo, acc))) ++nsat;  // every active source has now reached v
 }
 
 // Pull step of level d (see file comment), with items of GW words. At level
@@ -550,6 +567,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     const VT* actV = reinterpret_cast<const VT*>(a.act);
     const VT zero = vzero(VT{});
     int any = 0;
+    unsigned nsat = 0;
 
     // heavy vertices: one warp per (v, g), lanes split the neighbour list
     const long long heavy_items = (long long)a.n_heavy * G;
@@ -560,11 +578,15 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const size_t off = (size_t)v * G + g;
         if (a.sat) {  // the whole warp reads the same state: uniform branches
             const uint8_t st = a.sat[off];
-            if (st == 2) continue;
+            if (st == 2) {
+                if (lane == 0) ++nsat;
+                continue;
+            }
             if (st == 1) {
                 if (lane == 0) {
                     NV[off] = zero;
                     a.sat[off] = 2;
+                    ++nsat;
                 }
                 continue;
             }
@@ -597,30 +619,45 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
             if (vnz(vandnot(s1, s0))) SV[off] = s1;
             any |= vnz(acc) ? 1 : 0;
             if (a.sat && !vnz(todo)) a.sat[off] = 1;
+            if (!vnz(vandnot(todo, acc))) ++nsat;
         }
     }
 
-    // light vertices: one thread per (v, g), eight neighbour loads in flight
+    // light vertices: one thread per (v, g), eight neighbour loads in flight.
+    // An item index t = position * G + g advances by the stride as a
+    // (position, group) pair: no division per item.
     if (!STAGED) {  // rows from the global CSR, items over the whole grid
-        const long long total = (long long)a.n_light * G;
-        for (long long t = gtid; t < total; t += nthr) {
-            const int li = (int)(t / G);
-            const int g = (int)(t - (long long)li * G);
+        const int step_li = (int)(nthr / G), step_g = (int)(nthr - (long long)step_li * G);
+        int li = (int)(gtid / G), g = (int)(gtid - (long long)li * G);
+        while (li < a.n_light) {
             const int v = __ldg(a.light + li);
             pull_light_item<GW, NB, false>(FV, NV, SV, actV, G, g, v, a.col, __ldg(a.row_ptr + v),
-                                           __ldg(a.row_ptr + v + 1), fold, a.sat, fe, ue, any);
+                                           __ldg(a.row_ptr + v + 1), fold, a.sat, fe, ue, any, nsat);
+            li += step_li;
+            g += step_g;
+            if (g >= G) {
+                g -= G;
+                ++li;
+            }
         }
     } else {  // this CTA's slice of positions, rows from shared memory (mode 1) or global (mode 2)
-        const long long total = (long long)sv.P * G;
-        for (long long t = threadIdx.x; t < total; t += blockDim.x) {
-            const int pi = (int)(t / G);
-            const int g = (int)(t - (long long)pi * G);
+        const int B = (int)blockDim.x;
+        const int step_pi = B / G, step_g = B - step_pi * G;
+        int pi = (int)threadIdx.x / G, g = (int)threadIdx.x - pi * G;
+        while (pi < sv.P) {
             const int2 m0 = sv.meta[pi], m1 = sv.meta[pi + 1];
             pull_light_item<GW, NB, true>(FV, NV, SV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase, fold,
-                                          a.sat, fe, ue, any);
+                                          a.sat, fe, ue, any, nsat);
+            pi += step_pi;
+            g += step_g;
+            if (g >= G) {
+                g -= G;
+                ++pi;
+            }
         }
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
+    if (!a.partial) block_add(nsat, &a.ctr->sat_items[d % 4]);
     if (a.direction == 0) {  // the statistics only feed the automatic choice
         block_add(fe, &a.ctr->f_edges[d % 4]);
         block_add(ue, &a.ctr->u_edges[d % 4]);
@@ -763,16 +800,16 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
         uint32_t needw = need0;
         int32_t* oi = a.out_idx + (size_t)j * a.k;
         uint16_t* od = a.out_dist + (size_t)j * a.k;
-        // four 32-vertex tiles per round, their loads issued together
-        for (int v00 = 0; v00 < a.n && (needw != 0u || ap); v00 += 128) {
-            uint32_t xs[4];
+        // eight 32-vertex tiles per round, their loads issued together
+        for (int v00 = 0; v00 < a.n && (needw != 0u || ap); v00 += 256) {
+            uint32_t xs[8];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 8; ++q) {
                 const int v = v00 + 32 * q + lane;
                 xs[q] = (v < a.n) ? __ldcg(Nc + (size_t)v * a.W + w) : 0u;
             }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
+            for (int q = 0; q < 8; ++q) {
                 // a lane whose source needs no entries has c == k and appends none
                 const uint32_t x = ap ? xs[q] : (xs[q] & needw);
                 if (__ballot_sync(kFull, x != 0u) == 0u) continue;
@@ -911,6 +948,7 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
             a.ctr->qcnt[(d + 1) % 4] = 0;
             a.ctr->f_edges[(d + 1) % 4] = 0ull;
             a.ctr->u_edges[(d + 1) % 4] = 0ull;
+            a.ctr->sat_items[(d + 1) % 4] = 0ull;
         }
         // Direction of level d, decided identically by every thread from
         // values settled before the last barrier: push when the edges out of
@@ -925,6 +963,7 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
             const unsigned long long ue = *reinterpret_cast<volatile unsigned long long*>(&a.ctr->u_edges[last_pull % 4]);
             push = fe * (unsigned long long)a.push_div < ue;
         }
+        bool all_sat = false;
         if (push) {
             phase_push_prep(a, Fc, Nc, d);
             if (pend) phase_extract(a, Fc, pend);
@@ -939,6 +978,8 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             lap(kPull);
             last_pull = d;
+            all_sat = !a.partial && *reinterpret_cast<volatile unsigned long long*>(&a.ctr->sat_items[d % 4]) ==
+                                        (unsigned long long)a.n * (unsigned long long)(a.W / GW);
         }
         pend = 0;
         if (ld_volatile_u32(&a.ctr->lvl_any[d % 3]) == 0u) break;
@@ -948,8 +989,11 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
         uint32_t* t = Fc;
         Fc = Nc;
         Nc = t;
+        // every active source has reached every vertex: level d + 1 would find
+        // nothing, so only the extraction of level d remains (after the loop)
+        if (all_sat) break;
     }
-    if (pend) {  // the loop ran out of levels with an extraction pending (it breaks before, in practice)
+    if (pend) {  // every item saturated (or the loop ran out of levels) with an extraction pending
         phase_extract(a, Fc, pend);
         if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
         lap(kExtract);
