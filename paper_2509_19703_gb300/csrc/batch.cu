@@ -200,10 +200,13 @@ __global__ void __launch_bounds__(kThreads, 1) batch_kernel(BatchArgs a) {
                         for (int tl = c * per; tl < (c + 1) * per && tl < tiles; ++tl) {
                             const int v = tl * 32 + lane;
                             const uint32_t x = (v < n ? Nc[v * W + w] : 0u) & needw;
-                            if (__ballot_sync(kFull, x != 0u) == 0u) continue;
+                            // one ballot per source with a vertex in the tile
+                            uint32_t cols = __reduce_or_sync(kFull, x);
+                            if (cols == 0u) continue;
                             uint32_t m = 0u;
-#pragma unroll
-                            for (int b = 0; b < 32; ++b) {
+                            while (cols) {
+                                const int b = __ffs(cols) - 1;
+                                cols &= cols - 1u;
                                 const uint32_t tb = __ballot_sync(kFull, (x >> b) & 1u);
                                 if (lane == b) m = tb;
                             }

@@ -44,6 +44,7 @@ struct DeviceCounters {
     // full form: (v, group) items all of whose active sources have reached v
     // after the pull of level d; when it is every item, level d + 1 is empty
     unsigned long long sat_items[4];
+    uint32_t sat_seen;         // 1 once some pull item has had every active source reach it
     // ---- kept across launches
     int32_t status;
     int32_t levels;            // deepest level reached by the last MS-BFS launch

@@ -496,12 +496,12 @@ __device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* _
                                                 typename PullVec<GW>::T* __restrict__ SV,
                                                 const typename PullVec<GW>::T* __restrict__ actV, int G, int g, int v,
                                                 const int32_t* __restrict__ col, int e0, int e1, bool fold,
-                                                uint8_t* __restrict__ sat, unsigned long long& fe,
-                                                unsigned long long& ue, int& any, unsigned& nsat) {
+                                                uint8_t* __restrict__ sat, bool use_sat, unsigned long long& fe,
+                                                unsigned long long& ue, int& any, unsigned& nsat, int& newsat) {
     using VT = typename PullVec<GW>::T;
     const VT zero = vzero(VT{});
     const size_t off = (size_t)v * G + g;
-    if (sat) {  // a saturated item: zero the N buffer once more, then skip it for good
+    if (use_sat) {  // a saturated item: zero the N buffer once more, then skip it for good
         const uint8_t st = sat[off];
         if (st == 2) {
             ++nsat;
@@ -540,7 +540,10 @@ __device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* _
     const VT s1 = vor(seen, acc);
     if (vnz(vandnot(s1, s0))) SV[off] = s1;
     any |= vnz(acc) ? 1 : 0;
-    if (sat && !vnz(todo)) sat[off] = 1;
+    if (sat && !vnz(todo)) {
+        sat[off] = 1;
+        newsat = 1;
+    }
     if (!vnz(vandnot(todo, acc))) ++nsat;  // every active source has now reached v
 }
 
@@ -568,6 +571,10 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     const VT zero = vzero(VT{});
     int any = 0;
     unsigned nsat = 0;
+    // A light item's saturation state is read only once some item has
+    // saturated: before that every state byte is 0 and the loads are wasted.
+    const bool use_sat = a.sat && ld_volatile_u32(&a.ctr->sat_seen) != 0u;
+    int newsat = 0;
 
     // heavy vertices: one warp per (v, g), lanes split the neighbour list
     const long long heavy_items = (long long)a.n_heavy * G;
@@ -618,7 +625,10 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
             const VT s1 = vor(seen, acc);
             if (vnz(vandnot(s1, s0))) SV[off] = s1;
             any |= vnz(acc) ? 1 : 0;
-            if (a.sat && !vnz(todo)) a.sat[off] = 1;
+            if (a.sat && !vnz(todo)) {
+                a.sat[off] = 1;
+                newsat = 1;
+            }
             if (!vnz(vandnot(todo, acc))) ++nsat;
         }
     }
@@ -632,7 +642,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         while (li < a.n_light) {
             const int v = __ldg(a.light + li);
             pull_light_item<GW, NB, false>(FV, NV, SV, actV, G, g, v, a.col, __ldg(a.row_ptr + v),
-                                           __ldg(a.row_ptr + v + 1), fold, a.sat, fe, ue, any, nsat);
+                                           __ldg(a.row_ptr + v + 1), fold, a.sat, use_sat, fe, ue, any, nsat, newsat);
             li += step_li;
             g += step_g;
             if (g >= G) {
@@ -647,7 +657,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         while (pi < sv.P) {
             const int2 m0 = sv.meta[pi], m1 = sv.meta[pi + 1];
             pull_light_item<GW, NB, true>(FV, NV, SV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase, fold,
-                                          a.sat, fe, ue, any, nsat);
+                                          a.sat, use_sat, fe, ue, any, nsat, newsat);
             pi += step_pi;
             g += step_g;
             if (g >= G) {
@@ -658,6 +668,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     }
     if (__syncthreads_or(any) && threadIdx.x == 0) atomicOr(&a.ctr->lvl_any[slot], 1u);
     if (!a.partial) block_add(nsat, &a.ctr->sat_items[d % 4]);
+    if (__syncthreads_or(newsat) && threadIdx.x == 0 && !use_sat) atomicOr(&a.ctr->sat_seen, 1u);
     if (a.direction == 0) {  // the statistics only feed the automatic choice
         block_add(fe, &a.ctr->f_edges[d % 4]);
         block_add(ue, &a.ctr->u_edges[d % 4]);
@@ -812,10 +823,14 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
             for (int q = 0; q < 8; ++q) {
                 // a lane whose source needs no entries has c == k and appends none
                 const uint32_t x = ap ? xs[q] : (xs[q] & needw);
-                if (__ballot_sync(kFull, x != 0u) == 0u) continue;
+                // transpose the 32x32 tile with one ballot per source that has
+                // a vertex in it (the OR over the lanes lists those sources)
+                uint32_t cols = __reduce_or_sync(kFull, x);
+                if (cols == 0u) continue;
                 uint32_t mine = 0u;
-#pragma unroll
-                for (int b = 0; b < 32; ++b) {
+                while (cols) {
+                    const int b = __ffs(cols) - 1;
+                    cols &= cols - 1u;
                     const uint32_t t = __ballot_sync(kFull, (x >> b) & 1u);
                     if (lane == b) mine = t;
                 }

@@ -177,14 +177,18 @@ def test_block_tiling_ragged(bits):
     assert_parity(run_gpu(g, 15, "partial", engine=MSBFS, block_bits=bits), ref, f"partial bits={bits}")
 
 
+@pytest.mark.parametrize("bits", [512, 4480])
+@pytest.mark.parametrize("mode", ["full", "partial"])
 @pytest.mark.parametrize("heavy", [0, 3, 1 << 30])
-def test_heavy_threshold(heavy):
-    """Warp-per-item (heavy) and thread-per-item (light) pulls agree."""
+def test_heavy_threshold(heavy, mode, bits):
+    """Warp-per-item (heavy) and thread-per-item (light) pulls agree, in both
+    forms, with 4 and with 35 groups of 128 source bits per row."""
     g = gg.disjoint_union([gg.barabasi_albert(1500, 3, 64), gg.star(200), gg.gnp(300, 0.05, 65)], "hv")
     ref = oracle_ref(g, 15, "full")
-    with gumap.KnnGraph.from_graph(g, 15) as kg:
+    with gumap.KnnGraph.from_graph(g, 15, mode=gumap.FULL if mode == "full" else gumap.PARTIAL) as kg:
+        kg.set_option(gumap.OPT_ENGINE, MSBFS)
         kg.set_option(gumap.OPT_HEAVY_DEGREE, heavy)
-        kg.set_option(gumap.OPT_BLOCK_BITS, 512)
+        kg.set_option(gumap.OPT_BLOCK_BITS, bits)
         out = kg.run()
         kg.check()
         assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
