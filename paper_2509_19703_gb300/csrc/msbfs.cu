@@ -14,7 +14,9 @@
 // vertex already reached by every active source costs no neighbour loads.
 // Such a saturated item stays saturated (S only grows, act only shrinks):
 // after writing its N word 0 in both buffers it is skipped for good (one
-// state byte per item).
+// state byte per item, read only once some item has saturated). In the full
+// form each pull also counts the items that are saturated after it; when
+// that is every item, the next level could reach nothing and is not run.
 //
 // Work of a level is the set of (vertex v, 128-bit group g) items. Items of
 // vertices of ordinary degree are one thread each (the neighbour loop is
