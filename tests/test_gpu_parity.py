@@ -181,15 +181,23 @@ def test_block_tiling_ragged(bits):
 @pytest.mark.parametrize("mode", ["full", "partial"])
 @pytest.mark.parametrize("heavy", [0, 3, 1 << 30])
 def test_heavy_threshold(heavy, mode, bits):
-    """Warp-per-item (heavy) and thread-per-item (light) pulls agree, in both
-    forms, with 4 and with 35 groups of 128 source bits per row."""
+    """Heavy vertices as warp-wide items give the light pull's rows, with the
+    rows read from the CSR (a grid size's first launch) and staged (later
+    launches), in both forms, with 4 and with 35 groups of 128 source bits
+    per row."""
     g = gg.disjoint_union([gg.barabasi_albert(1500, 3, 64), gg.star(200), gg.gnp(300, 0.05, 65)], "hv")
     ref = oracle_ref(g, 15, "full")
     with gumap.KnnGraph.from_graph(g, 15, mode=gumap.FULL if mode == "full" else gumap.PARTIAL) as kg:
         kg.set_option(gumap.OPT_ENGINE, MSBFS)
         kg.set_option(gumap.OPT_HEAVY_DEGREE, heavy)
         kg.set_option(gumap.OPT_BLOCK_BITS, bits)
+        first = kg.run()
+        kg.check()
+        assert np.array_equal(first["idx"].cpu().numpy(), ref["idx"])
+        kg.reset_stats()
         out = kg.run()
+        if heavy == 3:
+            assert kg.stats()["bfs_staged_launches"] > 0
         kg.check()
         assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
         assert float(np.max(np.abs(out["w"].cpu().numpy() - ref["w"]))) <= 1e-5
