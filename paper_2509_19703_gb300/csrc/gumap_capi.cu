@@ -563,6 +563,8 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
         a.queue = reinterpret_cast<int32_t*>(base + 3 * words);
         a.inq = a.queue + 4 * (size_t)h->n;
         a.sat = reinterpret_cast<uint8_t*>(h->bits.p) + sat_off;
+        // pull-only levels over consecutive sources pull from the seen sets
+        a.seen_only = (identity && h->opt_direction == 1) ? 1 : 0;
         const int grid = msbfs_grid_for(a, h->coop_grid[a.pull_width == 2][a.ctas_per_sm == 4]);
         const int cap = h->stage_cap[a.ctas_per_sm == 4];
         // The layout costs host work, uploads and a stream synchronisation, so a

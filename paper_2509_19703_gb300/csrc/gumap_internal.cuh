@@ -124,6 +124,12 @@ struct MsbfsArgs {
     int32_t staged;          // 2: staged build reading the slice from global memory (the path
                              // taken when a copy does not complete; for tests)
     int32_t stage_bytes;     // dynamic shared memory of the launch (0 when not staged)
+    // 1: pull from the seen sets (consecutive sources, pull-only levels):
+    // S_d lives in buffer d % 3 of {F, N, S}; a level reads S_{d-1} (own row
+    // and the neighbours' rows) and writes S_d = S_{d-1} | (OR of the
+    // neighbours' S_{d-1} & act & ~S_{d-1}); level d's new pairs are
+    // S_d & ~S_{d-1}. 0: the frontier scheme of the file comment of msbfs.cu.
+    int32_t seen_only;
 };
 
 // Shared-memory bytes one CTA's staged slice takes (the kernel rounds the

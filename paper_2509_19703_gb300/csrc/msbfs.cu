@@ -50,6 +50,8 @@
 // grid barrier whose waits are bounded in time (kWaitLimitNs).
 #include "gumap_internal.cuh"
 
+#include <algorithm>
+
 namespace gumap {
 
 namespace {
@@ -272,6 +274,7 @@ __device__ __forceinline__ void block_add(unsigned long long x, unsigned long lo
 // per warp. The per-launch counters were zeroed by the host.
 constexpr int kInitRound = 8;  // row entries per lane loaded together by the level-1 pull
 
+template <bool SO>
 __device__ void phase_init_identity(const MsbfsArgs& a) {
     __shared__ __align__(16) uint32_t s_chunk[8][128];  // per warp: 128 words = 4096 source bits
     const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -329,7 +332,7 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
             if (g < G4) {
                 const uint4 nbits = reinterpret_cast<const uint4*>(sc)[lane];
                 const size_t off = (size_t)v * G4 + g;
-                N4[off] = nbits;
+                if (!SO) N4[off] = nbits;
                 uint4 sbits = z;
                 if (j >= 0 && j < a.nb && (j >> 7) == g) {
                     const uint32_t bit = 1u << (j & 31);
@@ -339,8 +342,12 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
                     sbits.z = wi == 2 ? bit : 0u;
                     sbits.w = wi == 3 ? bit : 0u;
                 }
-                S4[off] = or4(sbits, nbits);  // S holds levels 0 and 1: level 2 needs no fold
-                if (clear_f) F4[off] = z;
+                if (SO) {
+                    N4[off] = or4(sbits, nbits);  // S_1 in buffer 1 % 3 (N)
+                } else {
+                    S4[off] = or4(sbits, nbits);  // S holds levels 0 and 1: level 2 needs no fold
+                    if (clear_f) F4[off] = z;
+                }
                 if (nz4(nbits)) {
                     any = 1;
                     fe += (unsigned long long)(r1 - r0);
@@ -549,13 +556,67 @@ __device__ __forceinline__ void pull_light_item(const typename PullVec<GW>::T* _
     if (!vnz(vandnot(todo, acc))) ++nsat;  // every active source has now reached v
 }
 
+// A light item of the seen-set pull (MsbfsArgs::seen_only): PV holds
+// S_{d-1}, CV receives S_d. The state byte counts the buffers that already
+// hold a saturated item's final row: 2 after the level that found it
+// saturated (S_{d-1} and S_d), 3 one level later, and from then on the item
+// is skipped.
+template <int GW, int NB, bool SLICE>
+__device__ __forceinline__ void pull_seen_item(const typename PullVec<GW>::T* __restrict__ PV,
+                                               typename PullVec<GW>::T* __restrict__ CV,
+                                               const typename PullVec<GW>::T* __restrict__ actV, int G, int g, int v,
+                                               const int32_t* __restrict__ col, int e0, int e1,
+                                               uint8_t* __restrict__ sat, bool use_sat, unsigned long long& fe,
+                                               unsigned long long& ue, int& any, unsigned& nsat, int& newsat) {
+    using VT = typename PullVec<GW>::T;
+    const VT zero = vzero(VT{});
+    const size_t off = (size_t)v * G + g;
+    const unsigned st = use_sat ? sat[off] : 0u;
+    if (st == 3) {
+        ++nsat;
+        return;
+    }
+    const VT own = vld(PV + off);
+    const VT todo = vandnot(vld(actV + g), own);
+    if (!vnz(todo)) {  // saturated: carry the row into level d's buffer
+        CV[off] = own;
+        if (sat) {
+            sat[off] = st == 2 ? 3 : 2;
+            newsat = 1;
+        }
+        ++nsat;
+        return;
+    }
+    VT acc = zero;
+    const VT* fg = PV + g;
+    for (int e = e0; e < e1; e += NB) {
+        int u[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) u[q] = (e + q < e1) ? (SLICE ? col[e + q] : __ldg(col + e + q)) : -1;
+        VT f[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) f[q] = u[q] >= 0 ? vld(fg + (size_t)u[q] * G) : zero;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) acc = vor(acc, f[q]);
+        if (vcovers(acc, todo)) break;
+    }
+    acc = vand(acc, todo);
+    const unsigned long long dv = (unsigned long long)(e1 - e0);
+    if (vnz(acc)) fe += dv;
+    if (vnz(vandnot(todo, acc))) ue += dv;
+    else ++nsat;  // every active source has now reached v
+    CV[off] = vor(own, acc);
+    any |= vnz(acc) ? 1 : 0;
+}
+
 // Pull step of level d (see file comment), with items of GW words. At level
 // 2 the frontier F (level 1) is not yet in S: it is ORed in here. Also
 // measures, for the choice of the next level's direction, the edges of the
 // new frontier (sum of deg(v) over nonzero (v, group) items: what a push
 // would touch) and of the items still unvisited (what the next pull would
 // touch at most).
-template <int GW, int NB, bool STAGED>
+// SO (seen-set pull): Fc holds S_{d-1}, Nc receives S_d, a.S is not used.
+template <int GW, int NB, bool STAGED, bool SO>
 __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, uint32_t* __restrict__ Nc,
                            int slot, int d, const StageView& sv) {
     using VT = typename PullVec<GW>::T;
@@ -585,6 +646,47 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         const int g = (int)(it - (long long)h * G);
         const int v = __ldg(a.heavy + h);
         const size_t off = (size_t)v * G + g;
+        if constexpr (SO) {  // seen-set pull: FV holds S_{d-1}, NV receives S_d
+            const unsigned st = use_sat ? a.sat[off] : 0u;  // uniform over the warp
+            if (st == 3) {
+                if (lane == 0) ++nsat;
+                continue;
+            }
+            const VT own = vld(FV + off);
+            const VT todo = vandnot(vld(actV + g), own);
+            if (!vnz(todo)) {
+                if (lane == 0) {
+                    NV[off] = own;
+                    if (a.sat) {
+                        a.sat[off] = st == 2 ? 3 : 2;
+                        newsat = 1;
+                    }
+                    ++nsat;
+                }
+                continue;
+            }
+            VT acc = zero;
+            const int e0 = __ldg(a.row_ptr + v), e1 = __ldg(a.row_ptr + v + 1);
+            for (int base = e0; base < e1; base += 64) {
+                const int ea = base + lane, eb = base + 32 + lane;
+                const int ua = ea < e1 ? __ldg(a.col + ea) : -1;
+                const int ub = eb < e1 ? __ldg(a.col + eb) : -1;
+                if (ua >= 0) acc = vor(acc, vld(FV + (size_t)ua * G + g));
+                if (ub >= 0) acc = vor(acc, vld(FV + (size_t)ub * G + g));
+                acc = vwarp_or(acc);
+                if (vcovers(acc, todo)) break;
+            }
+            acc = vand(acc, todo);
+            if (lane == 0) {
+                const unsigned long long dv = (unsigned long long)(e1 - e0);
+                if (vnz(acc)) fe += dv;
+                if (vnz(vandnot(todo, acc))) ue += dv;
+                else ++nsat;
+                NV[off] = vor(own, acc);
+                any |= vnz(acc) ? 1 : 0;
+            }
+            continue;
+        }
         if (a.sat) {  // the whole warp reads the same state: uniform branches
             const uint8_t st = a.sat[off];
             if (st == 2) {
@@ -643,8 +745,13 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         int li = (int)(gtid / G), g = (int)(gtid - (long long)li * G);
         while (li < a.n_light) {
             const int v = __ldg(a.light + li);
-            pull_light_item<GW, NB, false>(FV, NV, SV, actV, G, g, v, a.col, __ldg(a.row_ptr + v),
-                                           __ldg(a.row_ptr + v + 1), fold, a.sat, use_sat, fe, ue, any, nsat, newsat);
+            if constexpr (SO)
+                pull_seen_item<GW, NB, false>(FV, NV, actV, G, g, v, a.col, __ldg(a.row_ptr + v),
+                                              __ldg(a.row_ptr + v + 1), a.sat, use_sat, fe, ue, any, nsat, newsat);
+            else
+                pull_light_item<GW, NB, false>(FV, NV, SV, actV, G, g, v, a.col, __ldg(a.row_ptr + v),
+                                               __ldg(a.row_ptr + v + 1), fold, a.sat, use_sat, fe, ue, any, nsat,
+                                               newsat);
             li += step_li;
             g += step_g;
             if (g >= G) {
@@ -658,8 +765,12 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         int pi = (int)threadIdx.x / G, g = (int)threadIdx.x - pi * G;
         while (pi < sv.P) {
             const int2 m0 = sv.meta[pi], m1 = sv.meta[pi + 1];
-            pull_light_item<GW, NB, true>(FV, NV, SV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase, fold,
-                                          a.sat, use_sat, fe, ue, any, nsat, newsat);
+            if constexpr (SO)
+                pull_seen_item<GW, NB, true>(FV, NV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase,
+                                             a.sat, use_sat, fe, ue, any, nsat, newsat);
+            else
+                pull_light_item<GW, NB, true>(FV, NV, SV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase,
+                                              fold, a.sat, use_sat, fe, ue, any, nsat, newsat);
             pi += step_pi;
             g += step_g;
             if (g >= G) {
@@ -797,7 +908,9 @@ __device__ void phase_push(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
 // sources (every column when the all-pairs rows are requested: each newly
 // reached (source, vertex) pair gets its distance d there). Lane b owns
 // source 32*w + b.
-__device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
+// Prev (seen-set pull): level d's new pairs are Nc & ~Prev (S_d & ~S_{d-1});
+// NULL: Nc holds them.
+__device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, const uint32_t* Prev, int d) {
     const int lane = threadIdx.x & 31;
     const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -820,6 +933,7 @@ __device__ void phase_extract(const MsbfsArgs& a, const uint32_t* Nc, int d) {
             for (int q = 0; q < 8; ++q) {
                 const int v = v00 + 32 * q + lane;
                 xs[q] = (v < a.n) ? __ldcg(Nc + (size_t)v * a.W + w) : 0u;
+                if (Prev && v < a.n) xs[q] &= ~__ldcg(Prev + (size_t)v * a.W + w);
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -894,7 +1008,7 @@ __device__ void stage_issue(const MsbfsArgs& a, unsigned long long* bar, int* st
 
 // All levels of one launch. copies_done: the staged slice's copies (if any
 // were issued) have landed, so the CTA may exit.
-template <int GW, int NB, bool STAGED>
+template <int GW, int NB, bool STAGED, bool SO>
 __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long long* bar, const int* st,
                                              unsigned char* dyn, bool& copies_done) {
     // phase times of block 0's thread 0, kept in shared memory (not in
@@ -914,7 +1028,7 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
         }
     };
     if (a.identity) {
-        phase_init_identity(a);
+        phase_init_identity<SO>(a);
         if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
     } else {
         phase_init(a);
@@ -945,6 +1059,11 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
 
     uint32_t* Fc = a.N;  // level-1 frontier was pushed into N
     uint32_t* Nc = a.F;
+    // seen-set pull: S_d in buffer d % 3 of {F, N, S}
+    auto buf = [&](int i) -> uint32_t* {
+        const int r = i % 3;
+        return r == 0 ? a.F : (r == 1 ? a.N : a.S);
+    };
     int last = 1;
     bool go = ld_volatile_u32(&a.ctr->lvl_any[1]) != 0u;
     if (a.partial && ld_volatile_i32(&a.ctr->n_need) == 0) go = false;
@@ -973,7 +1092,8 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
         // (Beamer's rule in bit-parallel form). The estimate of unexplored
         // edges comes from a pull at most two levels back; older, pull again.
         bool push = false;
-        if (a.direction == 2) {
+        if (SO) {  // the seen-set pull runs pull-only levels
+        } else if (a.direction == 2) {
             push = true;
         } else if (a.direction == 0 && d - last_pull <= 2) {
             const unsigned long long fe = *reinterpret_cast<volatile unsigned long long*>(&a.ctr->f_edges[(d - 1) % 4]);
@@ -983,15 +1103,20 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
         bool all_sat = false;
         if (push) {
             phase_push_prep(a, Fc, Nc, d);
-            if (pend) phase_extract(a, Fc, pend);
+            if (pend) phase_extract(a, Fc, nullptr, pend);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             phase_push(a, Fc, Nc, d);
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             lap(kPush);
             if (timer) ++s_time[kPushes];
         } else {
-            phase_pull<GW, NB, STAGED>(a, Fc, Nc, d % 3, d, sv);
-            if (pend) phase_extract(a, Fc, pend);
+            if (SO) {
+                phase_pull<GW, NB, STAGED, true>(a, buf(d - 1), buf(d), d % 3, d, sv);
+                if (pend) phase_extract(a, buf(pend), buf(pend - 1), pend);
+            } else {
+                phase_pull<GW, NB, STAGED, false>(a, Fc, Nc, d % 3, d, sv);
+                if (pend) phase_extract(a, Fc, nullptr, pend);
+            }
             if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
             lap(kPull);
             last_pull = d;
@@ -1011,7 +1136,7 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
         if (all_sat) break;
     }
     if (pend) {  // every item saturated (or the loop ran out of levels) with an extraction pending
-        phase_extract(a, Fc, pend);
+        phase_extract(a, SO ? buf(pend) : Fc, SO ? buf(pend - 1) : nullptr, pend);
         if (!grid_barrier(&a.ctr->bar, &a.ctr->status)) return;
         lap(kExtract);
     }
@@ -1031,7 +1156,7 @@ __device__ __forceinline__ void msbfs_levels(const MsbfsArgs& a, unsigned long l
 // thread; 4: 64 registers, more warps to hide latency). STAGED: the light
 // rows come from the CTA's slice staged in shared memory (a separate build,
 // so the other one carries none of its code or registers).
-template <int GW, int OCC, bool STAGED>
+template <int GW, int OCC, bool STAGED, bool SO>
 __global__ void __launch_bounds__(256, OCC) msbfs_kernel(MsbfsArgs a) {
     __shared__ __align__(8) unsigned long long s_bar;
     __shared__ int s_stage[5];
@@ -1040,7 +1165,7 @@ __global__ void __launch_bounds__(256, OCC) msbfs_kernel(MsbfsArgs a) {
     bool copies_done = !STAGED;
     // eight neighbour loads in flight per light item (fewer measured slower even where the
     // 64-register build spills)
-    msbfs_levels<GW, 8, STAGED>(a, &s_bar, s_stage, s_dyn, copies_done);
+    msbfs_levels<GW, 8, STAGED, SO>(a, &s_bar, s_stage, s_dyn, copies_done);
     // a CTA that left early must not exit while a bulk copy still writes its shared memory
     if (STAGED && !copies_done && s_stage[3]) mbar_wait_bounded(&s_bar, 0, kWaitLimitNs);
 }
@@ -1076,34 +1201,46 @@ __global__ void identity_kernel(int32_t* dst, int32_t n) {
 
 namespace {
 
-template <bool STAGED>
+template <bool STAGED, bool SO>
 const void* msbfs_kernel_for_t(int pull_width, int ctas_per_sm) {
     if (pull_width == 2)
-        return ctas_per_sm == 4 ? (const void*)msbfs_kernel<2, 4, STAGED> : (const void*)msbfs_kernel<2, 3, STAGED>;
-    return ctas_per_sm == 4 ? (const void*)msbfs_kernel<4, 4, STAGED> : (const void*)msbfs_kernel<4, 3, STAGED>;
+        return ctas_per_sm == 4 ? (const void*)msbfs_kernel<2, 4, STAGED, SO>
+                                : (const void*)msbfs_kernel<2, 3, STAGED, SO>;
+    return ctas_per_sm == 4 ? (const void*)msbfs_kernel<4, 4, STAGED, SO> : (const void*)msbfs_kernel<4, 3, STAGED, SO>;
 }
 
-const void* msbfs_kernel_for(int pull_width, int ctas_per_sm, bool staged) {
-    return staged ? msbfs_kernel_for_t<true>(pull_width, ctas_per_sm) : msbfs_kernel_for_t<false>(pull_width, ctas_per_sm);
+const void* msbfs_kernel_for(int pull_width, int ctas_per_sm, bool staged, bool seen_only) {
+    if (seen_only)
+        return staged ? msbfs_kernel_for_t<true, true>(pull_width, ctas_per_sm)
+                      : msbfs_kernel_for_t<false, true>(pull_width, ctas_per_sm);
+    return staged ? msbfs_kernel_for_t<true, false>(pull_width, ctas_per_sm)
+                  : msbfs_kernel_for_t<false, false>(pull_width, ctas_per_sm);
 }
 
 }  // namespace
 
+// Resident CTAs per SM of a build: the smaller over its two schemes, so one
+// cooperative grid size serves both.
 int msbfs_max_blocks_per_sm(int block_threads, int pull_width, int ctas_per_sm, size_t dyn_smem, bool staged) {
-    int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, msbfs_kernel_for(pull_width, ctas_per_sm, staged),
-                                                      block_threads, dyn_smem) != cudaSuccess)
-        return 0;
-    return nb;
+    int best = 1 << 30;
+    for (bool so : {false, true}) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, msbfs_kernel_for(pull_width, ctas_per_sm, staged, so),
+                                                          block_threads, dyn_smem) != cudaSuccess)
+            return 0;
+        best = std::min(best, nb);
+    }
+    return best;
 }
 
 cudaError_t msbfs_allow_smem(int bytes) {
     for (int w : {2, 4})
-        for (int c : {3, 4}) {
-            cudaError_t e = cudaFuncSetAttribute(msbfs_kernel_for(w, c, true),
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-            if (e != cudaSuccess) return e;
-        }
+        for (int c : {3, 4})
+            for (bool so : {false, true}) {
+                cudaError_t e = cudaFuncSetAttribute(msbfs_kernel_for(w, c, true, so),
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+                if (e != cudaSuccess) return e;
+            }
     return cudaSuccess;
 }
 
@@ -1132,8 +1269,8 @@ int msbfs_grid_for(const MsbfsArgs& a, int max_grid) {
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s) {
     MsbfsArgs copy = a;
     void* params[] = {&copy};
-    return cudaLaunchCooperativeKernel(msbfs_kernel_for(a.pull_width, a.ctas_per_sm, a.staged != 0), dim3(grid),
-                                       dim3(block), params, a.staged ? (size_t)a.stage_bytes : 0, s);
+    return cudaLaunchCooperativeKernel(msbfs_kernel_for(a.pull_width, a.ctas_per_sm, a.staged != 0, a.seen_only != 0),
+                                       dim3(grid), dim3(block), params, a.staged ? (size_t)a.stage_bytes : 0, s);
 }
 
 cudaError_t launch_barrier_selftest(GridBarrier* bar, int32_t* status, unsigned long long limit_ns, int grid,
