@@ -18,6 +18,16 @@
 // form each pull also counts the items that are saturated after it; when
 // that is every item, the next level could reach nothing and is not run.
 //
+// Pull-only levels over a block of consecutive sources (every run over all
+// vertices) use the seen sets alone: a source first reaches v at level d
+// exactly when it had reached some neighbour of v by level d - 1 and not v,
+// so S_d[v] = S_{d-1}[v] | ((OR_{u in adj(v)} S_{d-1}[u]) & act & ~S_{d-1}[v]).
+// S_{d-1}, S_d and S_{d+1} rotate over the three buffers, a level reads one
+// row stream and writes one (no frontier stream), and level d's new pairs,
+// which the extraction needs, are S_d & ~S_{d-1}. A saturated item's state
+// byte then counts the buffers already holding its final row (2, then 3),
+// after which the item is skipped.
+//
 // Work of a level is the set of (vertex v, 128-bit group g) items. Items of
 // vertices of ordinary degree are one thread each (the neighbour loop is
 // short). Items of vertices whose degree is far above the mean (hubs of
