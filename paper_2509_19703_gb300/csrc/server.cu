@@ -409,6 +409,7 @@ bool start_launch(gumap_server* s, std::vector<Request*>& group, int stream) {
             a.partial = 0;
             a.ctr = ctr;
             a.direction = 1;  // pull only (see GUMAP_OPT_DIRECTION)
+            a.seen_only = 1;  // so the levels pull from the seen sets (MsbfsArgs::seen_only)
             a.push_div = 8;
             a.queue = reinterpret_cast<int32_t*>(dptr(o_queue));
             a.inq = a.queue + 4 * (size_t)N;
