@@ -961,7 +961,15 @@ def run_serve_workload(args, emit=True):
     from paper_2509_19703_gb300 import gumap
 
     torch.cuda.set_device(0)
+    t_stage = [time.perf_counter()]
+
+    def stage(name):
+        t = time.perf_counter()
+        print(f"[bench] serve {name}: {t - t_stage[0]:.1f} s", file=sys.stderr, flush=True)
+        t_stage[0] = t
+
     reqs = serve_requests(args.serve_requests, 5, args.serve_n_cap)
+    stage("requests generated")
     budget = 64 << 30
     small_n = 27000
 
@@ -975,7 +983,16 @@ def run_serve_workload(args, emit=True):
         """Submit `sub` with Poisson gaps at `rate` (0: all at once), taking
         every finished result back (and releasing it) while submitting, as a
         client does; latency is submit to completion on the server clock."""
+        tc = [time.perf_counter()]
+        marks = []
+
+        def mark(name):
+            t = time.perf_counter()
+            marks.append(f"{name} {t - tc[0]:.1f}")
+            tc[0] = t
+
         s = gumap.gumap_server_create(0, budget, max_batch_vertices=args.serve_batch_vertices)
+        mark("create")
         rng = np.random.default_rng(55)
         gaps = rng.exponential(1.0 / rate, size=len(sub)) if rate else np.zeros(len(sub))
         lat, t_first, t_last, batched = [], None, 0.0, []
@@ -1029,12 +1046,16 @@ def run_serve_workload(args, emit=True):
                     if e.status != gumap.ERR_AGAIN:
                         raise
                     drain()
+        mark("submit")
         for i in list(pending):
             st, r = gumap.gumap_serve_wait(s, pending[i], 600.0)
             assert st == gumap.OK, gumap.gumap_status_string(st)
             take(i, pending.pop(i), r)
+        mark("wait")
         stats = gumap.gumap_server_get_stats(s)
         gumap.gumap_server_destroy(s)
+        mark("destroy")
+        print(f"[bench] serve stream rate {rate:.1f}/s: " + ", ".join(marks) + " s", file=sys.stderr, flush=True)
         res = {"graphs_per_s": len(lat) / (t_last - t_first), "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
                "launches": stats["launches"], "mean_graphs_per_launch": float(np.mean(batched)),
                "arena_peak_gb": stats["arena_peak_bytes"] / 2**30,
@@ -1043,16 +1064,19 @@ def run_serve_workload(args, emit=True):
         return res, rows
 
     run_stream(0, reqs[:500])  # warm-up (module loading, allocator)
+    stage("warm-up stream")
     check = set()
     if not args.no_cpu_baseline:  # a seeded sample of graphs small enough for the oracle's full BFS
         cand = [i for i, (g, _, _) in enumerate(reqs) if g.n <= 3000]
         check = set(int(i) for i in np.random.default_rng(56).choice(cand, size=min(len(cand), 40), replace=False))
     sat, rows = run_stream(0, reqs, check)
+    stage("saturated stream")
     points = []
     for frac in args.serve_rates:
         p, _ = run_stream(frac * sat["graphs_per_s"], reqs)
         p["offered_rate_frac"] = frac
         points.append(p)
+        stage(f"stream at {frac} of saturation")
     parity = None
     if check:
         import oracle
@@ -1063,6 +1087,7 @@ def run_serve_workload(args, emit=True):
             bad += int(np.sum(np.any(gi != ref["idx"], axis=1) | np.any(gd != ref["dist"], axis=1)))
             dw = max(dw, float(np.max(np.abs(gw.astype(np.float64) - ref["w"]))))
         parity = {"requests_checked": len(rows), "rows_differing": bad, "max_abs_dw": dw}
+    stage("oracle parity")
 
     # baseline: the same requests, one handle and one synchronous run each;
     # each one's time alone gives the service time of its class
@@ -1075,6 +1100,7 @@ def run_serve_workload(args, emit=True):
             kg.check()
         alone.setdefault(cls(g, m), []).append(time.perf_counter() - t1)
     single = len(reqs) / (time.perf_counter() - t0)
+    stage("one handle per request")
     alone_ms = {c: {"p50_ms": pct(v, 50), "p99_ms": pct(v, 99), "max_ms": max(v) * 1e3}
                 for c, v in sorted(alone.items())}
     classes = {}
@@ -1273,6 +1299,9 @@ def run_extras(args):
                                        "gpu_launches"))
     lap("batched")
     sa = copy.copy(args)
+    # a shorter stream keeps the default run within minutes (the 10,000-request
+    # stream with its six rates is `--workload serve`)
+    sa.serve_requests = min(args.serve_requests, 3000)
     sa.serve_rates = [0.25, 0.5, 0.9]
     line = run_serve_workload(sa, emit=False)
     out["served"] = summary_of(line, ("metric", "value", "unit", "saturated", "latency_sweep", "parity",
