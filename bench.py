@@ -64,6 +64,10 @@ def parse_args():
                    default=None,
                    help="run one graph of the workload (config2: ba20k, er5k; partial: ba1m-k15 ... grid1m-k50) "
                         "for profiler captures; not a bench line")
+    p.add_argument("--engine", choices=["tuned", "msbfs"], default="tuned",
+                   help="headline workload: the autotuner's engine (default), or the MS-BFS kernel with the "
+                        "autotuner's other settings (for profiler captures, under which the tuner's timings "
+                        "are distorted)")
     p.add_argument("--frontier-build", choices=["tuned", "thread", "warp", "group"], default="tuned",
                    help="partial workload: the frontier engine's merge, autotuned (default) or forced "
                         "(for profiler captures)")
@@ -493,6 +497,9 @@ def run_ours(args):
     work_per_step = int(sum(int(w.sum()) for w in works))
     kgs = [gumap.KnnGraph.from_graph(g, K_NEIGHBOURS, mode=gumap.FULL) for g in graphs]
     tuned = [kg.autotune() for kg in kgs]  # engine settings timed on each graph, before any timed step
+    if args.engine == "msbfs":
+        for kg in kgs:
+            kg.set_option(gumap.OPT_ENGINE, gumap.ENGINE_MSBFS)
     for kg in kgs:
         kg.set_option(gumap.OPT_PROFILE, 1)
     outs = [kg.alloc_outputs(g.n) for kg, g in zip(kgs, graphs)]
