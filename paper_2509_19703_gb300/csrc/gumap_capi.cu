@@ -182,6 +182,7 @@ struct gumap_knn {
     // their rows: CTA b owns positions b, b + grid, b + 2 grid, ... (every
     // CTA gets the same mix of degrees), stored contiguously per CTA
     std::vector<int32_t> light_order;
+    std::vector<int32_t> heavy_order;  // the hubs, whose rows the layout also holds as segments
     struct SliceCut {
         int grid;
         int32_t* d_cut;    // [grid + 1] first pair of each CTA
@@ -189,6 +190,7 @@ struct gumap_knn {
         int32_t* d_ocol;   // the rows in that order, + 4 of padding
         size_t meta_bytes, ocol_bytes;
         int bytes;         // shared memory of the largest CTA share, rounded up to 1 KB
+        int hub_segments;  // 1: the hubs' rows are in the layout as segments
     };
     std::vector<SliceCut> cuts;
     int first_grid = -1;  // a grid size launched once without its layout (built on its second launch)
@@ -456,6 +458,7 @@ int build_order(gumap_knn* h) {
     CK(cudaMemcpy(h->d_order, order.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice), "order upload");
 
     h->light_order.assign(order.begin() + nh, order.end());
+    h->heavy_order.assign(order.begin(), order.begin() + nh);
     free_cuts(h);
     return GUMAP_OK;
 }
@@ -470,7 +473,20 @@ int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut**
             *out = &c;
             return GUMAP_OK;
         }
-    const int64_t nl = (int64_t)h->light_order.size();
+    // positions: the hubs' segments (heaviest hubs first), then the light
+    // vertices, each as (vertex or ~(hub * kHubSegMax + segment), row length)
+    std::vector<int2> pos;
+    const bool segs = !h->heavy_order.empty() && h->heavy_order.size() < (size_t)(INT32_MAX / kHubSegMax);
+    pos.reserve(h->light_order.size() + (segs ? h->heavy_order.size() : 0));
+    if (segs)
+        for (size_t hh = 0; hh < h->heavy_order.size(); ++hh) {
+            const int d = h->deg[(size_t)h->heavy_order[hh]];
+            const int len = hub_seg_len(d), nseg = hub_seg_count(d);
+            for (int sg = 0; sg < nseg; ++sg)
+                pos.push_back(make_int2(~(int)(hh * kHubSegMax + sg), std::min(len, d - sg * len)));
+        }
+    for (int32_t v : h->light_order) pos.push_back(make_int2(v, h->deg[(size_t)v]));
+    const int64_t nl = (int64_t)pos.size();
     std::vector<int2> meta((size_t)nl + 3);
     std::vector<int32_t> cut((size_t)grid + 1);
     int64_t off = 0, i = 0;
@@ -479,9 +495,8 @@ int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut**
         cut[(size_t)b] = (int32_t)i;
         const int64_t i0 = i, off0 = off;
         for (int64_t p = b; p < nl; p += grid) {
-            const int32_t v = h->light_order[(size_t)p];
-            meta[(size_t)i++] = make_int2(v, (int)off);
-            off += h->deg[(size_t)v];
+            meta[(size_t)i++] = make_int2(pos[(size_t)p].x, (int)off);
+            off += pos[(size_t)p].y;
         }
         worst = std::max(worst, stage_slice_bytes(i0, i, off0, off));
     }
@@ -489,7 +504,7 @@ int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut**
     for (int64_t j = nl; j < nl + 3; ++j) meta[(size_t)j] = make_int2(0, (int)off);
     gumap_knn::SliceCut c{grid, nullptr, nullptr, nullptr, sizeof(int2) * meta.size(),
                           sizeof(int32_t) * ((size_t)off + 4),
-                          (int)std::min<long long>(((worst + 1023) / 1024) * 1024, 1 << 30)};
+                          (int)std::min<long long>(((worst + 1023) / 1024) * 1024, 1 << 30), segs ? 1 : 0};
     cudaError_t e;
     if ((e = pool_alloc((void**)&c.d_cut, (size_t)(grid + 1) * 4)) != cudaSuccess ||
         (e = pool_alloc((void**)&c.d_meta, c.meta_bytes)) != cudaSuccess ||
@@ -503,7 +518,7 @@ int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut**
     CK(cudaMemcpyAsync(c.d_cut, cut.data(), (size_t)(grid + 1) * 4, cudaMemcpyHostToDevice, st), "cut upload");
     CK(cudaMemcpyAsync(c.d_meta, meta.data(), c.meta_bytes, cudaMemcpyHostToDevice, st), "pairs upload");
     CK(cudaMemsetAsync(c.d_ocol + off, 0, 4 * sizeof(int32_t), st), "row padding");
-    CK(launch_gather_rows(h->d_rp, h->d_col, c.d_meta, (int32_t)nl, c.d_ocol, st), "gather rows");
+    CK(launch_gather_rows(h->d_rp, h->d_col, h->d_order, c.d_meta, (int32_t)nl, c.d_ocol, st), "gather rows");
     // the host vectors go out of scope: make sure the copies have read them
     CK(cudaStreamSynchronize(st), "layout upload");
     *out = &h->cuts.back();
@@ -583,6 +598,7 @@ int run_msbfs(gumap_knn* h, const int32_t* src, bool identity, int32_t n_src, in
                 a.meta = c->d_meta;
                 a.ocol = c->d_ocol;
                 a.slice = c->d_cut;
+                a.hub_segments = c->hub_segments;
                 h->staged_launches++;
             }
         }

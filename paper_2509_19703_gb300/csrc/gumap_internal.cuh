@@ -118,9 +118,17 @@ struct MsbfsArgs {
     // per launch and reads every level's neighbour ids from there; the host
     // has checked that each slice fits stage_bytes. staged = 0: rows are
     // read from the global CSR.
+    // Hub segments: a position whose vertex field is negative, ~(h *
+    // kHubSegMax + s), is segment s of heavy vertex heavy[h] (its row entries
+    // [s L, min((s + 1) L, deg)), L = hub_seg_len(deg)). hub_segments = 1 when
+    // the layout holds them: the seen-set pull then runs the hubs from the
+    // slices (each segment ORs its row into S_d with atomics, exact because
+    // seen sets only grow) and the frontier scheme skips these positions and
+    // runs its warp-wide heavy items.
     const int2* meta;
     const int32_t* ocol;
     const int32_t* slice;
+    int32_t hub_segments;
     int32_t staged;          // 2: staged build reading the slice from global memory (the path
                              // taken when a copy does not complete; for tests)
     int32_t stage_bytes;     // dynamic shared memory of the launch (0 when not staged)
@@ -136,6 +144,18 @@ struct MsbfsArgs {
 // same way): the (vertex, offset) pairs of positions [p0, p1] from an even
 // index, and the neighbour ids [c0, c1) from a multiple of 4, so both
 // copies start and end on 16-byte boundaries.
+// Hub segments of the staged layout (see MsbfsArgs::meta): at most
+// kHubSegMax per hub, each of at least 16 row entries.
+constexpr int kHubSegMax = 4096;
+__host__ __device__ inline int hub_seg_len(int deg) {
+    const int l = (deg + kHubSegMax - 1) / kHubSegMax;
+    return l < 16 ? 16 : l;
+}
+__host__ __device__ inline int hub_seg_count(int deg) {
+    const int l = hub_seg_len(deg);
+    return (deg + l - 1) / l;
+}
+
 inline long long stage_slice_bytes(long long p0, long long p1, long long c0, long long c1) {
     const long long m = (((p1 + 2) & ~1ll) - (p0 & ~1ll)) * 8;
     const long long c = (((c1 + 3) & ~3ll) - (c0 & ~3ll)) * 4;
@@ -219,7 +239,8 @@ int msbfs_max_blocks_per_sm(int block_threads, int pull_width = 4, int ctas_per_
                             bool staged = false);
 // Allows the kernel builds up to `bytes` of dynamic shared memory.
 cudaError_t msbfs_allow_smem(int bytes);
-cudaError_t launch_gather_rows(const int32_t* row_ptr, const int32_t* col, const int2* meta, int32_t n_pos,
+cudaError_t launch_gather_rows(const int32_t* row_ptr, const int32_t* col, const int32_t* heavy, const int2* meta,
+                               int32_t n_pos,
                                int32_t* ocol, cudaStream_t s);
 cudaError_t launch_msbfs(const MsbfsArgs& a, int grid, int block, cudaStream_t s);
 int msbfs_grid_for(const MsbfsArgs& a, int max_grid);

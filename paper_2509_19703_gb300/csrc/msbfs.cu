@@ -367,6 +367,17 @@ __device__ void phase_init_identity(const MsbfsArgs& a) {
         }
         if (a.inq && lane == 0) a.inq[v] = 0;
     }
+    // seen-set pull with hub segments: the hubs' rows of the buffers of S_2
+    // and S_3, which segments OR into, start empty
+    if (SO && a.hub_segments) {
+        const long long items = (long long)a.n_heavy * G4;
+        for (long long t = gtid; t < items; t += nthr) {
+            const long long h = t / G4;
+            const size_t off = (size_t)__ldg(a.heavy + h) * G4 + (size_t)(t - h * G4);
+            F4[off] = z;
+            S4[off] = z;
+        }
+    }
     // level-1 kNN entries of each source and the padding after them
     for (long long jj = gwarp; jj < a.nb; jj += nwarps) {
         const int s = a.src_lo + (int)jj;
@@ -619,6 +630,68 @@ __device__ __forceinline__ void pull_seen_item(const typename PullVec<GW>::T* __
     any |= vnz(acc) ? 1 : 0;
 }
 
+__device__ __forceinline__ void vatomic_or(uint32_t* p, uint4 v) {
+    if (v.x) atomicOr(p + 0, v.x);
+    if (v.y) atomicOr(p + 1, v.y);
+    if (v.z) atomicOr(p + 2, v.z);
+    if (v.w) atomicOr(p + 3, v.w);
+}
+__device__ __forceinline__ void vatomic_or(uint32_t* p, uint2 v) {
+    if (v.x) atomicOr(p + 0, v.x);
+    if (v.y) atomicOr(p + 1, v.y);
+}
+
+// One segment (row entries col[e0, e1), staged) of a hub's item (v, g) in
+// the seen-set pull. The segments of an item run in any order on any CTAs:
+// each ORs what it finds into S_d[v][g] with atomics, segment 0 also ORs
+// S_{d-1}[v][g]. The buffer of S_d held S_{d-3} (or zero, at levels 2 and
+// 3), a subset of S_{d-1}, so the result is exactly S_{d-1} | found, with no
+// initialisation and no finishing step. A saturated item is handled by every
+// segment the same way (plain stores of the same value); segment 0 counts it.
+template <int GW, int NB>
+__device__ __forceinline__ void pull_seen_segment(const typename PullVec<GW>::T* __restrict__ PV,
+                                                  typename PullVec<GW>::T* __restrict__ CV,
+                                                  const typename PullVec<GW>::T* __restrict__ actV, int G, int g,
+                                                  int v, bool first, const int32_t* __restrict__ col, int e0, int e1,
+                                                  uint8_t* __restrict__ sat, bool use_sat, int& any, unsigned& nsat,
+                                                  int& newsat) {
+    using VT = typename PullVec<GW>::T;
+    const VT zero = vzero(VT{});
+    const size_t off = (size_t)v * G + g;
+    const unsigned st = use_sat ? sat[off] : 0u;
+    if (st == 3) {
+        if (first) ++nsat;
+        return;
+    }
+    const VT own = vld(PV + off);
+    const VT todo = vandnot(vld(actV + g), own);
+    if (!vnz(todo)) {
+        CV[off] = own;
+        if (sat) {
+            sat[off] = st == 2 ? 3 : 2;
+            newsat = 1;
+        }
+        if (first) ++nsat;
+        return;
+    }
+    VT acc = zero;
+    const VT* fg = PV + g;
+    for (int e = e0; e < e1; e += NB) {
+        int u[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) u[q] = (e + q < e1) ? col[e + q] : -1;
+        VT f[NB];
+#pragma unroll
+        for (int q = 0; q < NB; ++q) f[q] = u[q] >= 0 ? vld(fg + (size_t)u[q] * G) : zero;
+#pragma unroll
+        for (int q = 0; q < NB; ++q) acc = vor(acc, f[q]);
+        if (vcovers(acc, todo)) break;
+    }
+    acc = vand(acc, todo);
+    any |= vnz(acc) ? 1 : 0;
+    vatomic_or(reinterpret_cast<uint32_t*>(CV + off), first ? vor(own, acc) : acc);
+}
+
 // Pull step of level d (see file comment), with items of GW words. At level
 // 2 the frontier F (level 1) is not yet in S: it is ORed in here. Also
 // measures, for the choice of the next level's direction, the edges of the
@@ -650,7 +723,7 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
     int newsat = 0;
 
     // heavy vertices: one warp per (v, g), lanes split the neighbour list
-    const long long heavy_items = (long long)a.n_heavy * G;
+    const long long heavy_items = (SO && STAGED && a.hub_segments) ? 0 : (long long)a.n_heavy * G;
     for (long long it = gtid >> 5; it < heavy_items; it += nthr >> 5) {
         const int h = (int)(it / G);
         const int g = (int)(it - (long long)h * G);
@@ -775,12 +848,20 @@ __device__ void phase_pull(const MsbfsArgs& a, const uint32_t* __restrict__ Fc, 
         int pi = (int)threadIdx.x / G, g = (int)threadIdx.x - pi * G;
         while (pi < sv.P) {
             const int2 m0 = sv.meta[pi], m1 = sv.meta[pi + 1];
-            if constexpr (SO)
+            if (m0.x < 0) {  // a hub segment: the seen-set pull runs it, the frontier scheme's heavy items cover it
+                if constexpr (SO) {
+                    const int hs = ~m0.x;
+                    pull_seen_segment<GW, NB>(FV, NV, actV, G, g, __ldg(a.heavy + hs / kHubSegMax),
+                                              hs % kHubSegMax == 0, sv.col, m0.y - sv.cbase, m1.y - sv.cbase, a.sat,
+                                              use_sat, any, nsat, newsat);
+                }
+            } else if constexpr (SO) {
                 pull_seen_item<GW, NB, true>(FV, NV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase,
                                              a.sat, use_sat, fe, ue, any, nsat, newsat);
-            else
+            } else {
                 pull_light_item<GW, NB, true>(FV, NV, SV, actV, G, g, m0.x, sv.col, m0.y - sv.cbase, m1.y - sv.cbase,
                                               fold, a.sat, use_sat, fe, ue, any, nsat, newsat);
+            }
             pi += step_pi;
             g += step_g;
             if (g >= G) {
@@ -1191,12 +1272,24 @@ __global__ void barrier_selftest_kernel(GridBarrier* bar, int32_t* status, unsig
 
 // ocol[meta[p].y ...] = the CSR row of vertex meta[p].x, one warp per position.
 __global__ void gather_rows_kernel(const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
-                                   const int2* __restrict__ meta, int32_t n_pos, int32_t* __restrict__ ocol) {
+                                   const int32_t* __restrict__ heavy, const int2* __restrict__ meta, int32_t n_pos,
+                                   int32_t* __restrict__ ocol) {
     const int lane = threadIdx.x & 31;
     for (long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < n_pos;
          p += ((long long)gridDim.x * blockDim.x) >> 5) {
         const int2 m = meta[p];
-        const int e0 = row_ptr[m.x], e1 = row_ptr[m.x + 1];
+        int e0, e1;
+        if (m.x >= 0) {
+            e0 = row_ptr[m.x];
+            e1 = row_ptr[m.x + 1];
+        } else {  // segment s of heavy vertex heavy[h]
+            const int h = ~m.x / kHubSegMax, sg = ~m.x % kHubSegMax;
+            const int v = heavy[h];
+            const int r0 = row_ptr[v], r1 = row_ptr[v + 1];
+            const int len = hub_seg_len(r1 - r0);
+            e0 = r0 + sg * len;
+            e1 = min(r1, e0 + len);
+        }
         for (int e = e0 + lane; e < e1; e += 32) ocol[m.y + (e - e0)] = col[e];
     }
 }
@@ -1254,12 +1347,12 @@ cudaError_t msbfs_allow_smem(int bytes) {
     return cudaSuccess;
 }
 
-cudaError_t launch_gather_rows(const int32_t* row_ptr, const int32_t* col, const int2* meta, int32_t n_pos,
-                               int32_t* ocol, cudaStream_t s) {
+cudaError_t launch_gather_rows(const int32_t* row_ptr, const int32_t* col, const int32_t* heavy, const int2* meta,
+                               int32_t n_pos, int32_t* ocol, cudaStream_t s) {
     if (n_pos <= 0) return cudaSuccess;
     long long g = ((long long)n_pos * 32 + 255) / 256;
     if (g > device_sm_count() * 16ll) g = device_sm_count() * 16ll;
-    gather_rows_kernel<<<(unsigned)g, 256, 0, s>>>(row_ptr, col, meta, n_pos, ocol);
+    gather_rows_kernel<<<(unsigned)g, 256, 0, s>>>(row_ptr, col, heavy, meta, n_pos, ocol);
     return cudaGetLastError();
 }
 
