@@ -237,6 +237,22 @@ def test_config2_full_all_sources(maker):
     print(f"{g.name} full k=15: max |dw| = {err:.3g}, blocks = {res['stats']['n_blocks']}")
 
 
+def test_hub_beyond_the_segment_limit():
+    """The staged seen-set pull cuts a hub's row into at most 4096 segments,
+    so a hub of more than 16 x 4096 neighbours gets segments longer than 16
+    entries (this star's centre: 70,000 neighbours, segments of 18). Full
+    form on the MS-BFS engine over several source blocks (the staged layout
+    is used from the second block on); the centre's row and 40 sampled rows
+    against the oracle's full BFS."""
+    g = gg.star(70001)
+    res = run_gpu(g, 15, "full", engine=MSBFS, coo=False)
+    assert res["stats"]["bfs_staged_launches"] > 0
+    rows = np.concatenate([[0], np.random.default_rng(5).choice(np.arange(1, g.n), size=40, replace=False)])
+    rows = np.sort(rows).astype(np.int32)
+    fi, fd = oracle.knn_full(g, 15, sources=rows)
+    assert np.array_equal(res["idx"][rows], fi) and np.array_equal(res["dist"][rows], fd)
+
+
 def test_config2_partial_msbfs_matches():
     g = gg.config_ba20k()
     _full_size_check(g, 15, "partial", MSBFS)
