@@ -36,14 +36,20 @@
 // walking a hub's adjacency. Both lists run in decreasing degree. In the
 // staged build each CTA owns an interleaved slice of the ordinary vertices,
 // whose neighbour ids it bulk-copies (cp.async.bulk, completion on an
-// mbarrier) into shared memory once per launch.
+// mbarrier) into shared memory once per launch. The slices also hold each
+// hub's row cut into segments of at least 16 entries; the seen-set pull runs
+// those segments like ordinary rows, every segment ORing what it finds into
+// the hub's S_d row with atomics (exact, as the buffer held S_{d-3}, a
+// subset of S_{d-1}), and then needs no warp-wide hub items.
 //
 // Level 1 of a block of consecutive sources (every run over all vertices)
-// is a pull from the sorted rows that writes N and S in full; for an
+// is a pull from the sorted rows that writes N and S in full (S_1 alone in
+// the seen-set pull); for an
 // explicit source list it is a push from the sources' rows into N only, and
 // level 2 folds the level-1 frontier into S. Its kNN entries are the first
 // k entries of each source's sorted CSR row. For later levels the
-// extraction scans each word column of N in vertex order, transposes 32x32
+// extraction scans each word column of N (of S_d & ~S_{d-1} in the seen-set
+// pull) in vertex order, transposes 32x32
 // bit tiles with warp ballots, and appends to every incomplete source the
 // vertices it reached at this level in ascending id until its list holds k
 // entries: this is exactly the (distance, id) order, because levels are
