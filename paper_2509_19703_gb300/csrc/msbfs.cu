@@ -652,8 +652,12 @@ __device__ __forceinline__ void vatomic_or(uint32_t* p, uint2 v) {
 // each ORs what it finds into S_d[v][g] with atomics, segment 0 also ORs
 // S_{d-1}[v][g]. The buffer of S_d held S_{d-3} (or zero, at levels 2 and
 // 3), a subset of S_{d-1}, so the result is exactly S_{d-1} | found, with no
-// initialisation and no finishing step. A saturated item is handled by every
-// segment the same way (plain stores of the same value); segment 0 counts it.
+// initialisation and no finishing step. A saturated item's row is stored by
+// every segment that sees it (the same value); its state byte is advanced by
+// segment 0 alone, so a segment that reads the byte after segment 0 advanced
+// it in the same level only stores the row again or skips, never advancing
+// it twice (which would mark a buffer final that was not written).
+// Segment 0 also counts the item.
 template <int GW, int NB>
 __device__ __forceinline__ void pull_seen_segment(const typename PullVec<GW>::T* __restrict__ PV,
                                                   typename PullVec<GW>::T* __restrict__ CV,
@@ -673,7 +677,7 @@ __device__ __forceinline__ void pull_seen_segment(const typename PullVec<GW>::T*
     const VT todo = vandnot(vld(actV + g), own);
     if (!vnz(todo)) {
         CV[off] = own;
-        if (sat) {
+        if (sat && first) {
             sat[off] = st == 2 ? 3 : 2;
             newsat = 1;
         }
