@@ -219,6 +219,19 @@ def recorded_traffic():
     return rec.get("dram_bytes_per_launch")
 
 
+def recorded_l2():
+    """L2 throughput (% of peak) per launch from the committed ncu summary, if
+    it was taken on the current kernel source; otherwise None."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_code_sha256") != kernel_sha():
+        return None
+    return rec.get("l2_throughput_pct_of_peak")
+
+
 def msbfs_alg_bytes(g, block_bits, level_sum, launches):
     """Algorithmic bytes of the MS-BFS launches: per level the frontier,
     visited and next bitsets once each (3 n S / 8 = 12 n W bytes, W = S / 32)
@@ -549,6 +562,7 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if peak else None,
                 "traffic": traffic, "peak_source": peak_kind,
+                "l2_throughput_pct_of_peak": recorded_l2(),
                 "kernel": "msbfs_kernel", "launches": launches,
                 "avg_launch_ms": bfs_ms / launches if launches else None,
                 "alg_bytes_per_launch": alg / launches if launches else None,
