@@ -343,14 +343,6 @@ int spectral_layout(const SpectralInput& in, int dim, float* out_X, double* out_
         if (e2 != cudaSuccess) return e2;
         return sub(t, 1, w);
     };
-    // full reorthogonalisation against Q[0 .. m), twice, then against t
-    auto reorth = [&](double* w, int m) -> cudaError_t {
-        cudaError_t e2;
-        for (int pass = 0; pass < 2; ++pass) {
-            if ((e2 = dots(Q, m, w, nullptr)) != cudaSuccess || (e2 = sub(Q, m, w)) != cudaSuccess) return e2;
-        }
-        return deflate(w);
-    };
     auto normalize_into = [&](const double* w, double* dst, double* nrm_out) -> cudaError_t {
         double nn = 0.0;
         cudaError_t e2 = dots(w, 1, w, &nn);
