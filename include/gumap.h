@@ -109,6 +109,13 @@ extern "C" {
                                    (default: groups of lanes), 1 = one thread per source (k <= 64;
                                    larger k use a warp), 2 = one warp per source, 3 = a group of
                                    4 to 32 lanes per source (by k); same rows either way          */
+#define GUMAP_OPT_GRAPH      14 /* value: 1 = once two runs in a row had the same sources, outputs and
+                                   (non-default) stream, the third is captured into a CUDA graph
+                                   and every later run with those arguments replays it (one launch
+                                   of the graph instead of one per kernel); any other call on the
+                                   handle drops the graph; a capture the driver refuses falls back
+                                   to ordinary launches; not with GUMAP_OPT_PROFILE. 0 (default) =
+                                   ordinary launches                                              */
 #define GUMAP_OPT_STAGE      10 /* value: 1 (default) = each MS-BFS CTA bulk-copies its slice of the
                                    ordinary-degree rows into shared memory once per launch when
                                    every slice fits; 0 = neighbour ids always read from the CSR;
@@ -279,6 +286,7 @@ typedef struct {
     int64_t batch_model_bytes; /* batched engine: its units' bytes on the per-level model of the
                                   bit-parallel BFS (3 bitset rows of n x W words, in shared memory
                                   there, plus the CSR, per level), since the last reset */
+    int64_t graph_replays;   /* runs served by replaying a captured CUDA graph (GUMAP_OPT_GRAPH) */
 } gumap_knn_stats;
 
 typedef struct {

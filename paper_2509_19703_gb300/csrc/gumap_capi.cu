@@ -202,6 +202,26 @@ struct gumap_knn {
     int opt_engine = GUMAP_ENGINE_AUTO;
     int64_t opt_block_bits = 0;
     int opt_profile = 0;
+    // GUMAP_OPT_GRAPH: the arguments of a run, the run captured for them and
+    // the host-side counts one replay stands for
+    struct RunKey {
+        const int32_t* src = nullptr;
+        int32_t n_src = 0;
+        int32_t* idx = nullptr;
+        uint16_t* dist = nullptr;
+        float* w = nullptr;
+        cudaStream_t st = nullptr;
+        bool operator==(const RunKey& o) const {
+            return src == o.src && n_src == o.n_src && idx == o.idx && dist == o.dist && w == o.w && st == o.st;
+        }
+    };
+    int opt_graph = 0;
+    cudaGraphExec_t graph_exec = nullptr;
+    RunKey graph_key, warm_key, refused_key;
+    int warm_runs = 0;
+    bool graph_refused = false;
+    int64_t graph_d_kernels = 0, graph_d_bfs = 0, graph_d_staged = 0, graph_d_sort = 0;
+    int64_t graph_replays = 0;
     int64_t opt_state_bytes = 0;
     // GUMAP_OPT_DIRECTION: pull only by default. Push levels are correct but
     // were slower on every measured workload: with many sources per block the
@@ -514,13 +534,21 @@ int get_cut(gumap_knn* h, int grid, cudaStream_t st, const gumap_knn::SliceCut**
         pool_free(c.d_ocol, c.ocol_bytes);
         return cuda_fail(e, "cudaMalloc");
     }
+    // the host vectors go out of scope: the copies must have read them before
+    // the layout is registered (a layout whose upload failed is never kept)
+    if ((e = cudaMemcpyAsync(c.d_cut, cut.data(), (size_t)(grid + 1) * 4, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess ||
+        (e = cudaMemcpyAsync(c.d_meta, meta.data(), c.meta_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(c.d_ocol + off, 0, 4 * sizeof(int32_t), st)) != cudaSuccess ||
+        (e = launch_gather_rows(h->d_rp, h->d_col, h->d_order, c.d_meta, (int32_t)nl, c.d_ocol, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+        pool_free(c.d_cut, (size_t)(grid + 1) * 4);
+        pool_free(c.d_meta, c.meta_bytes);
+        pool_free(c.d_ocol, c.ocol_bytes);
+        return cuda_fail(e, "layout upload");
+    }
     h->cuts.push_back(c);  // owned by the handle from here on (freed with it)
-    CK(cudaMemcpyAsync(c.d_cut, cut.data(), (size_t)(grid + 1) * 4, cudaMemcpyHostToDevice, st), "cut upload");
-    CK(cudaMemcpyAsync(c.d_meta, meta.data(), c.meta_bytes, cudaMemcpyHostToDevice, st), "pairs upload");
-    CK(cudaMemsetAsync(c.d_ocol + off, 0, 4 * sizeof(int32_t), st), "row padding");
-    CK(launch_gather_rows(h->d_rp, h->d_col, h->d_order, c.d_meta, (int32_t)nl, c.d_ocol, st), "gather rows");
-    // the host vectors go out of scope: make sure the copies have read them
-    CK(cudaStreamSynchronize(st), "layout upload");
     *out = &h->cuts.back();
     return GUMAP_OK;
 }
@@ -832,6 +860,60 @@ int run_path(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_i
     return GUMAP_OK;
 }
 
+// GUMAP_OPT_GRAPH: forget the captured run (any call that may change the
+// handle's buffers or the state a replay relies on does this first).
+void drop_graph(gumap_knn* h) {
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    h->graph_exec = nullptr;
+}
+
+// Any other call on the handle: the captured run and the warm-up count go.
+void forget_runs(gumap_knn* h) {
+    drop_graph(h);
+    h->warm_runs = 0;
+}
+
+// Capture one run of `key` into a CUDA graph and launch it. The run's
+// buffers exist (two runs with the same arguments came before), so
+// run_path issues only stream-ordered work. Returns false, with no work
+// issued and the host counters as they were, when the capture or the
+// instantiation is refused; the caller then runs normally.
+bool capture_run(gumap_knn* h, const gumap_knn::RunKey& key) {
+    const int64_t k0 = h->kernel_launches, b0 = h->bfs_launches, s0 = h->staged_launches, o0 = h->sort_launches;
+    if (cudaStreamBeginCapture(key.st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int rc = run_path(h, key.src, key.n_src, key.idx, key.dist, key.w, key.st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e_end = cudaStreamEndCapture(key.st, &g);
+    cudaGraphExec_t ex = nullptr;
+    const bool ok = rc == GUMAP_OK && e_end == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    const int64_t dk = h->kernel_launches - k0, db = h->bfs_launches - b0, ds = h->staged_launches - s0,
+                  dso = h->sort_launches - o0;
+    h->kernel_launches = k0;
+    h->bfs_launches = b0;
+    h->staged_launches = s0;
+    h->sort_launches = o0;
+    if (!ok || cudaGraphLaunch(ex, key.st) != cudaSuccess) {
+        if (ex) cudaGraphExecDestroy(ex);
+        cudaGetLastError();
+        return false;
+    }
+    h->graph_exec = ex;
+    h->graph_key = key;
+    h->graph_d_kernels = dk;
+    h->graph_d_bfs = db;
+    h->graph_d_staged = ds;
+    h->graph_d_sort = dso;
+    h->kernel_launches += dk;
+    h->bfs_launches += db;
+    h->staged_launches += ds;
+    h->sort_launches += dso;
+    return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -858,6 +940,7 @@ int gumap_knn_destroy(gumap_knn* h) {
     if (!h) return GUMAP_OK;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();  // nothing queued may still use the buffers handed back below
+    drop_graph(h);
     reap(h, true);
     pool_free(h->d_rp, sizeof(int32_t) * ((size_t)h->n + 2));
     pool_free(h->d_col, sizeof(int32_t) * (size_t)std::max<int64_t>(h->nnz, 1));
@@ -1077,16 +1160,52 @@ int gumap_knn_run(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* 
     CK(cudaSetDevice(h->device), "cudaSetDevice");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     reap(h, false);
+    gumap_knn::RunKey key;
+    key.src = sources;
+    key.n_src = n_src;
+    key.idx = out_idx;
+    key.dist = out_dist;
+    key.w = out_w;
+    key.st = st;
+    const bool graphs = h->opt_graph && !h->opt_profile && st != nullptr;
+    if (graphs && h->graph_exec && h->graph_key == key) {  // replay the captured run
+        CK(cudaGraphLaunch(h->graph_exec, st), "cudaGraphLaunch");
+        h->kernel_launches += h->graph_d_kernels;
+        h->bfs_launches += h->graph_d_bfs;
+        h->staged_launches += h->graph_d_staged;
+        h->sort_launches += h->graph_d_sort;
+        h->graph_replays++;
+        h->last_stream = st;
+        return GUMAP_OK;
+    }
+    drop_graph(h);
     h->last_n_src = n_src;
     h->last_union = false;
+    if (graphs && h->warm_key == key && h->warm_runs >= 2 && !(h->graph_refused && h->refused_key == key)) {
+        if (capture_run(h, key)) {
+            h->graph_replays++;
+            h->last_stream = st;
+            return GUMAP_OK;
+        }
+        h->graph_refused = true;  // this run's capture was refused: run it, and it, normally from now on
+        h->refused_key = key;
+        h->last_n_src = n_src;
+        h->last_union = false;
+    }
     const int rc = run_path(h, sources, n_src, out_idx, out_dist, out_w, st);
     h->last_stream = st;
+    if (graphs && rc == GUMAP_OK) {
+        h->warm_runs = h->warm_key == key ? h->warm_runs : 0;
+        h->warm_key = key;
+        h->warm_runs++;
+    }
     return rc;
 }
 
 int gumap_knn_apsp(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t* out_idx, uint16_t* out_dist,
                    uint16_t* out_apsp, void* stream) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    forget_runs(h);  // a captured run may not outlive this call (GUMAP_OPT_GRAPH)
     if (!(h->flags & GUMAP_EMIT_APSP)) return fail(GUMAP_ERR_INVALID_ARG, "handle not created with GUMAP_EMIT_APSP");
     if (h->batch) return fail(GUMAP_ERR_INVALID_ARG, "all-pairs rows of a batch handle are not available");
     if (h->n > 65535) return fail(GUMAP_ERR_INVALID_ARG, "all-pairs rows need n <= 65535 (uint16 distances)");
@@ -1110,6 +1229,7 @@ int gumap_knn_apsp(gumap_knn* h, const int32_t* sources, int32_t n_src, int32_t*
 int gumap_quality_np(gumap_knn* h, const float* X, int32_t dim, int32_t r, int32_t* out_c, int32_t* out_inter,
                      double* out_sum, void* stream) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    forget_runs(h);  // a captured run may not outlive this call (GUMAP_OPT_GRAPH)
     if (h->batch) return fail(GUMAP_ERR_INVALID_ARG, "quality metrics take a single graph's handle");
     if (!X || !out_sum) return fail(GUMAP_ERR_INVALID_ARG, "NULL drawing or output");
     if (dim < 1 || dim > 8) return fail(GUMAP_ERR_INVALID_ARG, "dim must be in [1, 8]");
@@ -1130,6 +1250,7 @@ int gumap_quality_np(gumap_knn* h, const float* X, int32_t dim, int32_t r, int32
 int gumap_quality_stress(gumap_knn* h, const float* X, int32_t dim, double* out_rows, double* out_stress,
                          void* stream) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    forget_runs(h);  // a captured run may not outlive this call (GUMAP_OPT_GRAPH)
     if (h->batch) return fail(GUMAP_ERR_INVALID_ARG, "quality metrics take a single graph's handle");
     if (!X || !out_stress) return fail(GUMAP_ERR_INVALID_ARG, "NULL drawing or output");
     if (dim < 1 || dim > 8) return fail(GUMAP_ERR_INVALID_ARG, "dim must be in [1, 8]");
@@ -1160,6 +1281,7 @@ int gumap_quality_stress(gumap_knn* h, const float* X, int32_t dim, double* out_
 int gumap_spectral_layout(gumap_knn* h, int32_t dim, float* out_X, double* out_mu, gumap_spectral_info* info,
                           void* stream) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    forget_runs(h);  // a captured run may not outlive this call (GUMAP_OPT_GRAPH)
     if (!out_X) return fail(GUMAP_ERR_INVALID_ARG, "NULL output");
     if (dim < 1 || dim > 8) return fail(GUMAP_ERR_INVALID_ARG, "dim must be in [1, 8]");
     if (!h->last_union) return fail(GUMAP_ERR_INVALID_ARG, "the last run built no union COO");
@@ -1278,6 +1400,7 @@ int gumap_knn_check(gumap_knn* h, void* stream) {
 
 int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
     if (!h) return fail(GUMAP_ERR_INVALID_ARG, "NULL handle");
+    forget_runs(h);  // a captured run may not outlive this call (GUMAP_OPT_GRAPH)
     switch (option) {
         case GUMAP_OPT_ENGINE:
             if (value < GUMAP_ENGINE_AUTO || value > GUMAP_ENGINE_BATCH || value == GUMAP_ENGINE_MSBFS_SM)
@@ -1328,6 +1451,10 @@ int gumap_knn_set_option(gumap_knn* h, int option, int64_t value) {
         case GUMAP_OPT_FRONTIER_BUILD:
             if (value < 0 || value > 3) return fail(GUMAP_ERR_INVALID_ARG, "frontier build must be 0, 1, 2 or 3");
             h->opt_frontier_build = (int)value;
+            return GUMAP_OK;
+        case GUMAP_OPT_GRAPH:
+            if (value != 0 && value != 1) return fail(GUMAP_ERR_INVALID_ARG, "graph option must be 0 or 1");
+            h->opt_graph = (int)value;
             return GUMAP_OK;
         case GUMAP_OPT_STAGE:
             if (value < 0 || value > 2) return fail(GUMAP_ERR_INVALID_ARG, "stage must be 0, 1 or 2");
@@ -1398,6 +1525,7 @@ int gumap_knn_get_stats(gumap_knn* h, gumap_knn_stats* out) {
     out->bfs_push_ms = (double)c.t_push_ns * 1e-6;
     out->bfs_push_levels = c.push_levels;
     out->bfs_staged_launches = h->staged_launches;
+    out->graph_replays = h->graph_replays;
     out->weights_ms = h->weights_ms_done;
     out->sort_ms = h->sort_ms_done;
     out->sort_launches = h->sort_launches;
@@ -1416,6 +1544,7 @@ int gumap_knn_reset_stats(gumap_knn* h) {
     h->weights_ms_done = 0.0;
     h->sort_ms_done = 0.0;
     h->sort_launches = 0;
+    h->graph_replays = 0;
     h->ev_used = 0;
     DeviceCounters c;
     CK(cudaMemcpy(&c, h->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");

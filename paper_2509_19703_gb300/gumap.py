@@ -27,6 +27,7 @@ OPT_DIRECTION, OPT_PUSH_DIV, OPT_PULL_WIDTH, OPT_CTAS_PER_SM, OPT_STAGE = 6, 7, 
 OPT_BATCH_WIDTH = 11
 OPT_COO_BUILD = 12
 OPT_FRONTIER_BUILD = 13
+OPT_GRAPH = 14
 COO_AUTO, COO_RADIX, COO_ROWS = 0, 1, 2
 FRONTIER_AUTO, FRONTIER_THREAD, FRONTIER_WARP, FRONTIER_GROUP = 0, 1, 2, 3
 DIRECTION_AUTO, DIRECTION_PULL, DIRECTION_PUSH = 0, 1, 2
@@ -56,7 +57,7 @@ class _Stats(ctypes.Structure):
                 ("bfs_push_ms", ctypes.c_double), ("bfs_push_levels", ctypes.c_int64),
                 ("bfs_staged_launches", ctypes.c_int64), ("weights_ms", ctypes.c_double),
                 ("sort_ms", ctypes.c_double), ("sort_launches", ctypes.c_int64),
-                ("batch_model_bytes", ctypes.c_int64)]
+                ("batch_model_bytes", ctypes.c_int64), ("graph_replays", ctypes.c_int64)]
 
 
 class _Info(ctypes.Structure):
