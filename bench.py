@@ -1180,6 +1180,19 @@ def config1_summary(args):
            "ms_per_run": ms, "default_engine_ms_per_run": default_ms,
            "gteps": 1024 * 1984 / (ms * 1e-3) / 1e9,
            "autotuned": {key: tuned[key] for key in ("engine", "batch_width", "best_ms")}}
+    # the same runs replayed from a captured CUDA graph (GUMAP_OPT_GRAPH, on a
+    # stream of their own); the parity check below reads a replayed run's rows
+    try:
+        import torch
+        side = torch.cuda.Stream()
+        kg.set_option(gumap.OPT_GRAPH, 1)
+        with torch.cuda.stream(side):
+            graph_ms = event_ms(lambda: kg.run(out=out), reps=50)
+        torch.cuda.synchronize()
+        kg.check()
+        res["graph_replay"] = {"ms_per_run": graph_ms, "replays": kg.stats()["graph_replays"]}
+    except Exception as e:  # reported, not fatal: the line above stands without it
+        res["graph_replay"] = {"error": str(e)[:200]}
     if not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
